@@ -1,0 +1,397 @@
+"""Pins of the oracle against what the mathematics and the paper fix.
+
+None of these checks re-types an oracle formula: each compares the oracle to
+a closed form, an exact conservation identity, a textbook special case, a
+brute-force computation, or an accuracy order stated in the paper (IBB
+second order, IBM first order, Sec. 2.2; IBM-B closer than IBM-U, Sec. 2.2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+
+def test_lattice_isotropy(orc):
+    c, w, opp = orc.lattice()
+    assert abs(w.sum() - 1.0) < 1e-15
+    # second moment c_s^2 delta_ab with c_s^2 = 1/3, zero first and third moments
+    m2 = np.einsum("i,ia,ib->ab", w, c, c)
+    assert np.allclose(m2, np.eye(3) / 3.0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0.0, atol=1e-15)
+    m4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    iso = np.zeros((3, 3, 3, 3))
+    for a in range(3):
+        for b in range(3):
+            for cc in range(3):
+                for d in range(3):
+                    iso[a, b, cc, d] = ((a == b) * (cc == d) + (a == cc) * (b == d) + (a == d) * (b == cc)) / 9.0
+    assert np.allclose(m4, iso, atol=1e-15)
+    for i in range(19):
+        assert np.all(c[opp[i]] == -c[i])
+
+
+def test_moment_basis_orthogonal_and_equilibrium_moments(orc):
+    M = orc.moment_matrix()
+    G = M @ M.T
+    assert np.allclose(G - np.diag(np.diag(G)), 0.0, atol=1e-12)
+    # d'Humieres et al. (2002) equilibrium moments of the second-order
+    # equilibrium, written from the literature's closed forms
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        rho = 1.0 + 0.05 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(3)
+        m = M @ orc.feq(rho, u)
+        ux, uy, uz = u
+        u2 = u @ u
+        expect = [rho, rho * (-11 + 19 * u2), rho * (3 - 5.5 * u2),
+                  rho * ux, -2 / 3 * rho * ux, rho * uy, -2 / 3 * rho * uy, rho * uz, -2 / 3 * rho * uz,
+                  rho * (3 * ux * ux - u2), -0.5 * rho * (3 * ux * ux - u2),
+                  rho * (uy * uy - uz * uz), -0.5 * rho * (uy * uy - uz * uz),
+                  rho * ux * uy, rho * uy * uz, rho * ux * uz, 0.0, 0.0, 0.0]
+        assert np.allclose(m, expect, atol=1e-14)
+
+
+def test_srt_mrt_equals_bgk(orc):
+    f = workloads.random_populations(8, seed=11)
+    rng = np.random.default_rng(4)
+    for k in range(8):
+        F = 1e-3 * rng.standard_normal(3)
+        for tau in (0.51, 0.6, 1.0, 1.7):
+            a = orc.collide_mrt(f[:, k], F, orc.RATES_SRT, tau)
+            b = orc.collide_bgk(f[:, k], F, tau)
+            assert np.max(np.abs(a - b)) < 1e-14
+
+
+def test_collision_conserves_mass_and_adds_force(orc):
+    f = workloads.random_populations(6, seed=5)
+    c, _, _ = orc.lattice()
+    F = np.array([1e-3, -2e-3, 5e-4])
+    for k in range(6):
+        for rs in (orc.RATES_SRT, orc.RATES_DHUMIERES):
+            out = orc.collide_mrt(f[:, k], F, rs, 0.53)
+            assert abs(out.sum() - f[:, k].sum()) < 1e-15
+            assert np.allclose(out @ c - f[:, k] @ c, F, atol=1e-15)
+
+
+def test_dhumieres_rates_relax_nonhydrodynamic_moments(orc):
+    # a population differing from equilibrium only in one ghost moment must
+    # relax that moment by exactly (1 - s_k)
+    M = orc.moment_matrix()
+    s = orc.rates(orc.RATES_DHUMIERES, 0.51)
+    base = orc.feq(1.0, np.zeros(3))
+    for k in (1, 2, 4, 9, 10, 13, 16):
+        dm = np.zeros(19)
+        dm[k] = 1e-3
+        f = base + np.linalg.solve(M, dm)
+        out = orc.collide_mrt(f, np.zeros(3), orc.RATES_DHUMIERES, 0.51)
+        mo = M @ (out - base)
+        assert abs(mo[k] - (1 - s[k]) * 1e-3) < 1e-13
+    assert s[9] == pytest.approx(1 / 0.51)
+
+
+def test_periodic_mass_exact_and_momentum_grows_by_force(orc):
+    n = 8
+    F = (1e-5, -2e-5, 3e-5)
+    S = orc.Sim(n, n, n, 0.7, force=F, rates=orc.RATES_DHUMIERES)
+    S.init_velocity(workloads.hit_velocity(n, seed=1, k_peak=2.0, u_rms=0.02))
+    c, _, _ = orc.lattice()
+    f0 = S.populations()
+    m0, p0 = f0.sum(), (f0.T @ c).sum(axis=0)
+    S.step(25)
+    f1 = S.populations()
+    assert abs(f1.sum() - m0) < 1e-11
+    assert np.allclose((f1.T @ c).sum(axis=0) - p0, 25 * n ** 3 * np.array(F), rtol=1e-10, atol=1e-14)
+
+
+def _taylor_green_ratio(orc, n, tau=0.8, u0=0.01):
+    S = orc.Sim(n, n, 1, tau)
+    k = 2 * np.pi / n
+    x = np.arange(n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    u = np.zeros((3, 1, n, n))
+    u[0, 0] = -u0 * np.cos(k * X) * np.sin(k * Y)
+    u[1, 0] = u0 * np.sin(k * X) * np.cos(k * Y)
+    S.init_velocity(u)
+    nu = (tau - 0.5) / 3
+    t1, t2 = int(0.2 / (nu * k * k)), int(1.0 / (nu * k * k))
+
+    def energy():
+        return float((S.macro()[1] ** 2).sum())
+
+    S.step(t1)
+    e1 = energy()
+    S.step(t2 - t1)
+    e2 = energy()
+    # kinetic energy decays as exp(-4 nu k^2 t): measured / expected rate
+    return math.log(e1 / e2) / (t2 - t1) / (4 * nu * k * k)
+
+
+def test_taylor_green_decay_recovers_viscosity(orc):
+    r16 = _taylor_green_ratio(orc, 16)
+    r32 = _taylor_green_ratio(orc, 32)
+    assert abs(r32 - 1) < 0.01
+    # second-order convergence of the decay rate
+    assert abs(r16 - 1) / abs(r32 - 1) > 3.0
+
+
+def _pipe_poiseuille_error(orc, R, bc, tau=0.8):
+    n = int(2 * R + 4)
+    g = 1e-6
+    S = orc.Sim(n, n, 1, tau, force=(0, 0, g))
+    S.set_pipe(R)
+    nu = (tau - 0.5) / 3
+    x = np.arange(n) - (n - 1) / 2
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    r2 = X ** 2 + Y ** 2
+    ua = np.where(r2 < R * R, g * (R * R - r2) / (4 * nu), 0.0)   # Hagen-Poiseuille
+    u = np.zeros((3, 1, n, n))
+    u[2, 0] = ua
+    S.init_velocity(u)
+    S.step(int(3 * R * R / nu), bc)
+    uz = S.macro()[1][2].reshape(n, n)
+    m = (r2 < R * R) & (S.solid()[0].reshape(n, n) == 0)
+    return math.sqrt(((uz - ua)[m] ** 2).sum() / (ua[m] ** 2).sum())
+
+
+def test_pipe_poiseuille_ibb_second_order(orc):
+    e = [_pipe_poiseuille_error(orc, R, orc.BC_IBB) for R in (4, 8, 16)]
+    order = math.log2(e[0] / e[2]) / 2
+    assert order > 1.8, e
+    assert e[2] < 1e-3
+
+
+def test_pipe_poiseuille_ibm_first_order_and_retraction_helps(orc):
+    eu = [_pipe_poiseuille_error(orc, R, orc.BC_IBM_U) for R in (4, 8)]
+    eb = [_pipe_poiseuille_error(orc, R, orc.BC_IBM_B) for R in (4, 8)]
+    assert 0.5 < math.log2(eu[0] / eu[1]) < 1.6, eu
+    assert eb[0] < eu[0] and eb[1] < eu[1]
+
+
+def test_peskin_delta_identities(orc):
+    rng = np.random.default_rng(0)
+    for r in rng.uniform(0, 1, 50):
+        js = np.arange(-3, 4)
+        ph = np.array([orc.peskin_phi(r - j) for j in js])
+        assert abs(ph.sum() - 1) < 1e-14
+        assert abs(((r - js) * ph).sum()) < 1e-14
+        assert abs((ph ** 2).sum() - 3 / 8) < 1e-14
+    assert orc.peskin_phi(2.0) == 0.0 and orc.peskin_phi(2.5) == 0.0
+
+
+def test_solid_fraction_volume_converges(orc):
+    errs = []
+    for R in (3.0, 6.0, 12.0):
+        X = np.array([0.3, 0.1, 0.2])
+        n = int(R) + 2
+        tot = 0.0
+        for z in range(-n, n + 1):
+            for y in range(-n, n + 1):
+                for x in range(-n, n + 1):
+                    tot += orc.solid_fraction([x, y, z], X, R)
+        errs.append(abs(tot - 4 / 3 * math.pi * R ** 3) / (4 / 3 * math.pi * R ** 3))
+    assert errs[2] < 3e-3
+    assert errs[0] / errs[2] > 6.0  # ~second order over a factor 4 in R
+
+
+def test_marker_counts_and_spacing(orc):
+    assert orc.marker_count(4.0) == 202
+    assert orc.marker_count(3.6) == 164
+    pts = orc.sphere_markers(4.0, 202)
+    assert np.allclose(np.linalg.norm(pts, axis=1), 1.0, atol=1e-14)
+    P = 4.0 * pts
+    d = np.linalg.norm(P[:, None] - P[None], axis=2) + np.eye(202) * 1e9
+    nn = d.min(axis=1)
+    assert 0.75 < nn.mean() < 1.25  # spacing close to one lattice unit
+
+
+def _brute_links(R, X, n):
+    """Brute-force links for one sphere: bisection for the crossing."""
+    idx = np.arange(n)
+    c = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                  [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1],
+                  [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+
+    def inside(p):
+        d = p - X
+        d -= n * np.rint(d / n)
+        return d @ d <= R * R
+
+    out = {}
+    for z in idx:
+        for y in idx:
+            for x in idx:
+                p = np.array([x, y, z], float)
+                if inside(p):
+                    continue
+                for i in range(1, 19):
+                    b = p + c[i]
+                    if not inside(b):
+                        continue
+                    lo, hi = 0.0, 1.0
+                    for _ in range(80):
+                        mid = 0.5 * (lo + hi)
+                        if inside(p + mid * c[i]):
+                            hi = mid
+                        else:
+                            lo = mid
+                    out[(x + n * (y + n * z), i)] = 0.5 * (lo + hi)
+    return out
+
+
+def test_links_match_brute_force(orc):
+    n = 12
+    X = np.array([5.3, 6.1, 5.7])
+    R = 3.2
+    S = orc.Sim(n, n, n, 0.6)
+    S.add_spheres(X[None], [R], U=np.zeros((1, 3)), fixed=True)
+    L = S.links()
+    got = {(int(c), int(d)): q for c, d, q in zip(L["cell"], L["dir"], L["q"])}
+    ref = _brute_links(R, X, n)
+    assert set(got) == set(ref)
+    assert max(abs(got[k] - ref[k]) for k in ref) < 1e-12
+    assert np.all((L["q"] > 0) & (L["q"] <= 1))
+    assert set(np.unique(L["scheme"])) <= {0, 1, 2}
+
+
+def test_uniform_flow_past_moving_sphere_stays_uniform(orc):
+    """f = f_eq(1, U) everywhere and a sphere moving with U: every IBB scheme,
+    the refill and the rigid-body update must keep the state exactly uniform,
+    and the Galilean-invariant momentum exchange must give zero force."""
+    n = 16
+    U = np.array([0.05, 0.02, -0.03])
+    S = orc.Sim(n, n, n, 0.6)
+    u = np.broadcast_to(U[:, None, None, None], (3, n, n, n)).copy()
+    S.init_velocity(u)
+    # two spheres 1.2 apart: the gap between them forces the linear and
+    # single-node fallbacks on some links
+    Xs = np.array([[5.3, 8.1, 7.7], [11.7, 8.3, 7.9]])
+    S.add_spheres(Xs, [2.6, 2.6], density_ratio=2.0, U=np.stack([U, U]), W=np.zeros((2, 3)))
+    schemes = set(S.links()["scheme"].tolist())
+    X0 = S.particles()["X"].copy()
+    feq = orc.feq(1.0, U)
+    for step in range(30):
+        S.step(1, orc.BC_IBB)
+        P = S.particles()
+        assert np.max(np.abs(P["F"])) < 1e-13
+        schemes |= set(S.links()["scheme"].tolist())
+    f = S.populations()
+    solid = S.solid()[0].astype(bool)
+    assert np.max(np.abs(f[:, ~solid] - feq[:, None])) < 1e-14
+    assert np.allclose(S.particles()["U"], U[None], atol=1e-15)
+    assert np.allclose(S.particles()["W"], 0.0, atol=1e-15)
+    moved = (X0 + 30 * U[None]) % n
+    assert np.allclose(S.particles()["X"], moved, atol=1e-12)
+    assert schemes == {0, 1, 2}
+
+
+def test_momentum_exchange_balances_fluid_momentum(orc):
+    """For a fixed wall, the fluid momentum changes per step by exactly the
+    body force on the fluid cells minus the momentum-exchange force."""
+    n = 14
+    g = np.array([2e-5, -1e-5, 0.5e-5])
+    S = orc.Sim(n, n, n, 0.65, force=g, rates=orc.RATES_DHUMIERES)
+    S.init_velocity(workloads.hit_velocity(n, seed=2, k_peak=2.0, u_rms=0.01))
+    S.add_spheres(np.array([[6.4, 7.2, 6.9]]), [3.7], U=np.zeros((1, 3)), W=np.zeros((1, 3)), fixed=True)
+    c, _, _ = orc.lattice()
+    fluid = S.solid()[0] == 0
+    S.step(3, orc.BC_IBB)
+    for _ in range(4):
+        p0 = (S.populations()[:, fluid].T @ c).sum(axis=0)
+        S.step(1, orc.BC_IBB)
+        p1 = (S.populations()[:, fluid].T @ c).sum(axis=0)
+        F = S.particles()["F"][0]
+        assert np.allclose(p1 - p0, fluid.sum() * g - F, rtol=0, atol=1e-15 + 1e-11 * np.abs(F).max())
+    assert np.abs(F).max() > 1e-5
+
+
+def test_ibm_spreading_identities(orc):
+    """Sum of the spread force equals the marker force sum, and its moment
+    about the centre equals the marker torque (partition of unity and zero
+    first moment of the Peskin kernel); the momentum budget of the fluid
+    closes with the IBM force."""
+    n = 16
+    S = orc.Sim(n, n, n, 0.7)
+    S.init_velocity(workloads.hit_velocity(n, seed=7, k_peak=2.0, u_rms=0.02))
+    Xp = np.array([7.3, 8.6, 7.9])
+    S.add_spheres(Xp[None], [3.5], density_ratio=3.0, U=np.array([[0.01, 0.0, -0.005]]),
+                  W=np.array([[0.0, 0.002, 0.001]]), fixed=True)
+    c, _, _ = orc.lattice()
+    S.step(1, orc.BC_IBM_B)
+    p0 = (S.populations().T @ c).sum(axis=0)
+    S.step(1, orc.BC_IBM_B)
+    p1 = (S.populations().T @ c).sum(axis=0)
+    Fx = S.ibm_force()
+    m = S.markers()
+    Fl = m["F"] * m["dV"][:, None]
+    assert np.allclose(Fx.sum(axis=1), Fl.sum(axis=0), atol=1e-15)
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([xx.ravel(), yy.ravel(), zz.ravel()]) - Xp[:, None]
+    r -= n * np.rint(r / n)
+    tx = np.cross(r.T, Fx.T).sum(axis=0)
+    rl = m["X"] - Xp
+    rl -= n * np.rint(rl / n)
+    tl = np.cross(rl, Fl).sum(axis=0)
+    assert np.allclose(tx, tl, atol=1e-14)
+    # the fluid gains exactly the IBM force (no body force here)
+    assert np.allclose(p1 - p0, Fl.sum(axis=0), atol=1e-14)
+    # residual of the no-slip condition shrinks over the three passes
+    res = [S.marker_residual(k) for k in range(3)]
+    assert res[0] > res[1] > res[2]
+
+
+def test_particle_integrator_free_flight_and_restitution(orc):
+    n = 64
+    S = orc.Sim(n, 8, 8, 0.6)
+    R = 4.0
+    X = np.array([[20.0, 4.0, 4.0], [40.0, 4.0, 4.0]])
+    v = 0.01
+    S.add_spheres(X, [R, R], density_ratio=5.0, U=np.array([[v, 0, 0], [-v, 0, 0]]),
+                  W=np.array([[0, 0, 0.003], [0, 0, 0]]))
+    S.particles_advance(1200)
+    P = S.particles()
+    # head-on collision in vacuum: relative speed returns scaled by e = 0.97
+    vrel = P["U"][1, 0] - P["U"][0, 0]
+    assert vrel == pytest.approx(2 * v * 0.97, rel=0.03)
+    assert np.allclose(P["U"][:, 1:], 0.0, atol=1e-18)
+    assert P["W"][0, 2] == 0.003  # torque-free: rotation kept exactly
+    # momentum conserved exactly in the contact
+    assert abs(P["U"][0, 0] + P["U"][1, 0]) < 1e-16
+
+
+def test_dissipation_of_single_mode(orc):
+    """eps = 2 nu <s_ij s_ij> with central differences: for u_x = A sin(k y)
+    it is nu A^2 sin(k)^2 / 2; the kinetic energy is A^2/4."""
+    n, A, tau = 16, 1e-3, 0.8
+    k = 2 * np.pi * 3 / n
+    S = orc.Sim(n, n, n, tau)
+    y = np.arange(n)
+    u = np.zeros((3, n, n, n))
+    u[0] = A * np.sin(k * y)[None, :, None]
+    S.init_velocity(u)
+    st = S.stats(0)
+    nu = (tau - 0.5) / 3
+    assert st["dissipation"] == pytest.approx(nu * A * A * math.sin(k) ** 2 / 2, rel=1e-9)
+    assert st["kinetic_energy"] == pytest.approx(A * A / 4, rel=1e-9)
+
+
+def test_radial_bins_count_shells(orc):
+    n = 20
+    S = orc.Sim(n, n, n, 0.6)
+    u = np.zeros((3, n, n, n))
+    u[1] = 0.01
+    S.init_velocity(u)
+    Xp = np.array([9.4, 10.2, 9.8])
+    S.add_spheres(Xp[None], [4.0], U=np.array([[0.0, 0.01, 0.0]]), fixed=True)
+    st = S.stats(orc.STATS_BINS)
+    zz, yy, xx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    d = np.stack([xx, yy, zz]).reshape(3, -1) - Xp[:, None]
+    d -= n * np.rint(d / n)
+    r = np.sqrt((d ** 2).sum(axis=0)) / 4.0
+    fluid = r * 4.0 > 4.0
+    b = np.floor((r[fluid] - 1) / 0.05).astype(int)
+    cnt = np.bincount(b[(b >= 0) & (b < 40)], minlength=40)
+    assert np.array_equal(np.array(st["bin_count"]), cnt)
+    occupied = cnt > 0
+    assert np.allclose(np.array(st["bin_tke"])[occupied], 1.0, atol=1e-12)
