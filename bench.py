@@ -1,0 +1,385 @@
+"""Benchmark of the lattice Boltzmann hot path on GB300.
+
+Workload (the pipe-flow configuration of Sec. 2.1 on a reduced grid): a
+periodic pipe of diameter 146 lu and length 438 lu in a 148x148x438 D3Q19
+grid, FP32 populations, SRT collision, nu = 0.0032 (Table 1), body force from
+Re_tau = 180, initial laminar profile plus 5 % seeded divergence-free
+perturbations (synthetic stand-in for the developed turbulent pipe flow).
+One step = one lbm_step: the fused pull-stream-collide sweep with the linear
+interpolated bounce-back wall. The populations (2 x 1.46 GB) are far larger
+than L2, so no flush is needed between steps.
+
+Also reported in the same line: the IBM-B wall, FP16/BF16 population storage,
+and the particle-laden 256^3 box with 2000 moving spheres (IBB and IBM-B), the
+oracle (CPU, FP64) on a bounded sample of the pipe, and the end-to-end rate
+through the C ABI with the initial field uploaded from pinned host memory and
+the final velocity field read back.
+
+--impl reference times the oracle (the plain CPU implementation) on a
+148x148x32 slab of the same pipe per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+PIPE = workloads.PIPE_148
+PP = workloads.pipe_parameters(PIPE["radius"], PIPE["nu"], PIPE["re_tau"])
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def pipe_field(nz=None):
+    nz = nz or PIPE["nz"]
+    return workloads.pipe_velocity(PIPE["nx"], PIPE["ny"], nz, PIPE["radius"], PP["u_bulk"],
+                                   PIPE["perturbation"], seed=0)
+
+
+# ------------------------------------------------------------------ clocks --
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- GPU runs ----
+def run_case(lbm, torch, name, nx, ny, nz, tau, force, storage, rates, bc, steps, warmup, setup, fluid_cells=None,
+             profile=True):
+    """Build one context, warm up, time `steps` steps with CUDA events on the
+    library's stream; returns MLUPS and the per-group kernel profile."""
+    L = lbm.Lattice(nx, ny, nz, tau, force=force, storage=storage, rates=rates,
+                    max_particles=setup.get("max_particles", 0))
+    setup["init"](L)
+    L.step(warmup, bc)
+    torch.cuda.synchronize()
+    if fluid_cells is None:
+        fluid_cells = int(np.count_nonzero((L.flags() & 1) == 0)) if bc == lbm.BC_IBB else nx * ny * nz
+    s = L.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if profile:
+        L.profile_enable(True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    L.step(steps, bc)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = L.profile(0) if profile else None
+    st = L.stats(0)
+    ok = bool(np.isfinite(st["kinetic_energy"]))
+    bulk_cells = None
+    if bc == lbm.BC_IBB:
+        fl = L.flags()
+        bulk_cells = int(np.count_nonzero(fl & 3 == 0))
+    elif bc in (lbm.BC_IBM_U, lbm.BC_IBM_B):
+        fl = L.flags()
+        bulk_cells = int(np.count_nonzero(fl & 4 == 0))
+    else:
+        bulk_cells = nx * ny * nz
+    L.close()
+    del L
+    torch.cuda.empty_cache()
+    return dict(name=name, ms=ms, steps=steps, mlups=fluid_cells * steps / (ms * 1e-3) / 1e6, fluid_cells=fluid_cells,
+                bulk_cells=bulk_cells, ncells=nx * ny * nz, prof=prof, finite=ok)
+
+
+def pipe_setup(lbm, storage=None):
+    u = pipe_field()
+
+    def init(L):
+        L.init_velocity(u)
+        L.set_pipe(PIPE["radius"])
+    return dict(init=init)
+
+
+def hit_setup(n, n_particles, seed=0):
+    u = workloads.hit_velocity(n, seed=seed, k_peak=8.0, u_rms=0.03, dtype=np.float64)
+    X = workloads.place_spheres((n, n, n), n_particles, 4.0, 1.0, seed=seed)
+
+    def init(L):
+        L.init_velocity(u)
+        L.add_spheres(X, 4.0, density_ratio=5.0)
+    return dict(init=init, max_particles=n_particles)
+
+
+def e2e_pipe(lbm, torch, steps):
+    """Same workload through the C ABI from host buffers: the initial field is
+    uploaded from pinned host memory and the final velocity field read back,
+    both inside the timed region."""
+    nx, ny, nz = PIPE["nx"], PIPE["ny"], PIPE["nz"]
+    N = nx * ny * nz
+    u = pipe_field()
+    host_in = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+    host_in.numpy()[:] = u.reshape(-1)
+    host_out = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
+    L = lbm.Lattice(nx, ny, nz, PP["tau"], force=(0, 0, PP["g"]), storage=lbm.F32, rates=lbm.RATES_SRT)
+    L.set_pipe(PIPE["radius"])
+    fluid = int(np.count_nonzero((L.flags() & 1) == 0))
+    import ctypes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = L.L.lbm_init_velocity(L.h, ctypes.cast(host_in.data_ptr(), ctypes.POINTER(ctypes.c_double)), 1.0)
+    L._check(rc)
+    L.step(steps, lbm.BC_IBB)
+    rc = L.L.lbm_get_field(L.h, lbm.FIELD_U, ctypes.c_void_p(host_out.data_ptr()), 3 * N * 8)
+    L._check(rc)
+    t1 = time.perf_counter()
+    L.close()
+    sec = t1 - t0
+    return dict(value=fluid * steps / sec / 1e6, unit="MLUPS", h2d_bytes_per_step=3 * N * 8 // steps,
+                d2h_bytes_per_step=3 * N * 8 // steps, steps=steps, seconds=sec)
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def oracle_pipe_slab(nz_slab, steps, threads=None):
+    import oracle
+    if threads:
+        oracle.set_threads(threads)
+    nx, ny = PIPE["nx"], PIPE["ny"]
+    S = oracle.Sim(nx, ny, nz_slab, PP["tau"], force=(0, 0, PP["g"]))
+    S.init_velocity(pipe_field(nz_slab))
+    S.set_pipe(PIPE["radius"])
+    fluid = int(np.count_nonzero(S.solid()[0] == 0))
+    S.step(1, oracle.BC_IBB)
+    t0 = time.perf_counter()
+    S.step(steps, oracle.BC_IBB)
+    sec = time.perf_counter() - t0
+    S.close()
+    return fluid * steps / sec / 1e6, sec, oracle.get_threads(), fluid
+
+
+def cpu_baseline(target_seconds=12.0):
+    # calibrate on one step, then run ~target_seconds of oracle work
+    _, sec1, cores, _ = oracle_pipe_slab(16, 1)
+    steps = max(1, int(target_seconds / max(sec1, 1e-3)))
+    mlups, sec, cores, fluid = oracle_pipe_slab(16, steps)
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, IBB pipe slab 148x148x16 ({fluid} fluid cells), {steps} steps, {sec:.1f} s"}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_internal.cuh", "stream_collide.cu"):
+        with open(os.path.join(ROOT, "paper_1906_05448_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[kernel_key]
+        if e.get("source_hash") != source_hash():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ main ---
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        nz = 32
+        # warm-up steps of the sample, then the timed steps
+        oracle_pipe_slab(nz, max(1, min(args.warmup, 3)))
+        mlups, sec, cores, fluid = oracle_pipe_slab(nz, args.steps)
+        line = {"metric": "MLUPS (pipe 148x148x438, IBB wall)", "value": round(mlups, 4), "unit": "MLUPS",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * sec / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": "pipe D=146 L=438 in 148x148x438 D3Q19, IBB; oracle sample: 148x148x32 slab",
+                           "l2": "oracle on host cores"},
+                "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                 "sample": f"148x148x32 slab of the pipe ({fluid} fluid cells) per step"},
+                "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_1906_05448_gb300 import build as B
+    from paper_1906_05448_gb300 import lbm
+    B.build()
+    lbm.load()
+    dev = torch.cuda.current_device()
+    hbm_peak, peak_kind = peaks()
+
+    # main line: pipe, IBB, FP32 (replicas on every rank)
+    setup = pipe_setup(lbm)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    main_res = run_case(lbm, torch, "pipe_ibb_f32", PIPE["nx"], PIPE["ny"], PIPE["nz"], PP["tau"], (0, 0, PP["g"]),
+                        lbm.F32, lbm.RATES_SRT, lbm.BC_IBB, args.steps, args.warmup, setup)
+    clk = clocks.stop()
+    ms_total = main_res["ms"]
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    value = main_res["fluid_cells"] * args.steps * world / (ms_total * 1e-3) / 1e6
+    prof = main_res["prof"]
+    bulk_ms = prof["ms"]["bulk"] / max(1, prof["spans"]["bulk"])
+    bulk_bytes = 2 * 19 * 4 * main_res["bulk_cells"] + main_res["ncells"]  # populations + flag byte per cell
+    achieved = bulk_bytes / (bulk_ms * 1e-3) / 1e9
+    launches = sum(prof["launches"].values())
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for name, storage, bc in (("pipe_ibm_b_f32", lbm.F32, lbm.BC_IBM_B), ("pipe_ibb_f16s", lbm.F16S, lbm.BC_IBB),
+                                  ("pipe_ibb_bf16s", lbm.BF16S, lbm.BC_IBB)):
+            r = run_case(lbm, torch, name, PIPE["nx"], PIPE["ny"], PIPE["nz"], PP["tau"], (0, 0, PP["g"]),
+                         storage, lbm.RATES_SRT, bc, args.steps, min(args.warmup, 10), pipe_setup(lbm))
+            p = r["prof"]
+            bms = p["ms"]["bulk"] / max(1, p["spans"]["bulk"])
+            sb = 4 if storage == lbm.F32 else 2
+            variants[name] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms"] / r["steps"], 4),
+                              "bulk_kernel_gbs": round((2 * 19 * sb * r["bulk_cells"] + r["ncells"]) / (bms * 1e-3) / 1e9, 1),
+                              "group_ms_per_step": {k: round(v / r["steps"], 4) for k, v in p["ms"].items() if v > 0},
+                              "finite": r["finite"]}
+        hs = hit_setup(256, 2000)
+        for name, bc in (("hit256_2000p_ibb_f32", lbm.BC_IBB), ("hit256_2000p_ibm_b_f32", lbm.BC_IBM_B)):
+            r = run_case(lbm, torch, name, 256, 256, 256, 0.51, (0, 0, 0), lbm.F32, lbm.RATES_DHUMIERES, bc,
+                         max(20, args.steps // 4), 5, hs)
+            p = r["prof"]
+            variants[name] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms"] / r["steps"], 4),
+                              "group_ms_per_step": {k: round(v / r["steps"], 4) for k, v in p["ms"].items() if v > 0},
+                              "launches_per_step": round(sum(p["launches"].values()) / r["steps"], 1),
+                              "finite": r["finite"]}
+
+    e2e = None
+    if rank == 0:
+        e2e = e2e_pipe(lbm, torch, args.steps)
+        e2e = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in e2e.items()}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS (pipe 148x148x438, IBB wall)",
+            "value": round(value, 1),
+            "unit": "MLUPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_total / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "pipe D=146 L=438 in 148x148x438 D3Q19, FP32 populations, SRT, nu=0.0032, "
+                                   "Re_tau=180 body force, linear IBB wall",
+                       "fluid_cells": main_res["fluid_cells"], "parallelism": f"replicas x{world}",
+                       "l2": "no flush: populations 2x1.46 GB >> 129 MB L2"},
+            "roofline": {"bound": "hbm", "kernel": "stream_collide_bulk<f32,srt,ibb>",
+                         "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind,
+                         "traffic": traffic_for("stream_collide_bulk_pipe_f32"),
+                         "algorithmic_bytes_per_launch": bulk_bytes,
+                         "avg_launch_ms": round(bulk_ms, 5)},
+            "group_ms_per_step": {k: round(v / args.steps, 4) for k, v in prof["ms"].items() if v > 0},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

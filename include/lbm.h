@@ -1,0 +1,197 @@
+/* lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann library with
+ * interpolated bounce-back (IBB) and immersed boundary (IBM) no-slip walls.
+ *
+ * What it computes: the method compared in Peng et al., "Comparative study
+ * of IBB and IBM in the lattice Boltzmann method, Part II: turbulent flows"
+ * (arXiv:1906.05448): a D3Q19 MRT lattice Boltzmann fluid driven by a body
+ * force (Sec. 2.1), with no-slip walls on a pipe (Sec. 2.1, Table 1) and on
+ * moving spheres (Sec. 3.1, Table 2) realised either by interpolated
+ * bounce-back (quadratic/linear Bouzidi with single-node fallback,
+ * Galilean-invariant momentum exchange, refill of uncovered nodes) or by
+ * direct-forcing IBM (Uhlmann, or Breugem with r_d = 0.4, Peskin 4-point
+ * delta, two extra forcing iterations, Kempe inner-fluid inertia), with
+ * particle motion in FP64 and the statistics of Secs. 2.2 and 3.2.
+ *
+ * Conventions for every call:
+ *  - Lattice units (dx = dt = 1). Node (x,y,z) sits at coordinate (x,y,z).
+ *  - Scalar fields: idx = x + nx*(y + ny*z). Vector fields: three planes,
+ *    v[c*N + idx]. Populations: 19 planes, f[i*N + idx], velocity order
+ *    0:(0,0,0) 1:(1,0,0) 2:(-1,0,0) 3:(0,1,0) 4:(0,-1,0) 5:(0,0,1) 6:(0,0,-1)
+ *    7:(1,1,0) 8:(-1,-1,0) 9:(1,-1,0) 10:(-1,1,0) 11:(1,0,1) 12:(-1,0,-1)
+ *    13:(1,0,-1) 14:(-1,0,1) 15:(0,1,1) 16:(0,-1,-1) 17:(0,1,-1) 18:(0,-1,1).
+ *  - Particle arrays are (n,3) row-major FP64 on the host.
+ *  - Host pointers are read during the call only and never retained.
+ *  - Device memory: the caller owns one device buffer (the workspace) of at
+ *    least lbm_workspace_bytes() bytes, 256-byte aligned, alive until
+ *    lbm_destroy(). The library allocates no device memory of its own; it
+ *    allocates a small pinned host block for status words.
+ *  - Every kernel is launched on the caller's CUDA stream given at create.
+ *    Calls that return host data synchronise that stream; lbm_step does not.
+ *  - Errors: every call returns an lbm_status; lbm_last_error() gives a
+ *    one-line reason. After LBM_EUNSTABLE or LBM_ECUDA the context accepts
+ *    only lbm_stats / lbm_get_* / lbm_destroy (others return LBM_ESTATE).
+ *  - One context per host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* bad argument (sizes, pointers, enum values) */
+    LBM_ENOMEM = 2,      /* workspace too small or a capacity exceeded */
+    LBM_ECUDA = 3,       /* a CUDA call failed; detail in lbm_last_error */
+    LBM_EUNSTABLE = 4,   /* the watchdog saw NaN/Inf, rho outside [0.5,2] or |u| > 0.3 */
+    LBM_ETIMEOUT = 5,    /* a bounded host wait on the stream ran out */
+    LBM_ESTATE = 6,      /* call not allowed in the current state */
+    LBM_EUNSUPPORTED = 7 /* combination not built */
+} lbm_status;
+
+/* No-slip treatment used by lbm_step (Sec. 2.1, Sec. 3.1). */
+typedef enum {
+    LBM_BC_NONE = 0,  /* plain periodic box: geometry ignored */
+    LBM_BC_IBB = 1,   /* interpolated bounce-back */
+    LBM_BC_IBM_U = 2, /* direct-forcing IBM, markers on the surface (r_d = 0) */
+    LBM_BC_IBM_B = 3  /* direct-forcing IBM, markers retracted by r_d = 0.4 */
+} lbm_bc;
+
+/* Population storage in HBM. F64/F32 store f_i - w_i in that precision;
+ * F16S/BF16S store f_i - w_i in 16 bits (FP16 scaled by 2^10, or BF16),
+ * always with FP32 collision arithmetic. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_storage;
+
+/* Relaxation rates: SRT = all non-conserved moments at 1/tau (the
+ * single-parameter setting of Sec. 2.1); DHUMIERES = the multiple rates of
+ * d'Humieres et al. 2002 used in Sec. 3.1 (shear moments at 1/tau). */
+typedef enum { LBM_RATES_SRT = 0, LBM_RATES_DHUMIERES = 1 } lbm_rates;
+
+typedef struct {
+    int nx, ny, nz;          /* grid, each >= 4, nx*ny*nz < 2^31 */
+    int storage;             /* lbm_storage */
+    int rates;               /* lbm_rates */
+    int max_particles;       /* capacity for spheres (0: none) */
+    long long max_links;     /* IBB link capacity (0: derived from the grid and max_particles) */
+    long long max_markers;   /* IBM marker capacity (0: derived) */
+    long long max_sites;     /* boundary / support cell capacity (0: derived) */
+} lbm_grid;
+
+/* Bytes of device workspace lbm_create needs for this grid. 0 on bad input. */
+size_t lbm_workspace_bytes(const lbm_grid *grid);
+
+/* Create a context (Sec. 2.1 problem statement: periodic box, relaxation
+ * time tau > 0.5, uniform body force per unit volume `force` acting on the
+ * fluid cells). Populations start at equilibrium with rho = 1, u = 0.
+ * dev_workspace: caller-owned device buffer (see conventions);
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: LBM_EINVAL (bad grid/tau/pointers), LBM_ENOMEM (bytes too small),
+ * LBM_ECUDA. */
+lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], void *dev_workspace,
+                      size_t bytes, void *cuda_stream, lbm_ctx **out);
+
+/* Set every population to f_eq(rho0, u) from a host velocity field u
+ * (3*N doubles, component-major). Synchronous. Only before the first step. */
+lbm_status lbm_init_velocity(lbm_ctx *ctx, const double *u_host, double rho0);
+
+/* Set the populations from a host array of 19*N doubles (unshifted f_i). */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f_host);
+
+/* Pipe along z, centre ((nx-1)/2, (ny-1)/2), radius R: cells with
+ * (x-cx)^2 + (y-cy)^2 >= R^2 are outside (Sec. 2.1). Exclusive with spheres. */
+lbm_status lbm_set_pipe(lbm_ctx *ctx, double radius);
+
+/* Add n spheres (Sec. 3.1): centres xyz (n,3), radii (n), particle/fluid
+ * density ratio. vel/omega may be NULL: then the translation velocity is the
+ * fluid velocity averaged over the particle volume and the rotation is zero
+ * (the release of Sec. 3.1). fixed != 0 holds the particles in place (their
+ * velocities still move the wall). Once per context, before the first step. */
+lbm_status lbm_add_spheres(lbm_ctx *ctx, int n, const double *xyz, const double *radius, double density_ratio,
+                           const double *vel, const double *omega, int fixed);
+
+/* Advance nsteps time steps with no-slip treatment bc. The first call fixes
+ * bc for the life of the context (another bc later returns LBM_ESTATE).
+ * Asynchronous on the stream: instability found by the watchdog of one call
+ * is reported by the next call that synchronises (lbm_step when the previous
+ * check has completed, lbm_stats, lbm_get_*). */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps, int bc);
+
+#define LBM_STATS_UNMASK 1   /* IBM: statistics on the raw virtual fluid inside particles */
+#define LBM_STATS_BINS 4     /* radial profiles around particles (Sec. 3.2) */
+#define LBM_NBINS 40
+
+typedef struct {
+    double mass, momentum[3];
+    double kinetic_energy, dissipation;             /* averages over all cells (masked velocity) */
+    double kinetic_energy_fluid, dissipation_fluid; /* averages over cells outside solids */
+    double particle_ke, particle_ake;               /* sum 1/2 m U^2, sum 1/2 I W^2 */
+    double force[3], torque[3];                     /* summed hydrodynamic force / torque on particles */
+    double bulk_velocity;                           /* pipe: mean u_z inside */
+    int nbins;
+    double bin_r[LBM_NBINS], bin_tke[LBM_NBINS], bin_eps[LBM_NBINS];
+    long long bin_count[LBM_NBINS];
+    long long nfluid, nlinks, nmarkers, step;
+} lbm_stats_t;
+
+/* Statistics of the current state (Sec. 3.2 masking, 2nd-order central
+ * differences, dissipation 2 nu s_ij s_ij; Sec. 2.2 bulk velocity). Syncs. */
+lbm_status lbm_stats(lbm_ctx *ctx, int flags, lbm_stats_t *out);
+
+#define LBM_FIELD_RHO 0      /* N doubles */
+#define LBM_FIELD_U 1        /* 3N doubles */
+#define LBM_FIELD_POPS 2     /* 19N doubles, unshifted f_i (post-collision state) */
+#define LBM_FIELD_FLAGS 3    /* N bytes: bit0 solid, bit1 IBB boundary cell, bit2 IBM support cell */
+#define LBM_FIELD_IBM_FORCE 4 /* 3N doubles: IBM force of the last step */
+
+/* Copy a field to host memory dst of `bytes` bytes. Syncs. Populations of
+ * solid cells under IBB are undefined; rho and u report 0 there. */
+lbm_status lbm_get_field(lbm_ctx *ctx, int which, void *dst, size_t bytes);
+
+/* Number of IBB boundary links of the current geometry. */
+lbm_status lbm_num_links(lbm_ctx *ctx, long long *n);
+
+/* Boundary links sorted by (cell, dir): fluid cell, direction i with
+ * cell + c_i solid, scheme (0 quadratic, 1 linear, 2 single-node), wall
+ * fraction q in (0,1] (FP64), owning particle (-1 for the pipe). Each array
+ * holds at least `capacity` entries. Syncs. */
+lbm_status lbm_get_links(lbm_ctx *ctx, long long capacity, long long *cell, int *dir, int *scheme, double *q,
+                         int *pid);
+
+/* Particle state (n,3) arrays; any pointer may be NULL. F/T are the
+ * hydrodynamic force and torque of the last step. Syncs. */
+lbm_status lbm_get_particles(lbm_ctx *ctx, double *X, double *U, double *W, double *F, double *T);
+
+/* IBM markers of the current step: positions (m,3), accumulated force
+ * density (m,3), volume (m), owner (m; -1 for the pipe). Syncs. */
+lbm_status lbm_num_markers(lbm_ctx *ctx, long long *n);
+lbm_status lbm_get_markers(lbm_ctx *ctx, long long capacity, double *X, double *F, double *dV, int *pid);
+
+/* Per-kernel-group timing with CUDA events recorded on the library's stream
+ * around each group of launches, and a count of every kernel launch.
+ * Groups: 0 bulk stream-collide sweep, 1 IBB boundary cells, 2 IBM forcing
+ * passes, 3 IBM support-cell collision, 4 particle force/motion, 5 geometry
+ * update (flags, refill, link or support lists), 6 statistics.
+ * enable = 1 starts recording (and clears totals), 0 stops; out (nullable)
+ * receives the totals since the last enable, after synchronising. */
+#define LBM_NGROUPS 8
+typedef struct {
+    double ms[LBM_NGROUPS];
+    long long spans[LBM_NGROUPS];     /* timed spans per group */
+    long long launches[LBM_NGROUPS];  /* kernels launched per group */
+    long long total_launches;         /* every kernel launched since create */
+} lbm_profile_t;
+lbm_status lbm_profile(lbm_ctx *ctx, int enable, lbm_profile_t *out);
+
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(int status);
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,348 @@
+// Diagnostics (Sec. 3.2, Sec. 2.2): macroscopic fields of the current state,
+// rigid-body masking of particle regions, kinetic energy, dissipation
+// 2 nu s_ij s_ij from second-order central differences, radial profiles
+// around particles and the pipe bulk velocity. Sums are FP64 block partials
+// reduced on the host in block order (deterministic).
+#include "lbm_internal.cuh"
+
+#include <vector>
+#include <cstring>
+
+namespace lbmgb {
+
+__device__ __forceinline__ double dmimg(double d, int n) {
+    if (d > 0.5 * n) d = __dsub_rn(d, (double)n);
+    else if (d < -0.5 * n) d = __dadd_rn(d, (double)n);
+    return d;
+}
+__device__ __forceinline__ int dwrap(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// rho and u of the post-collision state: sum f c = rho u + F/2 after a Guo
+// collision with total force F (body force on fluid cells + IBM force).
+template <int S>
+__global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux, const double *sup_F, double *rho_o,
+                             double *u_o, long long N, double F0, double F1, double F2, int ibb, int ibm,
+                             long long max_sites) {
+    typedef typename Store<S>::T T;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const uint8_t fl = flags[c];
+    if (ibb && (fl & FL_SOLID)) {
+        rho_o[c] = 0.0;
+        u_o[c] = u_o[N + c] = u_o[2 * N + c] = 0.0;
+        return;
+    }
+    const T *P = (const T *)A;
+    double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+    for (int i = 0; i < 19; i++) {
+        double g;
+        if (S == LBM_F64) g = *(const double *)(P + i * N + c);
+        else if (S == LBM_F32) g = *(const float *)(P + i * N + c);
+        else if (S == LBM_F16S) g = (double)__half2float(*(const __half *)(P + i * N + c)) / (double)F16_SCALE;
+        else g = (double)__bfloat162float(*(const __nv_bfloat16 *)(P + i * N + c));
+        r += g;
+        j0 += g * cx(i);
+        j1 += g * cy(i);
+        j2 += g * cz(i);
+    }
+    const bool fluid = !(fl & FL_SOLID);
+    double Fx = fluid ? F0 : 0.0, Fy = fluid ? F1 : 0.0, Fz = fluid ? F2 : 0.0;
+    if (ibm && (fl & FL_SUP) && aux[c] >= 0 && aux[c] < max_sites) {
+        const int s = aux[c];
+        Fx += sup_F[3 * s];
+        Fy += sup_F[3 * s + 1];
+        Fz += sup_F[3 * s + 2];
+    }
+    const double rho = 1.0 + r;
+    rho_o[c] = rho;
+    u_o[c] = (j0 - 0.5 * Fx) / rho;
+    u_o[N + c] = (j1 - 0.5 * Fy) / rho;
+    u_o[2 * N + c] = (j2 - 0.5 * Fz) / rho;
+}
+
+cudaError_t launch_macro(Ctx &c, int /*mask_mode*/) {
+    count_launch(c, G_STATS);
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+    const int ibb = c.armed_bc == LBM_BC_IBB;
+    const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
+    switch (c.storage) {
+#define MK(S) macro_kernel<S><<<nb, 256, 0, c.stream>>>(c.fA, c.flags, c.aux, c.sup_F, c.rho_f, c.u_f, c.N, c.F[0], \
+                                                           c.F[1], c.F[2], ibb, ibm, c.max_sites)
+    case LBM_F64: MK(LBM_F64); break;
+    case LBM_F32: MK(LBM_F32); break;
+    case LBM_F16S: MK(LBM_F16S); break;
+    default: MK(LBM_BF16S); break;
+#undef MK
+    }
+    return cudaGetLastError();
+}
+
+constexpr int SB = 256;     // threads per statistics block
+constexpr int SNB = 1024;   // statistics blocks (fixed: the reduction order does not depend on the grid)
+constexpr int NP = 16;      // partial sums per block
+
+template <int NV>
+__device__ void sblock_sum(double v[NV], double *sh) {
+    for (int k = 0; k < NV; k++) sh[k * SB + threadIdx.x] = v[k];
+    __syncthreads();
+    for (int s = SB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < NV; k++) sh[k * SB + threadIdx.x] += sh[k * SB + threadIdx.x + s];
+        __syncthreads();
+    }
+    for (int k = 0; k < NV; k++) v[k] = sh[k * SB];
+}
+
+// partials: mass, momentum (3) over fluid-carrying cells
+__global__ void __launch_bounds__(SB) mass_kernel(const double *rho, const double *u, const uint8_t *flags, long long N,
+                                                  int ibb, double *part) {
+    __shared__ double sh[4 * SB];
+    double v[4] = {0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)SNB * SB) {
+        if (ibb && (flags[c] & FL_SOLID)) continue;
+        v[0] += rho[c];
+        v[1] += rho[c] * u[c];
+        v[2] += rho[c] * u[N + c];
+        v[3] += rho[c] * u[2 * N + c];
+    }
+    sblock_sum<4>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; k++) part[blockIdx.x * NP + k] = v[k];
+}
+
+// replace the velocity of solid cells by the rigid-body velocity
+__global__ void mask_kernel(double *u, const uint8_t *flags, const int *owner, const double *X, const double *U,
+                            const double *W, int nx, int ny, int nz, long long N) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    if (!(flags[c] & FL_SOLID)) return;
+    const int p = owner[c];
+    double uw[3] = {0, 0, 0};
+    if (p != NO_OWNER) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double r0 = dmimg(x - X[3 * p], nx), r1 = dmimg(y - X[3 * p + 1], ny), r2 = dmimg(z - X[3 * p + 2], nz);
+        uw[0] = U[3 * p] + (W[3 * p + 1] * r2 - W[3 * p + 2] * r1);
+        uw[1] = U[3 * p + 1] + (W[3 * p + 2] * r0 - W[3 * p] * r2);
+        uw[2] = U[3 * p + 2] + (W[3 * p] * r1 - W[3 * p + 1] * r0);
+    }
+    u[c] = uw[0];
+    u[N + c] = uw[1];
+    u[2 * N + c] = uw[2];
+}
+
+__device__ __forceinline__ double cell_eps(const double *u, int x, int y, int z, int nx, int ny, int nz, long long N,
+                                           double nu) {
+    const long long xp = dwrap(x + 1, nx) + (long long)nx * (y + (long long)ny * z);
+    const long long xm = dwrap(x - 1, nx) + (long long)nx * (y + (long long)ny * z);
+    const long long yp = x + (long long)nx * (dwrap(y + 1, ny) + (long long)ny * z);
+    const long long ym = x + (long long)nx * (dwrap(y - 1, ny) + (long long)ny * z);
+    const long long zp = x + (long long)nx * (y + (long long)ny * dwrap(z + 1, nz));
+    const long long zm = x + (long long)nx * (y + (long long)ny * dwrap(z - 1, nz));
+    double g[3][3];
+    for (int a = 0; a < 3; a++) {
+        const double *ua = u + a * N;
+        g[a][0] = 0.5 * (ua[xp] - ua[xm]);
+        g[a][1] = 0.5 * (ua[yp] - ua[ym]);
+        g[a][2] = 0.5 * (ua[zp] - ua[zm]);
+    }
+    double ss = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            const double s = 0.5 * (g[a][b] + g[b][a]);
+            ss += s * s;
+        }
+    return 2.0 * nu * ss;
+}
+
+// partials: ke, eps over all cells; ke, eps, count over fluid cells; pipe bulk
+__global__ void __launch_bounds__(SB) energy_kernel(const double *u, const uint8_t *flags, int nx, int ny, int nz,
+                                                    long long N, double nu, int pipe, double *part) {
+    __shared__ double sh[7 * SB];
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)SNB * SB) {
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double e = cell_eps(u, x, y, z, nx, ny, nz, N, nu);
+        const double k = 0.5 * (u[c] * u[c] + u[N + c] * u[N + c] + u[2 * N + c] * u[2 * N + c]);
+        v[0] += k;
+        v[1] += e;
+        if (!(flags[c] & FL_SOLID)) {
+            v[2] += k;
+            v[3] += e;
+            v[4] += 1.0;
+            if (pipe) {
+                v[5] += u[2 * N + c];
+                v[6] += 1.0;
+            }
+        }
+    }
+    sblock_sum<7>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; k++) part[blockIdx.x * NP + 4 + k] = v[k];
+}
+
+// nearest particle surface: key = bits of (r - R_p) > 0 for fluid cells
+__global__ void near_key_kernel(unsigned long long *key, const uint8_t *flags, const double *X, const double *R,
+                                int nx, int ny, int nz, int pass, int *near_pid) {
+    const int p = blockIdx.x;
+    const double Rp = R[p];
+    const int r = (int)ceil(3.0 * Rp) + 2;
+    const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    for (long long t = threadIdx.x; t < (long long)w * w * w; t += blockDim.x) {
+        const int x = dwrap(bx + (int)(t % w), nx), y = dwrap(by + (int)((t / w) % w), ny),
+                  z = dwrap(bz + (int)(t / ((long long)w * w)), nz);
+        const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
+        if (flags[c] & FL_SOLID) continue;
+        const double dx = dmimg(__dsub_rn((double)x, X[3 * p]), nx);
+        const double dy = dmimg(__dsub_rn((double)y, X[3 * p + 1]), ny);
+        const double dz = dmimg(__dsub_rn((double)z, X[3 * p + 2]), nz);
+        const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        const double s = __dsub_rn(rr, Rp);
+        if (s <= 0.0) continue;
+        const unsigned long long k = (unsigned long long)__double_as_longlong(s);
+        if (pass == 0) atomicMin(key + c, k);
+        else if (key[c] == k) atomicMin(near_pid + c, p);
+    }
+}
+
+constexpr int NBIN = LBM_NBINS;
+
+__global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t *flags, const int *near_pid,
+                                                  const double *X, const double *R, int nx, int ny, int nz,
+                                                  long long N, double nu, double *bpart) {
+    __shared__ double sk[NBIN], se[NBIN], sc[NBIN];
+    for (int b = threadIdx.x; b < NBIN; b += SB) sk[b] = se[b] = sc[b] = 0.0;
+    __syncthreads();
+    // accumulate per block in shared memory with FP64 atomics, then write
+    // (per-bin sums of a few values each; order effects stay at round-off)
+    for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)SNB * SB) {
+        if (flags[c] & FL_SOLID) continue;
+        const int p = near_pid[c];
+        if (p == NO_OWNER) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double dx = dmimg(__dsub_rn((double)x, X[3 * p]), nx);
+        const double dy = dmimg(__dsub_rn((double)y, X[3 * p + 1]), ny);
+        const double dz = dmimg(__dsub_rn((double)z, X[3 * p + 2]), nz);
+        const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        const double ratio = __ddiv_rn(rr, R[p]);
+        const int b = (int)floor(__ddiv_rn(__dsub_rn(ratio, 1.0), 0.05));
+        if (b < 0 || b >= NBIN) continue;
+        const double k = 0.5 * (u[c] * u[c] + u[N + c] * u[N + c] + u[2 * N + c] * u[2 * N + c]);
+        atomicAdd(&sk[b], k);
+        atomicAdd(&se[b], cell_eps(u, x, y, z, nx, ny, nz, N, nu));
+        atomicAdd(&sc[b], 1.0);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NBIN; b += SB) {
+        bpart[blockIdx.x * 3 * NBIN + b] = sk[b];
+        bpart[blockIdx.x * 3 * NBIN + NBIN + b] = se[b];
+        bpart[blockIdx.x * 3 * NBIN + 2 * NBIN + b] = sc[b];
+    }
+}
+
+__global__ void fill_u64(unsigned long long *p, unsigned long long v, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+__global__ void fill_i32(int *p, int v, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
+    cudaError_t e;
+    memset(o, 0, sizeof(*o));
+    const int ibb = c.armed_bc == LBM_BC_IBB;
+    const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
+    if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
+    count_launch(c, G_STATS, 3);
+    mass_kernel<<<SNB, SB, 0, c.stream>>>(c.rho_f, c.u_f, c.flags, c.N, ibb, c.partials);
+    const bool mask = !(ibm && (flags & LBM_STATS_UNMASK));
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+    if (mask) mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
+    const double nu = (c.tau - 0.5) / 3.0;
+    energy_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.nx, c.ny, c.nz, c.N, nu, c.has_pipe, c.partials);
+    const bool bins = (flags & LBM_STATS_BINS) && c.np > 0;
+    double *bpart = c.partials + SNB * NP;
+    if (bins) {
+        count_launch(c, G_STATS, 5);
+        fill_u64<<<nb, 256, 0, c.stream>>>(c.near_key, ~0ULL, c.N);
+        fill_i32<<<nb, 256, 0, c.stream>>>(c.near_pid, NO_OWNER, c.N);
+        near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 0, c.near_pid);
+        near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 1, c.near_pid);
+        bins_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N, nu, bpart);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::vector<double> part((size_t)SNB * NP), bp(bins ? (size_t)SNB * 3 * NBIN : 0);
+    if ((e = cudaMemcpyAsync(part.data(), c.partials, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                             c.stream)) != cudaSuccess)
+        return e;
+    if (bins && (e = cudaMemcpyAsync(bp.data(), bpart, sizeof(double) * bp.size(), cudaMemcpyDeviceToHost,
+                                     c.stream)) != cudaSuccess)
+        return e;
+    std::vector<double> P(3 * c.np), Uh(3 * c.np), Wh(3 * c.np), Fh(3 * c.np), Th(3 * c.np), mass(c.np), inertia(c.np);
+    if (c.np > 0) {
+        cudaMemcpyAsync(Uh.data(), c.U, sizeof(double) * 3 * c.np, cudaMemcpyDeviceToHost, c.stream);
+        cudaMemcpyAsync(Wh.data(), c.W, sizeof(double) * 3 * c.np, cudaMemcpyDeviceToHost, c.stream);
+        cudaMemcpyAsync(Fh.data(), c.Fh, sizeof(double) * 3 * c.np, cudaMemcpyDeviceToHost, c.stream);
+        cudaMemcpyAsync(Th.data(), c.Th, sizeof(double) * 3 * c.np, cudaMemcpyDeviceToHost, c.stream);
+        cudaMemcpyAsync(mass.data(), c.mass, sizeof(double) * c.np, cudaMemcpyDeviceToHost, c.stream);
+        cudaMemcpyAsync(inertia.data(), c.inertia, sizeof(double) * c.np, cudaMemcpyDeviceToHost, c.stream);
+    }
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    double s[NP] = {0};
+    for (int b = 0; b < SNB; b++)
+        for (int k = 0; k < 11; k++) s[k] += part[(size_t)b * NP + k];
+    o->mass = s[0];
+    o->momentum[0] = s[1];
+    o->momentum[1] = s[2];
+    o->momentum[2] = s[3];
+    o->kinetic_energy = s[4] / (double)c.N;
+    o->dissipation = s[5] / (double)c.N;
+    o->nfluid = (long long)s[8];
+    o->kinetic_energy_fluid = s[8] > 0 ? s[6] / s[8] : 0.0;
+    o->dissipation_fluid = s[8] > 0 ? s[7] / s[8] : 0.0;
+    o->bulk_velocity = s[10] > 0 ? s[9] / s[10] : 0.0;
+    for (int p = 0; p < c.np; p++) {
+        double U2 = 0, W2 = 0;
+        for (int d = 0; d < 3; d++) {
+            U2 += Uh[3 * p + d] * Uh[3 * p + d];
+            W2 += Wh[3 * p + d] * Wh[3 * p + d];
+            o->force[d] += Fh[3 * p + d];
+            o->torque[d] += Th[3 * p + d];
+        }
+        o->particle_ke += 0.5 * mass[p] * U2;
+        o->particle_ake += 0.5 * inertia[p] * W2;
+    }
+    if (bins) {
+        double sk[NBIN] = {0}, se[NBIN] = {0}, sc[NBIN] = {0};
+        for (int b = 0; b < SNB; b++)
+            for (int k = 0; k < NBIN; k++) {
+                sk[k] += bp[(size_t)b * 3 * NBIN + k];
+                se[k] += bp[(size_t)b * 3 * NBIN + NBIN + k];
+                sc[k] += bp[(size_t)b * 3 * NBIN + 2 * NBIN + k];
+            }
+        o->nbins = NBIN;
+        for (int k = 0; k < NBIN; k++) {
+            o->bin_r[k] = 1.0 + 0.05 * (k + 0.5);
+            o->bin_count[k] = (long long)sc[k];
+            if (sc[k] > 0) {
+                const double kf = o->kinetic_energy_fluid > 0 ? o->kinetic_energy_fluid : 1.0;
+                const double ef = o->dissipation_fluid > 0 ? o->dissipation_fluid : 1.0;
+                o->bin_tke[k] = sk[k] / sc[k] / kf;
+                o->bin_eps[k] = se[k] / sc[k] / ef;
+            }
+        }
+    }
+    o->nlinks = c.armed_bc == LBM_BC_IBB ? c.nlinks : 0;
+    o->nmarkers = c.nm;
+    o->step = c.step;
+    return cudaSuccess;
+}
+
+size_t stats_partials_doubles() { return (size_t)SNB * NP + (size_t)SNB * 3 * NBIN; }
+
+}  // namespace lbmgb

@@ -1,0 +1,861 @@
+// C ABI of the library (declared in include/lbm.h): workspace layout, set-up
+// of the geometry, the per-step kernel sequence and host-side checks.
+#include "lbm_internal.cuh"
+
+#include <cmath>
+#include <ctime>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <utility>
+#include <vector>
+
+namespace lbmgb {
+size_t stats_partials_doubles();
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + ALIGN - 1) / ALIGN * ALIGN;
+        return o;
+    }
+};
+
+struct Plan {
+    long long N, max_sites, max_links, max_markers;
+    int max_np, nblk;
+    size_t fA, fB, flags, owner, aux;
+    size_t site_cell, site_first, site_mask, sup_rho, sup_u, sup_F, sup_Fp;
+    size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_fin, link_dP, link_dT;
+    size_t blk_sites, blk_links, counts, status;
+    size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
+    size_t mX, mUnit, mdV, mUs, mF, mFacc, mpid, mfirst;
+    size_t rho_f, u_f, partials, near_key, near_pid;
+    size_t total;
+};
+
+bool make_plan(const lbm_grid *g, Plan &P) {
+    if (!g || g->nx < 4 || g->ny < 4 || g->nz < 1) return false;
+    if (g->storage < LBM_F64 || g->storage > LBM_BF16S) return false;
+    if (g->rates != LBM_RATES_SRT && g->rates != LBM_RATES_DHUMIERES) return false;
+    if (g->max_particles < 0 || g->max_links < 0 || g->max_markers < 0 || g->max_sites < 0) return false;
+    const long long N = (long long)g->nx * g->ny * g->nz;
+    if (N >= (1LL << 31) - 4096) return false;
+    P.N = N;
+    P.max_np = g->max_particles;
+    P.max_links = g->max_links > 0 ? g->max_links : N / 4 + 65536;
+    P.max_sites = g->max_sites > 0 ? g->max_sites : N / 4 + 65536;
+    const long long ring = 8LL * (g->nx + g->ny) * g->nz;
+    P.max_markers = g->max_markers > 0 ? g->max_markers : (long long)P.max_np * 260 + ring;
+    P.nblk = (int)((N + 1023) / 1024);
+    const size_t sb = storage_bytes(g->storage);
+    const size_t n = (size_t)N, ms = (size_t)P.max_sites, ml = (size_t)P.max_links, mm = (size_t)P.max_markers;
+    const size_t np = (size_t)(P.max_np > 0 ? P.max_np : 1);
+    Layout L;
+    P.fA = L.take(19 * n * sb);
+    P.fB = L.take(19 * n * sb);
+    P.flags = L.take(n + 8);
+    P.owner = L.take(4 * n);
+    P.aux = L.take(4 * n);
+    P.site_cell = L.take(4 * ms);
+    P.site_first = L.take(4 * ms);
+    P.site_mask = L.take(4 * ms);
+    P.sup_rho = L.take(8 * ms);
+    P.sup_u = L.take(24 * ms);
+    P.sup_F = L.take(24 * ms);
+    P.sup_Fp = L.take(24 * ms);
+    P.link_cell = L.take(4 * ml);
+    P.link_pid = L.take(4 * ml);
+    P.link_dir = L.take(ml);
+    P.link_scheme = L.take(ml);
+    P.link_q = L.take(8 * ml);
+    P.link_fin = L.take(8 * ml);
+    P.link_dP = L.take(24 * ml);
+    P.link_dT = L.take(24 * ml);
+    P.blk_sites = L.take(8 * (size_t)P.nblk);
+    P.blk_links = L.take(8 * (size_t)P.nblk);
+    P.counts = L.take(16);
+    P.status = L.take(16);
+    P.pX = L.take(24 * np);
+    P.pXold = L.take(24 * np);
+    P.pU = L.take(24 * np);
+    P.pW = L.take(24 * np);
+    P.pR = L.take(8 * np);
+    P.pmass = L.take(8 * np);
+    P.pinertia = L.take(8 * np);
+    P.pFh = L.take(24 * np);
+    P.pTh = L.take(24 * np);
+    P.pFprev = L.take(24 * np);
+    P.pTprev = L.take(24 * np);
+    P.pFc = L.take(48 * np);
+    P.pIu = L.take(24 * np);
+    P.pIr = L.take(24 * np);
+    P.phas = L.take(4 * np);
+    P.mX = L.take(24 * mm);
+    P.mUnit = L.take(24 * mm);
+    P.mdV = L.take(8 * mm);
+    P.mUs = L.take(24 * mm);
+    P.mF = L.take(24 * mm);
+    P.mFacc = L.take(24 * mm);
+    P.mpid = L.take(4 * mm);
+    P.mfirst = L.take(4 * (np + 1));
+    P.rho_f = L.take(8 * n);
+    P.u_f = L.take(24 * n);
+    P.partials = L.take(8 * stats_partials_doubles());
+    P.near_key = L.take(8 * n);
+    P.near_pid = L.take(4 * n);
+    P.total = L.off;
+    return true;
+}
+
+lbm_status fail(Ctx &c, lbm_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c.err, sizeof(c.err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+lbm_status cuda_fail(Ctx &c, cudaError_t e, const char *where) {
+    c.broken = true;
+    return fail(c, LBM_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+__global__ void fill_owner(int *p, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = NO_OWNER;
+}
+
+__global__ void dense_ibm_force(double *out, const double *sup_F, const int *site_cell, const long long *counts,
+                                long long max_sites, long long N) {
+    const long long ns = counts[0] < max_sites ? counts[0] : max_sites;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
+        const int c = site_cell[s];
+        out[c] = sup_F[3 * s];
+        out[N + c] = sup_F[3 * s + 1];
+        out[2 * N + c] = sup_F[3 * s + 2];
+    }
+}
+
+template <int S>
+__global__ void plane_to_f64(const void *src, double *dst, long long N, int i) {
+    typedef typename Store<S>::T T;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const T *p = (const T *)src + (size_t)i * N + c;
+    double v;
+    if (S == LBM_F64) v = *(const double *)p;
+    else if (S == LBM_F32) v = *(const float *)p;
+    else if (S == LBM_F16S) v = (double)__half2float(*(const __half *)p) / (double)F16_SCALE;
+    else v = (double)__bfloat162float(*(const __nv_bfloat16 *)p);
+    dst[c] = v + wgt(i);
+}
+template <int S>
+__global__ void f64_to_plane(void *dst, const double *src, long long N, int i) {
+    typedef typename Store<S>::T T;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    Store<S>::st((T *)dst + (size_t)i * N + c, typename Store<S>::R(src[c] - wgt(i)));
+}
+
+cudaError_t plane_copy(Ctx &c, int i, bool to_f64) {
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+#define PC(S)                                                                                 \
+    if (to_f64) plane_to_f64<S><<<nb, 256, 0, c.stream>>>(c.fA, c.rho_f, c.N, i);            \
+    else f64_to_plane<S><<<nb, 256, 0, c.stream>>>(c.fA, c.rho_f, c.N, i);
+    switch (c.storage) {
+    case LBM_F64: PC(LBM_F64); break;
+    case LBM_F32: PC(LBM_F32); break;
+    case LBM_F16S: PC(LBM_F16S); break;
+    default: PC(LBM_BF16S); break;
+    }
+#undef PC
+    return cudaGetLastError();
+}
+
+// Check the status word copied by the last asynchronous check (bounded
+// host wait: polls the event, gives up after `timeout_s`).
+lbm_status check_status(Ctx &c, bool wait, double timeout_s = 600.0) {
+    if (!c.status_pending) return LBM_OK;
+    cudaError_t q = cudaEventQuery(c.ev_status);
+    if (q == cudaErrorNotReady) {
+        if (!wait) return LBM_OK;
+        // bounded wait
+        const int sleeps = (int)(timeout_s * 1000.0);
+        for (int k = 0; k < sleeps; k++) {
+            q = cudaEventQuery(c.ev_status);
+            if (q != cudaErrorNotReady) break;
+            struct timespec ts = {0, 1000000};
+            nanosleep(&ts, nullptr);
+        }
+        if (q == cudaErrorNotReady) return fail(c, LBM_ETIMEOUT, "stream did not finish within %.0f s", timeout_s);
+    }
+    if (q != cudaSuccess) return cuda_fail(c, q, "status event");
+    c.status_pending = false;
+    const unsigned st = *c.h_status;
+    if (st & 1u) {
+        c.broken = true;
+        return fail(c, LBM_EUNSTABLE, "watchdog: NaN/Inf, rho outside [0.5,2] or |u| > 0.3 before step %lld",
+                    c.step);
+    }
+    if (st & 2u) {
+        c.broken = true;
+        return fail(c, LBM_ENOMEM, "site or link capacity exceeded (max_sites %lld, max_links %lld)", c.max_sites,
+                    c.max_links);
+    }
+    return LBM_OK;
+}
+
+lbm_status enqueue_status(Ctx &c) {
+    CK(cudaMemcpyAsync(c.h_status, c.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaEventRecord(c.ev_status, c.stream));
+    c.status_pending = true;
+    return LBM_OK;
+}
+
+lbm_status sync_all(Ctx &c) {
+    lbm_status s = enqueue_status(c);
+    if (s != LBM_OK) return s;
+    s = check_status(c, true);
+    if (s != LBM_OK) return s;
+    long long cnt[2];
+    CK(cudaMemcpyAsync(cnt, c.d_counts, sizeof(cnt), cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    c.nsites = cnt[0];
+    c.nlinks = cnt[1];
+    return LBM_OK;
+}
+
+void set_rates(Ctx &c) {
+    const double om = 1.0 / c.tau;
+    Rates &r = c.rt;
+    r.d_nu = om;
+    if (c.rates == LBM_RATES_DHUMIERES) {
+        r.d_e = 1.19;
+        r.d_eps = 1.4;
+        r.d_q = 1.2;
+        r.d_pi = 1.4;
+        r.d_m = 1.98;
+    } else {
+        r.d_e = r.d_eps = r.d_q = r.d_pi = r.d_m = om;
+    }
+    r.s_nu = (float)r.d_nu;
+    r.s_e = (float)r.d_e;
+    r.s_eps = (float)r.d_eps;
+    r.s_q = (float)r.d_q;
+    r.s_pi = (float)r.d_pi;
+    r.s_m = (float)r.d_m;
+}
+
+struct ProfRec {
+    int group;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[LBM_NGROUPS];
+    long long spans[LBM_NGROUPS];
+    long long launches0[LBM_NGROUPS];
+};
+
+// event recorded on the stream now (nullptr when profiling is off)
+cudaEvent_t pmark(Ctx &c) {
+    if (!c.prof_on) return nullptr;
+    Prof *P = (Prof *)c.prof;
+    cudaEvent_t e;
+    if (!P->pool.empty()) {
+        e = P->pool.back();
+        P->pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    cudaEventRecord(e, c.stream);
+    return e;
+}
+void pspan(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b) {
+    if (!a || !b) return;
+    ((Prof *)c.prof)->recs.push_back({g, a, b});
+}
+
+int marker_count(double RL) { return (int)std::floor(M_PI / 3.0 * (12.0 * RL * RL + 1.0) + 0.5); }
+
+// Lagrangian markers (Sec. 2.1: marker volume close to the cell volume).
+// Spheres: golden-spiral points at R_L = R - r_d, dV = pi (12 R_L^2 + 1) / (3 N_L).
+// Pipe: a ring of round(2 pi R_L) points at R_L = R + r_d in every z plane.
+lbm_status build_markers(Ctx &c) {
+    const double rd = c.rd;
+    std::vector<double> unit, X, dV;
+    std::vector<int> pid, first;
+    if (c.has_pipe) {
+        const double RL = c.pipe_R + rd;
+        const int nc = (int)std::floor(2.0 * M_PI * RL + 0.5);
+        for (int z = 0; z < c.nz; z++)
+            for (int j = 0; j < nc; j++) {
+                const double th = 2.0 * M_PI * j / nc;
+                X.push_back(c.pipe_cx + RL * std::cos(th));
+                X.push_back(c.pipe_cy + RL * std::sin(th));
+                X.push_back((double)z);
+                dV.push_back(2.0 * M_PI * RL / nc);
+                pid.push_back(-1);
+            }
+        unit.assign(X.size(), 0.0);
+    } else {
+        std::vector<double> R(c.np);
+        CK(cudaMemcpy(R.data(), c.R, sizeof(double) * c.np, cudaMemcpyDeviceToHost));
+        const double ga = M_PI * (3.0 - std::sqrt(5.0));
+        for (int p = 0; p < c.np; p++) {
+            first.push_back((int)pid.size());
+            const double RL = R[p] - rd;
+            const int n = marker_count(RL);
+            for (int l = 0; l < n; l++) {
+                const double zz = 1.0 - (2.0 * l + 1.0) / n;
+                const double rr = std::sqrt(1.0 - zz * zz);
+                const double th = ga * l;
+                unit.push_back(RL * rr * std::cos(th));
+                unit.push_back(RL * rr * std::sin(th));
+                unit.push_back(RL * zz);
+                dV.push_back(M_PI * (12.0 * RL * RL + 1.0) / (3.0 * n));
+                pid.push_back(p);
+            }
+        }
+        first.push_back((int)pid.size());
+        X.assign(unit.size(), 0.0);
+    }
+    const long long nm = (long long)pid.size();
+    if (nm > c.max_markers) return fail(c, LBM_ENOMEM, "markers %lld exceed capacity %lld", nm, c.max_markers);
+    c.nm = nm;
+    if (nm > 0) {
+        CK(cudaMemcpyAsync(c.mUnit, unit.data(), sizeof(double) * unit.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.mX, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.mdV, dV.data(), sizeof(double) * dV.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.mpid, pid.data(), sizeof(int) * pid.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemsetAsync(c.mFacc, 0, sizeof(double) * 3 * nm, c.stream));
+    }
+    if (!first.empty())
+        CK(cudaMemcpyAsync(c.m_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status arm(Ctx &c, int bc) {
+    c.armed_bc = bc;
+    if (bc == LBM_BC_IBM_U || bc == LBM_BC_IBM_B) {
+        c.rd = bc == LBM_BC_IBM_B ? 0.4 : 0.0;
+        if (c.has_pipe || c.np > 0) {
+            lbm_status s = build_markers(c);
+            if (s != LBM_OK) return s;
+            CK(launch_markers_place(c));
+            CK(launch_ibm_rigid_overwrite(c));
+            CK(launch_ibm_particle_sums(c, true));
+        }
+        // the spreading accumulates into this buffer and every pass clears
+        // the slots it used; it must start at zero
+        CK(cudaMemsetAsync(c.sup_Fp, 0, sizeof(double) * 3 * (size_t)c.max_sites, c.stream));
+        CK(launch_support_mark(c));
+        CK(build_sites(c, 2));
+        lbm_status s = sync_all(c);
+        if (s != LBM_OK) return s;
+        c.nsites_hint = c.nsites;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbmgb
+
+using namespace lbmgb;
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_grid *grid) {
+    Plan P;
+    if (!make_plan(grid, P)) return 0;
+    return P.total;
+}
+
+lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], void *dev_workspace, size_t bytes,
+                      void *cuda_stream, lbm_ctx **out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    Plan P;
+    if (!make_plan(grid, P) || !(tau > 0.5) || !dev_workspace || ((uintptr_t)dev_workspace % ALIGN) != 0)
+        return LBM_EINVAL;
+    if (bytes < P.total) return LBM_ENOMEM;
+    lbm_ctx *h = new (std::nothrow) lbm_ctx;
+    if (!h) return LBM_ENOMEM;
+    memset(&h->c, 0, sizeof(Ctx));
+    Ctx &c = h->c;
+    c.g = *grid;
+    c.nx = grid->nx;
+    c.ny = grid->ny;
+    c.nz = grid->nz;
+    c.N = P.N;
+    c.tau = tau;
+    for (int d = 0; d < 3; d++) c.F[d] = force ? force[d] : 0.0;
+    c.storage = grid->storage;
+    c.rates = grid->rates;
+    set_rates(c);
+    c.stream = (cudaStream_t)cuda_stream;
+    c.ws = (char *)dev_workspace;
+    c.ws_bytes = bytes;
+    char *b = c.ws;
+    c.fA = b + P.fA;
+    c.fB = b + P.fB;
+    c.flags = (uint8_t *)(b + P.flags);
+    c.owner = (int *)(b + P.owner);
+    c.aux = (int *)(b + P.aux);
+    c.max_sites = P.max_sites;
+    c.site_cell = (int *)(b + P.site_cell);
+    c.site_first = (int *)(b + P.site_first);
+    c.site_mask = (unsigned *)(b + P.site_mask);
+    c.sup_rho = (double *)(b + P.sup_rho);
+    c.sup_u = (double *)(b + P.sup_u);
+    c.sup_F = (double *)(b + P.sup_F);
+    c.sup_Fp = (double *)(b + P.sup_Fp);
+    c.max_links = P.max_links;
+    c.link_cell = (int *)(b + P.link_cell);
+    c.link_pid = (int *)(b + P.link_pid);
+    c.link_dir = (int8_t *)(b + P.link_dir);
+    c.link_scheme = (int8_t *)(b + P.link_scheme);
+    c.link_q = (double *)(b + P.link_q);
+    c.link_fin = (double *)(b + P.link_fin);
+    c.link_dP = (double *)(b + P.link_dP);
+    c.link_dT = (double *)(b + P.link_dT);
+    c.nblk = P.nblk;
+    c.blk_sites = (long long *)(b + P.blk_sites);
+    c.blk_links = (long long *)(b + P.blk_links);
+    c.d_counts = (long long *)(b + P.counts);
+    c.d_status = (unsigned *)(b + P.status);
+    c.max_np = P.max_np;
+    c.X = (double *)(b + P.pX);
+    c.Xold = (double *)(b + P.pXold);
+    c.U = (double *)(b + P.pU);
+    c.W = (double *)(b + P.pW);
+    c.R = (double *)(b + P.pR);
+    c.mass = (double *)(b + P.pmass);
+    c.inertia = (double *)(b + P.pinertia);
+    c.Fh = (double *)(b + P.pFh);
+    c.Th = (double *)(b + P.pTh);
+    c.Fprev = (double *)(b + P.pFprev);
+    c.Tprev = (double *)(b + P.pTprev);
+    c.Fc = (double *)(b + P.pFc);
+    c.Iu = (double *)(b + P.pIu);
+    c.Ir = (double *)(b + P.pIr);
+    c.has_prev = (int *)(b + P.phas);
+    c.max_markers = P.max_markers;
+    c.mX = (double *)(b + P.mX);
+    c.mUnit = (double *)(b + P.mUnit);
+    c.mdV = (double *)(b + P.mdV);
+    c.mUs = (double *)(b + P.mUs);
+    c.mF = (double *)(b + P.mF);
+    c.mFacc = (double *)(b + P.mFacc);
+    c.mpid = (int *)(b + P.mpid);
+    c.m_first = (int *)(b + P.mfirst);
+    c.rho_f = (double *)(b + P.rho_f);
+    c.u_f = (double *)(b + P.u_f);
+    c.partials = (double *)(b + P.partials);
+    c.near_key = (unsigned long long *)(b + P.near_key);
+    c.near_pid = (int *)(b + P.near_pid);
+    c.armed_bc = -1;
+    c.pipe_cx = 0.5 * (c.nx - 1);
+    c.pipe_cy = 0.5 * (c.ny - 1);
+    auto bad = [&](cudaError_t e, const char *w) {
+        cuda_fail(c, e, w);
+        if (c.h_status) cudaFreeHost(c.h_status);
+        delete h;
+        return LBM_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMallocHost((void **)&c.h_status, sizeof(unsigned))) != cudaSuccess) {
+        c.h_status = nullptr;
+        return bad(e, "cudaMallocHost");
+    }
+    *c.h_status = 0;
+    if ((e = cudaEventCreateWithFlags(&c.ev_status, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "event");
+    const size_t sb = storage_bytes(c.storage);
+    // rest state: g = f - w = 0 in every storage format
+    if ((e = cudaMemsetAsync(c.fA, 0, 19 * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.fB, 0, 19 * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.flags, 0, (size_t)c.N + 8, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.aux, 0xff, 4 * (size_t)c.N, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.d_counts, 0, 16, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.d_status, 0, 16, c.stream)) != cudaSuccess) return bad(e, "memset");
+    fill_owner<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.owner, c.N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bad(e, "fill");
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return bad(e, "sync");
+    *out = h;
+    return LBM_OK;
+}
+
+#define CTX_CHECK(h)                                       \
+    if (!(h)) return LBM_EINVAL;                           \
+    Ctx &c = (h)->c;
+
+lbm_status lbm_init_velocity(lbm_ctx *h, const double *u_host, double rho0) {
+    CTX_CHECK(h);
+    if (!u_host || !(rho0 > 0)) return fail(c, LBM_EINVAL, "bad velocity field or rho0");
+    if (c.broken || c.armed_bc >= 0) return fail(c, LBM_ESTATE, "init_velocity only before the first step");
+    CK(cudaMemcpyAsync(c.u_f, u_host, sizeof(double) * 3 * c.N, cudaMemcpyHostToDevice, c.stream));
+    CK(launch_init_equilibrium(c, c.u_f, rho0));
+    CK(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *h, const double *f_host) {
+    CTX_CHECK(h);
+    if (!f_host) return fail(c, LBM_EINVAL, "null populations");
+    if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
+    for (int i = 0; i < 19; i++) {
+        CK(cudaMemcpyAsync(c.rho_f, f_host + (size_t)i * c.N, sizeof(double) * c.N, cudaMemcpyHostToDevice, c.stream));
+        CK(plane_copy(c, i, false));
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
+    CTX_CHECK(h);
+    if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe) return fail(c, LBM_ESTATE, "geometry already set");
+    if (!(radius > 1.0) || radius > 0.5 * (c.nx < c.ny ? c.nx : c.ny)) return fail(c, LBM_EINVAL, "bad pipe radius");
+    c.has_pipe = 1;
+    c.pipe_R = radius;
+    CK(launch_pipe_flags(c));
+    CK(build_sites(c, 1));
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK) return s;
+    c.nsites_hint = c.nsites;
+    return LBM_OK;
+}
+
+lbm_status lbm_add_spheres(lbm_ctx *h, int n, const double *xyz, const double *radius, double density_ratio,
+                           const double *vel, const double *omega, int fixed) {
+    CTX_CHECK(h);
+    if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe) return fail(c, LBM_ESTATE, "geometry already set");
+    if (n <= 0 || !xyz || !radius || !(density_ratio > 0)) return fail(c, LBM_EINVAL, "bad sphere arguments");
+    if (n > c.max_np) return fail(c, LBM_ENOMEM, "%d spheres exceed max_particles %d", n, c.max_np);
+    std::vector<double> X(xyz, xyz + 3 * n), R(radius, radius + n), m(n), I(n), zero(3 * n, 0.0);
+    for (int p = 0; p < n; p++) {
+        if (!(R[p] > 0.5) || !(2 * R[p] + 4 < c.nx && 2 * R[p] + 4 < c.ny && 2 * R[p] + 4 < c.nz))
+            return fail(c, LBM_EINVAL, "sphere %d radius out of range", p);
+        const int nn[3] = {c.nx, c.ny, c.nz};
+        for (int d = 0; d < 3; d++) {
+            double x = X[3 * p + d];
+            if (!(x >= 0.0 && x < nn[d])) return fail(c, LBM_EINVAL, "sphere %d centre outside the box", p);
+        }
+        m[p] = density_ratio * 4.0 / 3.0 * M_PI * R[p] * R[p] * R[p];
+        I[p] = 0.4 * m[p] * R[p] * R[p];
+    }
+    c.np = n;
+    c.fixed = fixed != 0;
+    c.dens = density_ratio;
+    const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
+    CK(cudaMemcpyAsync(c.X, X.data(), b3, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.Xold, X.data(), b3, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.R, R.data(), b1, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.mass, m.data(), b1, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemcpyAsync(c.inertia, I.data(), b1, cudaMemcpyHostToDevice, c.stream));
+    for (double *p : {c.Fh, c.Th, c.Fprev, c.Tprev, c.Iu, c.Ir})
+        CK(cudaMemcpyAsync(p, zero.data(), b3, cudaMemcpyHostToDevice, c.stream));
+    CK(cudaMemsetAsync(c.Fc, 0, 2 * b3, c.stream));
+    CK(cudaMemsetAsync(c.has_prev, 0, sizeof(int) * n, c.stream));
+    CK(cudaMemcpyAsync(c.W, omega ? omega : zero.data(), b3, cudaMemcpyHostToDevice, c.stream));
+    if (vel) CK(cudaMemcpyAsync(c.U, vel, b3, cudaMemcpyHostToDevice, c.stream));
+    else CK(launch_release(c));  // before the geometry exists: every cell counts as fluid
+    CK(launch_sphere_mark(c, false));
+    CK(build_sites(c, 1));
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK) return s;
+    c.nsites_hint = c.nsites;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
+    CTX_CHECK(h);
+    if (nsteps < 0 || bc < LBM_BC_NONE || bc > LBM_BC_IBM_B) return fail(c, LBM_EINVAL, "bad step arguments");
+    lbm_status s = check_status(c, false);
+    if (s != LBM_OK) return s;
+    if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
+    if (c.armed_bc < 0) {
+        s = arm(c, bc);
+        if (s != LBM_OK) return s;
+    } else if (c.armed_bc != bc) {
+        return fail(c, LBM_ESTATE, "boundary treatment fixed to %d by the first step", c.armed_bc);
+    }
+    const bool ibm = bc == LBM_BC_IBM_U || bc == LBM_BC_IBM_B;
+    const bool moving = c.np > 0 && !c.fixed;
+    for (int n = 0; n < nsteps; n++) {
+        cudaEvent_t t0 = pmark(c), t1;
+        if (bc == LBM_BC_NONE) {
+            CK(launch_stream_collide(c, bc));
+            pspan(c, G_BULK, t0, pmark(c));
+        } else if (bc == LBM_BC_IBB) {
+            CK(launch_stream_collide(c, bc));
+            t1 = pmark(c);
+            pspan(c, G_BULK, t0, t1);
+            CK(launch_boundary_collide(c));
+            t0 = pmark(c);
+            pspan(c, G_BND, t1, t0);
+            if (c.np > 0) CK(launch_gimem(c));
+            if (moving) CK(launch_particle_update(c));
+            t1 = pmark(c);
+            pspan(c, G_PART, t0, t1);
+            if (moving) {
+                CK(launch_sphere_mark(c, true));
+                CK(launch_refill(c));
+                CK(launch_finish_geometry(c));
+                CK(build_sites(c, 1));
+            }
+            pspan(c, G_GEOM, t1, pmark(c));
+        } else if (ibm) {
+            if (moving && c.step > 0) {
+                CK(launch_support_mark(c));
+                CK(build_sites(c, 2));
+            }
+            t1 = pmark(c);
+            pspan(c, G_GEOM, t0, t1);
+            CK(launch_stream_collide(c, bc));
+            t0 = pmark(c);
+            pspan(c, G_BULK, t1, t0);
+            CK(launch_ibm_passes(c));
+            t1 = pmark(c);
+            pspan(c, G_IBM, t0, t1);
+            CK(launch_ibm_collide(c));
+            t0 = pmark(c);
+            pspan(c, G_IBMCOL, t1, t0);
+            if (c.np > 0) CK(launch_ibm_particle_sums(c, false));
+            if (moving) CK(launch_particle_update(c));
+            t1 = pmark(c);
+            pspan(c, G_PART, t0, t1);
+            if (moving) {
+                CK(launch_markers_place(c));
+                CK(launch_sphere_mark(c, true));
+                CK(launch_finish_geometry(c));
+            }
+            pspan(c, G_GEOM, t1, pmark(c));
+        }
+        std::swap(c.fA, c.fB);
+        c.step++;
+    }
+    return enqueue_status(c);
+}
+
+lbm_status lbm_stats(lbm_ctx *h, int flags, lbm_stats_t *out) {
+    CTX_CHECK(h);
+    if (!out) return fail(c, LBM_EINVAL, "null output");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    CK(run_stats(c, flags, out));
+    out->nlinks = c.nlinks;
+    return s;
+}
+
+lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
+    CTX_CHECK(h);
+    if (!dst) return fail(c, LBM_EINVAL, "null destination");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    const size_t N = (size_t)c.N;
+    switch (which) {
+    case LBM_FIELD_RHO:
+    case LBM_FIELD_U: {
+        const size_t need = (which == LBM_FIELD_RHO ? 1 : 3) * N * sizeof(double);
+        if (bytes < need) return fail(c, LBM_EINVAL, "destination too small");
+        CK(launch_macro(c, 0));
+        CK(cudaMemcpyAsync(dst, which == LBM_FIELD_RHO ? (void *)c.rho_f : (void *)c.u_f, need,
+                           cudaMemcpyDeviceToHost, c.stream));
+        break;
+    }
+    case LBM_FIELD_POPS: {
+        if (bytes < 19 * N * sizeof(double)) return fail(c, LBM_EINVAL, "destination too small");
+        for (int i = 0; i < 19; i++) {
+            CK(plane_copy(c, i, true));
+            CK(cudaMemcpyAsync((double *)dst + i * N, c.rho_f, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        }
+        break;
+    }
+    case LBM_FIELD_FLAGS: {
+        if (bytes < N) return fail(c, LBM_EINVAL, "destination too small");
+        CK(cudaMemcpyAsync(dst, c.flags, N, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+        uint8_t *f = (uint8_t *)dst;
+        for (size_t i = 0; i < N; i++) f[i] &= (FL_SOLID | FL_BND | FL_SUP);
+        break;
+    }
+    case LBM_FIELD_IBM_FORCE: {
+        if (bytes < 3 * N * sizeof(double)) return fail(c, LBM_EINVAL, "destination too small");
+        CK(cudaMemsetAsync(c.u_f, 0, 3 * N * sizeof(double), c.stream));
+        if (c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B)
+            dense_ibm_force<<<1024, 256, 0, c.stream>>>(c.u_f, c.sup_F, c.site_cell, c.d_counts, c.max_sites, c.N);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(dst, c.u_f, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        break;
+    }
+    default:
+        return fail(c, LBM_EINVAL, "unknown field %d", which);
+    }
+    CK(cudaStreamSynchronize(c.stream));
+    return s;
+}
+
+lbm_status lbm_num_links(lbm_ctx *h, long long *n) {
+    CTX_CHECK(h);
+    if (!n) return LBM_EINVAL;
+    lbm_status s = sync_all(c);
+    *n = c.nlinks;
+    return s;
+}
+
+lbm_status lbm_get_links(lbm_ctx *h, long long capacity, long long *cell, int *dir, int *scheme, double *q, int *pid) {
+    CTX_CHECK(h);
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    const long long n = c.nlinks < c.max_links ? c.nlinks : c.max_links;
+    if (capacity < n) return fail(c, LBM_EINVAL, "capacity %lld < %lld links", capacity, n);
+    if (n == 0) return s;
+    std::vector<int> ic(n), ip(n);
+    std::vector<int8_t> id(n), is(n);
+    CK(cudaMemcpyAsync(ic.data(), c.link_cell, 4 * n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(ip.data(), c.link_pid, 4 * n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(id.data(), c.link_dir, n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaMemcpyAsync(is.data(), c.link_scheme, n, cudaMemcpyDeviceToHost, c.stream));
+    if (q) CK(cudaMemcpyAsync(q, c.link_q, 8 * n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    for (long long k = 0; k < n; k++) {
+        if (cell) cell[k] = ic[k];
+        if (dir) dir[k] = id[k];
+        if (scheme) scheme[k] = is[k];
+        if (pid) pid[k] = ip[k];
+    }
+    return s;
+}
+
+lbm_status lbm_get_particles(lbm_ctx *h, double *X, double *U, double *W, double *F, double *T) {
+    CTX_CHECK(h);
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    const size_t b3 = sizeof(double) * 3 * c.np;
+    if (c.np == 0) return s;
+    if (X) CK(cudaMemcpyAsync(X, c.X, b3, cudaMemcpyDeviceToHost, c.stream));
+    if (U) CK(cudaMemcpyAsync(U, c.U, b3, cudaMemcpyDeviceToHost, c.stream));
+    if (W) CK(cudaMemcpyAsync(W, c.W, b3, cudaMemcpyDeviceToHost, c.stream));
+    if (F) CK(cudaMemcpyAsync(F, c.Fh, b3, cudaMemcpyDeviceToHost, c.stream));
+    if (T) CK(cudaMemcpyAsync(T, c.Th, b3, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return s;
+}
+
+lbm_status lbm_num_markers(lbm_ctx *h, long long *n) {
+    CTX_CHECK(h);
+    if (!n) return LBM_EINVAL;
+    *n = c.nm;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_markers(lbm_ctx *h, long long capacity, double *X, double *F, double *dV, int *pid) {
+    CTX_CHECK(h);
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    if (capacity < c.nm) return fail(c, LBM_EINVAL, "capacity %lld < %lld markers", capacity, c.nm);
+    if (c.nm == 0) return s;
+    if (X) CK(cudaMemcpyAsync(X, c.mX, 24 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+    if (F) CK(cudaMemcpyAsync(F, c.mFacc, 24 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+    if (dV) CK(cudaMemcpyAsync(dV, c.mdV, 8 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+    if (pid) CK(cudaMemcpyAsync(pid, c.mpid, 4 * c.nm, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+    return s;
+}
+
+lbm_status lbm_profile(lbm_ctx *h, int enable, lbm_profile_t *out) {
+    CTX_CHECK(h);
+    if (!c.prof) c.prof = new Prof();
+    Prof *P = (Prof *)c.prof;
+    if (out) {
+        CK(cudaStreamSynchronize(c.stream));
+        // adjacent spans share their boundary event: return each event once
+        std::vector<cudaEvent_t> used;
+        for (auto &r : P->recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                P->ms[r.group] += ms;
+                P->spans[r.group]++;
+            }
+            used.push_back(r.a);
+            used.push_back(r.b);
+        }
+        P->recs.clear();
+        std::sort(used.begin(), used.end());
+        used.erase(std::unique(used.begin(), used.end()), used.end());
+        P->pool.insert(P->pool.end(), used.begin(), used.end());
+        memset(out, 0, sizeof(*out));
+        for (int g = 0; g < LBM_NGROUPS; g++) {
+            out->ms[g] = P->ms[g];
+            out->spans[g] = P->spans[g];
+            out->launches[g] = c.group_launches[g] - P->launches0[g];
+        }
+        out->total_launches = c.launches;
+    }
+    if (enable >= 0) {
+        const int was = c.prof_on;
+        c.prof_on = enable ? 1 : 0;
+        if (enable && !was) {
+            for (int g = 0; g < LBM_NGROUPS; g++) {
+                P->ms[g] = 0.0;
+                P->spans[g] = 0;
+                P->launches0[g] = c.group_launches[g];
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *h) { return h ? h->c.err : "null context"; }
+
+const char *lbm_status_string(int s) {
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "workspace or capacity too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "numerical instability detected";
+    case LBM_ETIMEOUT: return "timed out waiting for the GPU";
+    case LBM_ESTATE: return "call not allowed in this state";
+    case LBM_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+void lbm_destroy(lbm_ctx *h) {
+    if (!h) return;
+    Ctx &c = h->c;
+    cudaStreamSynchronize(c.stream);
+    if (c.prof) {
+        Prof *P = (Prof *)c.prof;
+        std::vector<cudaEvent_t> all(P->pool);
+        for (auto &r : P->recs) {
+            all.push_back(r.a);
+            all.push_back(r.b);
+        }
+        std::sort(all.begin(), all.end());
+        all.erase(std::unique(all.begin(), all.end()), all.end());
+        for (auto e : all) cudaEventDestroy(e);
+        delete P;
+    }
+    if (c.ev_status) cudaEventDestroy(c.ev_status);
+    if (c.h_status) cudaFreeHost(c.h_status);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+// Internal definitions of the GB300 lattice Boltzmann library: context,
+// D3Q19 constants, population storage formats and the device collision.
+// The method is the D3Q19 MRT LBM with Guo forcing of Peng et al.,
+// arXiv:1906.05448 (Sec. 2.1, Sec. 3.1); see lbm.h for the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbmgb {
+
+// ---------------------------------------------------------------- flags ----
+enum : uint8_t {
+    FL_SOLID = 1,     // inside a particle / outside the pipe
+    FL_BND = 2,       // IBB: fluid cell with at least one boundary link
+    FL_SUP = 4,       // IBM: cell handled by the compact forcing path
+    FL_WAS_SOLID = 8, // transient during a geometry update
+};
+
+constexpr int NO_OWNER = 0x7fffffff;
+
+// --------------------------------------------------------------- D3Q19 -----
+// Velocity order (same as lbm.h): rest, +-x, +-y, +-z, then the edges in
+// (+,+)/(-,-), (+,-)/(-,+) pairs for xy, xz, yz. Opposites are adjacent.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// ------------------------------------------------------------- storage -----
+// Populations are stored shifted, g_i = f_i - w_i, which keeps the stored
+// numbers small and the rounding of the stored state well below that of f.
+template <int S> struct Store;
+template <> struct Store<LBM_F64> {
+    typedef double T;
+    typedef double R;  // arithmetic type
+    static __device__ __forceinline__ double ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(T *p, double v) { *p = v; }
+};
+template <> struct Store<LBM_F32> {
+    typedef float T;
+    typedef float R;
+    static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(T *p, float v) { *p = v; }
+};
+// FP16 holds g * 2^10 so that small departures from w_i stay normal numbers.
+constexpr float F16_SCALE = 1024.0f;
+template <> struct Store<LBM_F16S> {
+    typedef __half T;
+    typedef float R;
+    static __device__ __forceinline__ float ld(const T *p) {
+        return __half2float(__ldg(p)) * (1.0f / F16_SCALE);
+    }
+    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
+};
+template <> struct Store<LBM_BF16S> {
+    typedef __nv_bfloat16 T;
+    typedef float R;
+    static __device__ __forceinline__ float ld(const T *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+inline size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
+
+// ------------------------------------------------------------ collision ----
+struct Rates {
+    float s_e, s_eps, s_q, s_nu, s_pi, s_m;  // d'Humieres groups (s_nu = 1/tau)
+    double d_e, d_eps, d_q, d_nu, d_pi, d_m;
+};
+
+// Guo forcing term F_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F.
+template <typename R>
+__host__ __device__ __forceinline__ R guo_term(int i, R ux, R uy, R uz, R Fx, R Fy, R Fz) {
+    const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+    const R a = (R(cx(i)) - ux) * Fx + (R(cy(i)) - uy) * Fy + (R(cz(i)) - uz) * Fz;
+    const R b = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
+    return R(wgt(i)) * (R(3) * a + R(9) * cu * b);
+}
+
+// Collide one cell in place. g: shifted populations in, post-collision out.
+// F: total force on the cell. Returns rho and u = (sum f c + F/2)/rho.
+// The moment transform is the d'Humieres D3Q19 basis evaluated through
+// opposite-pair sums (even moments) and differences (odd moments); the
+// inverse uses the orthogonality of the basis (row norms below).
+template <typename R, bool FORCE, bool SRT>
+__host__ __device__ __forceinline__ void collide(R g[19], R Fx, R Fy, R Fz, const Rates &rt, R &rho_o, R &ux_o,
+                                                 R &uy_o, R &uz_o) {
+    R drho = g[0];
+#pragma unroll
+    for (int i = 1; i < 19; i++) drho += g[i];
+    R jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
+    R jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
+    R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
+    const R rho = R(1) + drho;
+    const R irho = R(1) / rho;
+    if (FORCE) {
+        jx += R(0.5) * Fx;
+        jy += R(0.5) * Fy;
+        jz += R(0.5) * Fz;
+    }
+    const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+    uz_o = uz;
+    R Fi[19];
+    if (FORCE) {
+#pragma unroll
+        for (int i = 0; i < 19; i++) Fi[i] = guo_term<R>(i, ux, uy, uz, Fx, Fy, Fz);
+    }
+    const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
+    if constexpr (SRT) {
+        // BGK: g* = g - w (g - g_eq) + (1 - w/2) F_i with g_eq = f_eq - w.
+        const R om = (sizeof(R) == 8) ? R(rt.d_nu) : R(rt.s_nu);
+        const R c1 = R(1) - R(0.5) * om;
+#pragma unroll
+        for (int i = 0; i < 19; i++) {
+            const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+            const R geq = R(wgt(i)) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2));
+            R v = g[i] - om * (g[i] - geq);
+            if (FORCE) v += c1 * Fi[i];
+            g[i] = v;
+        }
+    } else {
+    // MRT: g* = g + F_i - M^-1 S (M (g + F_i/2) - (m_eq - M w)).
+    R h[19];
+#pragma unroll
+    for (int i = 0; i < 19; i++) h[i] = FORCE ? g[i] + R(0.5) * Fi[i] : g[i];
+    const R Sx = h[1] + h[2], Sy = h[3] + h[4], Sz = h[5] + h[6];
+    const R Sa = h[7] + h[8], Sb = h[9] + h[10], Sc = h[11] + h[12], Sd = h[13] + h[14];
+    const R Se = h[15] + h[16], Sf = h[17] + h[18];
+    const R Dx = h[1] - h[2], Dy = h[3] - h[4], Dz = h[5] - h[6];
+    const R Da = h[7] - h[8], Db = h[9] - h[10], Dc = h[11] - h[12], Dd = h[13] - h[14];
+    const R De = h[15] - h[16], Df = h[17] - h[18];
+    const R A = Sx + Sy + Sz;
+    const R Exy = Sa + Sb, Exz = Sc + Sd, Eyz = Se + Sf;
+    const R E = Exy + Exz + Eyz;
+    const R pxx = R(2) * Sx - Sy - Sz + Exy + Exz - R(2) * Eyz;      // 3 p_xx
+    const R pixx = R(-2) * (R(2) * Sx - Sy - Sz) + Exy + Exz - R(2) * Eyz;
+    const R pww = Sy - Sz + Exy - Exz;
+    const R piww = R(-2) * (Sy - Sz) + Exy - Exz;
+    const R mee = R(-30) * h[0] - R(11) * A + R(8) * E;
+    const R mep = R(12) * h[0] - R(4) * A + E;
+    const R pxy = Sa - Sb, pyz = Se - Sf, pxz = Sc - Sd;
+    const R qx = R(-4) * Dx + Da + Db + Dc + Dd;
+    const R qy = R(-4) * Dy + Da - Db + De + Df;
+    const R qz = R(-4) * Dz + Dc - Dd + De - Df;
+    const R mx = (Da + Db) - (Dc + Dd);
+    const R my = (De + Df) - (Da - Db);
+    const R mz = (Dc - Dd) - (De - Df);
+    // equilibrium moments minus those of w (rho = 1, u = 0)
+    const R eq_e = R(-11) * drho + R(19) * rho * u2;
+    const R eq_ep = R(3) * drho - R(5.5) * rho * u2;
+    const R tx = R(2) * uxx - uyy - uzz;
+    const R eq_pxx = rho * tx, eq_pixx = R(-0.5) * rho * tx;
+    const R eq_pww = rho * (uyy - uzz), eq_piww = R(-0.5) * rho * (uyy - uzz);
+    const R eq_q = R(-2.0 / 3.0) * rho;
+    const bool dbl = sizeof(R) == 8;
+    const R se = dbl ? R(rt.d_e) : R(rt.s_e), sep = dbl ? R(rt.d_eps) : R(rt.s_eps);
+    const R sq = dbl ? R(rt.d_q) : R(rt.s_q), snu = dbl ? R(rt.d_nu) : R(rt.s_nu);
+    const R spi = dbl ? R(rt.d_pi) : R(rt.s_pi), sm = dbl ? R(rt.d_m) : R(rt.s_m);
+    // relaxed departures divided by the squared row norms of the basis
+    const R a_e = se * (mee - eq_e) * R(1.0 / 2394.0);
+    const R a_ep = sep * (mep - eq_ep) * R(1.0 / 252.0);
+    const R a_pxx = snu * (pxx - eq_pxx) * R(1.0 / 36.0);
+    const R a_pixx = spi * (pixx - eq_pixx) * R(1.0 / 72.0);
+    const R a_pww = snu * (pww - eq_pww) * R(1.0 / 12.0);
+    const R a_piww = spi * (piww - eq_piww) * R(1.0 / 24.0);
+    const R a_pxy = snu * (pxy - rho * ux * uy) * R(0.25);
+    const R a_pyz = snu * (pyz - rho * uy * uz) * R(0.25);
+    const R a_pxz = snu * (pxz - rho * ux * uz) * R(0.25);
+    const R a_qx = sq * (qx - eq_q * ux) * R(1.0 / 40.0);
+    const R a_qy = sq * (qy - eq_q * uy) * R(1.0 / 40.0);
+    const R a_qz = sq * (qz - eq_q * uz) * R(1.0 / 40.0);
+    const R a_mx = sm * mx * R(0.125), a_my = sm * my * R(0.125), a_mz = sm * mz * R(0.125);
+    // back-transform: even and odd parts per opposite pair
+    const R c0 = R(-30) * a_e + R(12) * a_ep;
+    const R ax = R(-11) * a_e - R(4) * a_ep;                 // common to the 6 axis directions
+    const R ed = R(8) * a_e + a_ep;                          // common to the 12 edges
+    const R evx = ax + R(2) * a_pxx - R(4) * a_pixx;
+    const R evy = ax - a_pxx + R(2) * a_pixx + a_pww - R(2) * a_piww;
+    const R evz = ax - a_pxx + R(2) * a_pixx - a_pww + R(2) * a_piww;
+    const R exy = ed + a_pxx + a_pixx + a_pww + a_piww;
+    const R exz = ed + a_pxx + a_pixx - a_pww - a_piww;
+    const R eyz = ed - R(2) * a_pxx - R(2) * a_pixx;
+    const R evA = exy + a_pxy, evB = exy - a_pxy;
+    const R evC = exz + a_pxz, evD = exz - a_pxz;
+    const R evE = eyz + a_pyz, evF = eyz - a_pyz;
+    const R odx = R(-4) * a_qx, ody = R(-4) * a_qy, odz = R(-4) * a_qz;
+    const R odA = a_qx + a_qy + a_mx - a_my;
+    const R odB = a_qx - a_qy + a_mx + a_my;
+    const R odC = a_qx + a_qz - a_mx + a_mz;
+    const R odD = a_qx - a_qz - a_mx - a_mz;
+    const R odE = a_qy + a_qz + a_my - a_mz;
+    const R odF = a_qy - a_qz + a_my + a_mz;
+    R corr[19];
+    corr[0] = c0;
+    corr[1] = evx + odx;  corr[2] = evx - odx;
+    corr[3] = evy + ody;  corr[4] = evy - ody;
+    corr[5] = evz + odz;  corr[6] = evz - odz;
+    corr[7] = evA + odA;  corr[8] = evA - odA;
+    corr[9] = evB + odB;  corr[10] = evB - odB;
+    corr[11] = evC + odC; corr[12] = evC - odC;
+    corr[13] = evD + odD; corr[14] = evD - odD;
+    corr[15] = evE + odE; corr[16] = evE - odE;
+    corr[17] = evF + odF; corr[18] = evF - odF;
+#pragma unroll
+    for (int i = 0; i < 19; i++) g[i] = FORCE ? g[i] + Fi[i] - corr[i] : g[i] - corr[i];
+    }
+}
+
+// ------------------------------------------------------------ context -----
+struct Ctx {
+    lbm_grid g;
+    int nx, ny, nz;
+    long long N;
+    double tau, F[3];
+    int storage, rates;
+    Rates rt;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    // fields
+    void *fA, *fB;
+    uint8_t *flags;
+    int *owner, *aux;
+    // compact sites (IBB boundary cells or IBM support cells)
+    long long max_sites;
+    int *site_cell, *site_first;
+    unsigned *site_mask;
+    double *sup_rho, *sup_u;    // IBM: rho and u* per site
+    double *sup_F, *sup_Fp;     // IBM: accumulated force and force of the current pass
+    // links
+    long long max_links;
+    int *link_cell, *link_pid;
+    int8_t *link_dir, *link_scheme;
+    double *link_q, *link_fin, *link_dP, *link_dT;
+    // compaction scratch
+    int nblk;
+    long long *blk_sites, *blk_links;
+    long long *d_counts;  // [0] sites, [1] links
+    long long nsites, nlinks;   // host copies (valid after a sync)
+    long long nsites_hint;      // launch sizing: a bound on the device count
+    // particles (FP64)
+    int max_np, np, fixed;
+    double dens;
+    double *X, *Xold, *U, *W, *R, *mass, *inertia, *Fh, *Th, *Fprev, *Tprev, *Fc, *Iu, *Ir;
+    int *has_prev;
+    // markers
+    long long max_markers, nm;
+    double *mX, *mUnit, *mdV, *mUs, *mF, *mFacc;
+    int *mpid, *m_first;
+    double rd;  // marker retraction (IBM-B: 0.4)
+    // statistics scratch
+    double *rho_f, *u_f, *partials;
+    unsigned long long *near_key;
+    int *near_pid;
+    // status
+    unsigned *d_status;
+    unsigned *h_status;
+    cudaEvent_t ev_status;
+    bool status_pending;
+    // geometry
+    int has_pipe;
+    double pipe_R, pipe_cx, pipe_cy;
+    int armed_bc;
+    long long step;
+    bool broken;
+    bool initialised_pops;
+    char err[256];
+    // profiling
+    long long launches;                 // every kernel launched
+    long long group_launches[LBM_NGROUPS];
+    int prof_on;
+    void *prof;                         // host-side event records (lbm_api.cu)
+};
+
+// every launcher calls this once per kernel it launches
+inline void count_launch(Ctx &c, int group, int n = 1) {
+    c.launches += n;
+    c.group_launches[group] += n;
+}
+enum { G_BULK = 0, G_BND = 1, G_IBM = 2, G_IBMCOL = 3, G_PART = 4, G_GEOM = 5, G_STATS = 6, G_OTHER = 7 };
+
+}  // namespace lbmgb
+
+struct lbm_ctx {
+    lbmgb::Ctx c;
+};
+
+// ------------------------------------------------ cross-file launchers ----
+namespace lbmgb {
+cudaError_t launch_init_equilibrium(Ctx &c, const double *u_dev, double rho0);
+cudaError_t launch_set_populations(Ctx &c, const double *f_dev);
+cudaError_t launch_get_populations(Ctx &c, double *f_dev);
+cudaError_t launch_stream_collide(Ctx &c, int bc);
+cudaError_t launch_boundary_collide(Ctx &c);
+cudaError_t launch_ibm_collide(Ctx &c);
+cudaError_t launch_pipe_flags(Ctx &c);
+cudaError_t launch_sphere_mark(Ctx &c, bool clear_old);
+cudaError_t launch_refill(Ctx &c);
+cudaError_t launch_finish_geometry(Ctx &c);
+cudaError_t build_sites(Ctx &c, int mode);  // mode 1: IBB links, 2: IBM support
+cudaError_t launch_gimem(Ctx &c);
+cudaError_t launch_release(Ctx &c);
+cudaError_t launch_particle_update(Ctx &c);
+cudaError_t launch_markers_place(Ctx &c);
+cudaError_t launch_support_mark(Ctx &c);
+cudaError_t launch_ibm_passes(Ctx &c);
+cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only);
+cudaError_t launch_ibm_rigid_overwrite(Ctx &c);
+cudaError_t launch_macro(Ctx &c, int mask_mode);
+cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);
+}  // namespace lbmgb

@@ -1,0 +1,578 @@
+// Particle-side kernels, FP64 throughout:
+//  - gimem_reduce: per-particle sum of the per-link momentum exchange
+//    (Galilean-invariant form of Wen et al. 2014, Sec. 3.1);
+//  - release_kernel: initial particle velocity = fluid velocity averaged
+//    over the particle volume (Sec. 3.1);
+//  - contact_kernel / eom_kernel: normal-only soft-sphere contacts and the
+//    rigid-body update (Sec. 3.1);
+//  - IBM: marker placement, support-cell marking, the three direct-forcing
+//    passes (interpolate with the Peskin 4-point delta, force, spread;
+//    Sec. 2.1 / 3.1) and the particle force with Kempe's inner-fluid term.
+// All reductions are block trees in a fixed order (bitwise reproducible for
+// a given launch configuration); only the IBM spreading uses FP64 atomics.
+#include "lbm_internal.cuh"
+
+namespace lbmgb {
+
+__device__ __forceinline__ double pmimg(double d, int n) {
+    if (d > 0.5 * n) d -= n;
+    else if (d < -0.5 * n) d += n;
+    return d;
+}
+__device__ __forceinline__ int pwrap(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+constexpr int PB = 256;  // threads per particle block
+
+// fixed-order block sum of NV doubles per thread; result valid in thread 0
+template <int NV>
+__device__ void block_sum(double v[NV], double *sh /* PB*NV */) {
+    for (int k = 0; k < NV; k++) sh[k * PB + threadIdx.x] = v[k];
+    __syncthreads();
+    for (int s = PB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < NV; k++) sh[k * PB + threadIdx.x] += sh[k * PB + threadIdx.x + s];
+        __syncthreads();
+    }
+    for (int k = 0; k < NV; k++) v[k] = sh[k * PB];
+}
+
+// ------------------------------------------------------------ GIMEM ------
+struct GimemArgs {
+    const uint8_t *flags;
+    const int *aux, *site_first, *link_pid;
+    const unsigned *site_mask;
+    const double *link_dP, *link_dT, *X, *R;
+    double *Fh, *Th;
+    int nx, ny, nz;
+    long long max_sites;
+};
+
+__global__ void __launch_bounds__(PB) gimem_reduce_kernel(GimemArgs a) {
+    __shared__ double sh[6 * PB];
+    const int p = blockIdx.x;
+    const int r = (int)ceil(a.R[p]) + 2;
+    const int bx = (int)floor(a.X[3 * p]) - r, by = (int)floor(a.X[3 * p + 1]) - r, bz = (int)floor(a.X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < w * w * w; t += PB) {
+        const int x = pwrap(bx + t % w, a.nx), y = pwrap(by + (t / w) % w, a.ny), z = pwrap(bz + t / (w * w), a.nz);
+        const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
+        if (!(a.flags[c] & FL_BND)) continue;
+        const int s = a.aux[c];
+        if (s < 0 || s >= a.max_sites) continue;
+        const int first = a.site_first[s];
+        const int n = __popc(a.site_mask[s]);
+        for (int k = first; k < first + n; k++) {
+            if (a.link_pid[k] != p) continue;
+            for (int d = 0; d < 3; d++) {
+                v[d] += a.link_dP[3 * k + d];
+                v[3 + d] += a.link_dT[3 * k + d];
+            }
+        }
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; d++) {
+            a.Fh[3 * p + d] = v[d];
+            a.Th[3 * p + d] = v[3 + d];
+        }
+}
+
+cudaError_t launch_gimem(Ctx &c) {
+    if (c.np == 0) return cudaSuccess;
+    GimemArgs a{c.flags, c.aux, c.site_first, c.link_pid, c.site_mask, c.link_dP, c.link_dT,
+                c.X, c.R, c.Fh, c.Th, c.nx, c.ny, c.nz, c.max_sites};
+    count_launch(c, G_PART);
+    gimem_reduce_kernel<<<c.np, PB, 0, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- solid fraction ----
+// Kempe et al. (2012): alpha = sum(-phi H(-phi)) / sum|phi| over the 8 cell
+// corners, phi = |x - X| - R (x relative to the particle, minimum image).
+__device__ double solid_fraction(double rx, double ry, double rz, double R) {
+    double num = 0.0, den = 0.0;
+    for (int m = 0; m < 8; m++) {
+        const double ax = rx + ((m & 1) ? 0.5 : -0.5), ay = ry + ((m & 2) ? 0.5 : -0.5), az = rz + ((m & 4) ? 0.5 : -0.5);
+        const double phi = sqrt(ax * ax + ay * ay + az * az) - R;
+        if (phi < 0.0) num += -phi;
+        den += fabs(phi);
+    }
+    return den > 0.0 ? num / den : 0.0;
+}
+
+// velocity of the post-collision state of cell c: (sum f c - F/2) / rho
+template <int S>
+__device__ void cell_velocity(const void *A, size_t N, long long c, double Fx, double Fy, double Fz, double &rho,
+                              double u[3]) {
+    typedef typename Store<S>::T T;
+    const T *P = (const T *)A;
+    double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+    for (int i = 0; i < 19; i++) {
+        double g;
+        if (S == LBM_F64) g = *(const double *)(P + i * N + c);
+        else if (S == LBM_F32) g = *(const float *)(P + i * N + c);
+        else if (S == LBM_F16S) g = (double)__half2float(*(const __half *)(P + i * N + c)) / (double)F16_SCALE;
+        else g = (double)__bfloat162float(*(const __nv_bfloat16 *)(P + i * N + c));
+        r += g;
+        j0 += g * cx(i);
+        j1 += g * cy(i);
+        j2 += g * cz(i);
+    }
+    rho = 1.0 + r;
+    u[0] = (j0 - 0.5 * Fx) / rho;
+    u[1] = (j1 - 0.5 * Fy) / rho;
+    u[2] = (j2 - 0.5 * Fz) / rho;
+}
+
+struct VolArgs {
+    const void *A;
+    const uint8_t *flags;
+    const int *aux;
+    const double *sup_u;
+    const double *X, *R;
+    double *out_u, *out_r;  // per particle (3): sum alpha u and sum alpha r x u (or averages)
+    int nx, ny, nz;
+    long long N;
+    double F[3];
+    int mode;  // 0: release average from populations, 1: Kempe integrals from populations, 2: from sup_u
+    long long max_sites;
+};
+
+template <int S>
+__global__ void __launch_bounds__(PB) volume_kernel(VolArgs a) {
+    __shared__ double sh[7 * PB];
+    const int p = blockIdx.x;
+    const double *Xp = a.X + 3 * p;
+    const double R = a.R[p];
+    const int r = (int)ceil(R) + 1;
+    const int bx = (int)floor(Xp[0]) - r, by = (int)floor(Xp[1]) - r, bz = (int)floor(Xp[2]) - r;
+    const int w = 2 * r + 2;
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < w * w * w; t += PB) {
+        const int x = pwrap(bx + t % w, a.nx), y = pwrap(by + (t / w) % w, a.ny), z = pwrap(bz + t / (w * w), a.nz);
+        const double rx = pmimg((double)x - Xp[0], a.nx), ry = pmimg((double)y - Xp[1], a.ny),
+                     rz = pmimg((double)z - Xp[2], a.nz);
+        const double al = solid_fraction(rx, ry, rz, R);
+        if (al <= 0.0) continue;
+        const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
+        double u[3], rho;
+        if (a.mode == 2) {
+            const int s = a.aux[c];
+            if (s < 0 || s >= a.max_sites) continue;
+            u[0] = a.sup_u[3 * s];
+            u[1] = a.sup_u[3 * s + 1];
+            u[2] = a.sup_u[3 * s + 2];
+        } else {
+            const bool fluid = a.mode == 0 ? true : !(a.flags[c] & FL_SOLID);
+            cell_velocity<S>(a.A, (size_t)a.N, c, fluid ? a.F[0] : 0.0, fluid ? a.F[1] : 0.0, fluid ? a.F[2] : 0.0,
+                             rho, u);
+        }
+        v[0] += al * u[0];
+        v[1] += al * u[1];
+        v[2] += al * u[2];
+        v[3] += al * (ry * u[2] - rz * u[1]);
+        v[4] += al * (rz * u[0] - rx * u[2]);
+        v[5] += al * (rx * u[1] - ry * u[0]);
+        v[6] += al;
+    }
+    block_sum<7>(v, sh);
+    if (threadIdx.x == 0) {
+        if (a.mode == 0) {
+            for (int d = 0; d < 3; d++) a.out_u[3 * p + d] = v[6] > 0.0 ? v[d] / v[6] : 0.0;
+        } else {
+            for (int d = 0; d < 3; d++) {
+                a.out_u[3 * p + d] = v[d];
+                a.out_r[3 * p + d] = v[3 + d];
+            }
+        }
+    }
+}
+
+static cudaError_t launch_volume(Ctx &c, int mode, double *out_u, double *out_r) {
+    if (c.np == 0) return cudaSuccess;
+    count_launch(c, G_PART);
+    VolArgs a{c.fA, c.flags, c.aux, c.sup_u, c.X, c.R, out_u, out_r, c.nx, c.ny, c.nz, c.N,
+              {c.F[0], c.F[1], c.F[2]}, mode, c.max_sites};
+    switch (c.storage) {
+    case LBM_F64: volume_kernel<LBM_F64><<<c.np, PB, 0, c.stream>>>(a); break;
+    case LBM_F32: volume_kernel<LBM_F32><<<c.np, PB, 0, c.stream>>>(a); break;
+    case LBM_F16S: volume_kernel<LBM_F16S><<<c.np, PB, 0, c.stream>>>(a); break;
+    default: volume_kernel<LBM_BF16S><<<c.np, PB, 0, c.stream>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_release(Ctx &c) { return launch_volume(c, 0, c.U, nullptr); }
+
+// ------------------------------------------------------- contacts, EOM ----
+struct EomArgs {
+    double *X, *Xold, *U, *W, *Fh, *Th, *Fprev, *Tprev, *Fc;
+    const double *R, *mass, *inertia;
+    int *has_prev;
+    int np, nx, ny, nz;
+};
+
+// Normal-only soft-sphere contact (Sec. 3.1): for a gap below zeta = 1, a
+// spring-dashpot along the line of centres, k_n = m (pi^2 + ln^2 e)/Tc^2,
+// eta_n = -2 m ln e / Tc, m the reduced mass, e = 0.97, Tc = 10 steps.
+// Pair contributions are added in increasing partner index.
+__global__ void contact_kernel(EomArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const double zeta = 1.0, e = 0.97, Tc = 10.0, PI = 3.14159265358979323846;
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < a.np; q++) {
+        if (q == p) continue;
+        const int ia = q < p ? q : p, ib = q < p ? p : q;  // pair evaluated as (a < b)
+        const double d0 = pmimg(a.X[3 * ia] - a.X[3 * ib], a.nx), d1 = pmimg(a.X[3 * ia + 1] - a.X[3 * ib + 1], a.ny),
+                     d2 = pmimg(a.X[3 * ia + 2] - a.X[3 * ib + 2], a.nz);
+        const double dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        const double gap = dist - (a.R[ia] + a.R[ib]);
+        if (gap >= zeta || dist <= 0.0) continue;
+        const double n0 = d0 / dist, n1 = d1 / dist, n2 = d2 / dist;
+        const double vn = (a.U[3 * ia] - a.U[3 * ib]) * n0 + (a.U[3 * ia + 1] - a.U[3 * ib + 1]) * n1 +
+                          (a.U[3 * ia + 2] - a.U[3 * ib + 2]) * n2;
+        const double meff = a.mass[ia] * a.mass[ib] / (a.mass[ia] + a.mass[ib]);
+        const double le = log(e);
+        const double kn = meff * (PI * PI + le * le) / (Tc * Tc);
+        const double eta = -2.0 * meff * le / Tc;
+        const double Fm = kn * (zeta - gap) - eta * vn;
+        const double sg = q < p ? -1.0 : 1.0;
+        F[0] += sg * (Fm * n0);
+        F[1] += sg * (Fm * n1);
+        F[2] += sg * (Fm * n2);
+    }
+    for (int d = 0; d < 3; d++) a.Fc[3 * p + d] = F[d];
+}
+
+// U += ((F_h^n + F_h^{n-1})/2 + F_c)/m, W += (T^n + T^{n-1})/(2 I), X += U_new.
+__global__ void eom_kernel(EomArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.np) return;
+    const int n[3] = {a.nx, a.ny, a.nz};
+    const bool hp = a.has_prev[p] != 0;
+    for (int d = 0; d < 3; d++) {
+        const double Fh = a.Fh[3 * p + d], Th = a.Th[3 * p + d];
+        const double Fa = hp ? 0.5 * (Fh + a.Fprev[3 * p + d]) : Fh;
+        const double Ta = hp ? 0.5 * (Th + a.Tprev[3 * p + d]) : Th;
+        const double u1 = a.U[3 * p + d] + (Fa + a.Fc[3 * p + d]) / a.mass[p];
+        a.U[3 * p + d] = u1;
+        a.W[3 * p + d] += Ta / a.inertia[p];
+        a.Xold[3 * p + d] = a.X[3 * p + d];
+        double x = a.X[3 * p + d] + u1;
+        if (x >= n[d]) x -= n[d];
+        if (x < 0.0) x += n[d];
+        a.X[3 * p + d] = x;
+        a.Fprev[3 * p + d] = Fh;
+        a.Tprev[3 * p + d] = Th;
+    }
+    a.has_prev[p] = 1;
+}
+
+cudaError_t launch_particle_update(Ctx &c) {
+    if (c.np == 0) return cudaSuccess;
+    EomArgs a{c.X, c.Xold, c.U, c.W, c.Fh, c.Th, c.Fprev, c.Tprev, c.Fc, c.R, c.mass, c.inertia, c.has_prev,
+              c.np, c.nx, c.ny, c.nz};
+    const int tb = 128, nb = (c.np + tb - 1) / tb;
+    count_launch(c, G_PART, 2);
+    contact_kernel<<<nb, tb, 0, c.stream>>>(a);
+    eom_kernel<<<nb, tb, 0, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- IBM ------
+__device__ __forceinline__ double peskin(double r) {
+    const double a = fabs(r);
+    if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
+    if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
+    return 0.0;
+}
+
+__global__ void markers_place_kernel(double *mX, const double *mUnit, const int *mpid, const double *X, long long nm,
+                                     int nx, int ny, int nz) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nm) return;
+    const int p = mpid[l];
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; d++) {
+        double x = X[3 * p + d] + mUnit[3 * l + d];
+        if (x >= n[d]) x -= n[d];
+        if (x < 0.0) x += n[d];
+        mX[3 * l + d] = x;
+    }
+}
+
+cudaError_t launch_markers_place(Ctx &c) {
+    if (c.np == 0 || c.nm == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((c.nm + 127) / 128);
+    count_launch(c, G_GEOM);
+    markers_place_kernel<<<nb, 128, 0, c.stream>>>(c.mX, c.mUnit, c.mpid, c.X, c.nm, c.nx, c.ny, c.nz);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ void flag_or(uint8_t *flags, long long c, uint8_t bit) {
+    unsigned *w = (unsigned *)(flags + (c & ~3LL));
+    atomicOr(w, ((unsigned)bit) << (8 * (c & 3)));
+}
+
+__global__ void clear_sup_kernel(uint8_t *flags, long long N) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const uint8_t f = flags[c];
+    if (f & FL_SUP) flags[c] = (uint8_t)(f & ~FL_SUP);
+}
+
+// support = 4x4x4 stencil of every marker
+__global__ void mark_stencil_kernel(uint8_t *flags, const double *mX, long long nm, int nx, int ny, int nz) {
+    const long long l = (long long)blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
+    if (l >= nm) return;
+    const int k = threadIdx.x & 63;
+    const int ox = k & 3, oy = (k >> 2) & 3, oz = k >> 4;
+    const int x = pwrap((int)floor(mX[3 * l]) - 1 + ox, nx), y = pwrap((int)floor(mX[3 * l + 1]) - 1 + oy, ny),
+              z = pwrap((int)floor(mX[3 * l + 2]) - 1 + oz, nz);
+    flag_or(flags, (long long)x + (long long)nx * (y + (long long)ny * z), FL_SUP);
+}
+
+// ... plus every cell overlapping a particle (|x - X| < R + 1), whose
+// velocity enters the inner-fluid integrals
+__global__ void mark_interior_kernel(uint8_t *flags, const double *X, const double *R, int nx, int ny, int nz) {
+    const int p = blockIdx.x;
+    const double Rp = R[p];
+    const int r = (int)ceil(Rp) + 1;
+    const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
+        const int x = pwrap(bx + t % w, nx), y = pwrap(by + (t / w) % w, ny), z = pwrap(bz + t / (w * w), nz);
+        const double rx = pmimg(x - X[3 * p], nx), ry = pmimg(y - X[3 * p + 1], ny), rz = pmimg(z - X[3 * p + 2], nz);
+        if (rx * rx + ry * ry + rz * rz < (Rp + 1.0) * (Rp + 1.0))
+            flag_or(flags, (long long)x + (long long)nx * (y + (long long)ny * z), FL_SUP);
+    }
+}
+
+cudaError_t launch_support_mark(Ctx &c) {
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+    count_launch(c, G_GEOM, 1 + (c.nm > 0) + (c.np > 0));
+    clear_sup_kernel<<<nb, 256, 0, c.stream>>>(c.flags, c.N);
+    if (c.nm > 0) {
+        const unsigned mb = (unsigned)((c.nm + 3) / 4);
+        mark_stencil_kernel<<<mb, 256, 0, c.stream>>>(c.flags, c.mX, c.nm, c.nx, c.ny, c.nz);
+    }
+    if (c.np > 0) mark_interior_kernel<<<c.np, 256, 0, c.stream>>>(c.flags, c.X, c.R, c.nx, c.ny, c.nz);
+    return cudaGetLastError();
+}
+
+struct IbmArgs {
+    const double *mX, *mdV;
+    const int *mpid;
+    double *mUs, *mF, *mFacc;
+    const int *aux;
+    double *sup_rho, *sup_u, *sup_F, *sup_Fp;
+    const double *X, *U, *W;
+    long long nm;
+    const long long *counts;
+    long long max_sites;
+    int nx, ny, nz;
+    int pass;
+};
+
+// interpolate U*_l = sum u* delta, rho_l = sum rho delta; F_l = 2 rho_l (U_d - U*_l)
+__global__ void ibm_interp_kernel(IbmArgs a) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.nm) return;
+    const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
+    const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
+    double ph0[4], ph1[4], ph2[4];
+    for (int k = 0; k < 4; k++) {
+        ph0[k] = peskin((double)(b0 + k) - X0);
+        ph1[k] = peskin((double)(b1 + k) - X1);
+        ph2[k] = peskin((double)(b2 + k) - X2);
+    }
+    double U0 = 0, U1 = 0, U2 = 0, rl = 0;
+    for (int kz = 0; kz < 4; kz++)
+        for (int ky = 0; ky < 4; ky++)
+            for (int kx = 0; kx < 4; kx++) {
+                const double wgt3 = ph0[kx] * ph1[ky] * ph2[kz];
+                const long long c = (long long)pwrap(b0 + kx, a.nx) +
+                                    (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
+                const int s = a.aux[c];
+                if (s < 0 || s >= a.max_sites) continue;
+                rl += wgt3 * a.sup_rho[s];
+                U0 += wgt3 * a.sup_u[3 * s];
+                U1 += wgt3 * a.sup_u[3 * s + 1];
+                U2 += wgt3 * a.sup_u[3 * s + 2];
+            }
+    double Ud[3] = {0, 0, 0};
+    const int p = a.mpid[l];
+    if (p >= 0) {
+        const double r0 = pmimg(X0 - a.X[3 * p], a.nx), r1 = pmimg(X1 - a.X[3 * p + 1], a.ny),
+                     r2 = pmimg(X2 - a.X[3 * p + 2], a.nz);
+        const double *Wp = a.W + 3 * p, *Up = a.U + 3 * p;
+        Ud[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
+        Ud[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
+        Ud[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
+    }
+    const double Fl[3] = {2.0 * rl * (Ud[0] - U0), 2.0 * rl * (Ud[1] - U1), 2.0 * rl * (Ud[2] - U2)};
+    a.mUs[3 * l] = U0;
+    a.mUs[3 * l + 1] = U1;
+    a.mUs[3 * l + 2] = U2;
+    for (int d = 0; d < 3; d++) {
+        a.mF[3 * l + d] = Fl[d];
+        a.mFacc[3 * l + d] = a.pass == 0 ? Fl[d] : a.mFacc[3 * l + d] + Fl[d];
+    }
+}
+
+// spread F(x) += F_l delta dV_l (one thread per stencil node)
+__global__ void ibm_spread_kernel(IbmArgs a) {
+    const long long l = (long long)blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
+    if (l >= a.nm) return;
+    const int k = threadIdx.x & 63;
+    const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
+    const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
+    const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
+    const double wgt3 = peskin((double)(b0 + kx) - X0) * peskin((double)(b1 + ky) - X1) * peskin((double)(b2 + kz) - X2);
+    const double sc = wgt3 * a.mdV[l];
+    const long long c = (long long)pwrap(b0 + kx, a.nx) +
+                        (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
+    const int s = a.aux[c];
+    if (s < 0 || s >= a.max_sites) return;
+    atomicAdd(a.sup_Fp + 3 * s, a.mF[3 * l] * sc);
+    atomicAdd(a.sup_Fp + 3 * s + 1, a.mF[3 * l + 1] * sc);
+    atomicAdd(a.sup_Fp + 3 * s + 2, a.mF[3 * l + 2] * sc);
+}
+
+// u* += F/(2 rho); accumulate the IBM force; clear the pass buffer
+__global__ void ibm_update_kernel(IbmArgs a) {
+    const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
+        const double ir = 0.5 / a.sup_rho[s];
+        for (int d = 0; d < 3; d++) {
+            const double f = a.sup_Fp[3 * s + d];
+            a.sup_u[3 * s + d] += f * ir;
+            a.sup_F[3 * s + d] = a.pass == 0 ? f : a.sup_F[3 * s + d] + f;
+            a.sup_Fp[3 * s + d] = 0.0;
+        }
+    }
+}
+
+cudaError_t launch_ibm_passes(Ctx &c) {
+    IbmArgs a{c.mX, c.mdV, c.mpid, c.mUs, c.mF, c.mFacc, c.aux, c.sup_rho, c.sup_u, c.sup_F, c.sup_Fp,
+              c.X, c.U, c.W, c.nm, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, 0};
+    long long ns = c.nsites_hint > 0 ? c.nsites_hint : c.max_sites;
+    if (ns > c.max_sites) ns = c.max_sites;
+    long long ub = (ns + 255) / 256;
+    if (ub < 1) ub = 1;
+    if (ub > 152 * 32) ub = 152 * 32;
+    count_launch(c, G_IBM, 3 * (1 + (c.nm > 0 ? 2 : 0)));
+    for (int pass = 0; pass < 3; pass++) {
+        a.pass = pass;
+        if (c.nm > 0) {
+            ibm_interp_kernel<<<(unsigned)((c.nm + 127) / 128), 128, 0, c.stream>>>(a);
+            ibm_spread_kernel<<<(unsigned)((c.nm + 3) / 4), 256, 0, c.stream>>>(a);
+        }
+        ibm_update_kernel<<<(unsigned)ub, 256, 0, c.stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// particle force/torque: -sum_l F_l dV_l (+ moment) plus the change of the
+// inner-fluid momentum sum alpha u (Kempe et al. 2012)
+struct SumArgs {
+    const double *mX, *mdV, *mFacc;
+    const int *m_first;
+    const double *X;
+    double *Fh, *Th, *Iu, *Ir;
+    const double *Iu_new, *Ir_new;
+    int nx, ny, nz;
+};
+
+__global__ void __launch_bounds__(PB) ibm_sum_kernel(SumArgs a) {
+    __shared__ double sh[6 * PB];
+    const int p = blockIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int l = a.m_first[p] + threadIdx.x; l < a.m_first[p + 1]; l += PB) {
+        const double F0 = -a.mFacc[3 * l] * a.mdV[l], F1 = -a.mFacc[3 * l + 1] * a.mdV[l],
+                     F2 = -a.mFacc[3 * l + 2] * a.mdV[l];
+        const double r0 = pmimg(a.mX[3 * l] - a.X[3 * p], a.nx), r1 = pmimg(a.mX[3 * l + 1] - a.X[3 * p + 1], a.ny),
+                     r2 = pmimg(a.mX[3 * l + 2] - a.X[3 * p + 2], a.nz);
+        v[0] += F0;
+        v[1] += F1;
+        v[2] += F2;
+        v[3] += r1 * F2 - r2 * F1;
+        v[4] += r2 * F0 - r0 * F2;
+        v[5] += r0 * F1 - r1 * F0;
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; d++) {
+            a.Fh[3 * p + d] = v[d] + (a.Iu_new[3 * p + d] - a.Iu[3 * p + d]);
+            a.Th[3 * p + d] = v[3 + d] + (a.Ir_new[3 * p + d] - a.Ir[3 * p + d]);
+            a.Iu[3 * p + d] = a.Iu_new[3 * p + d];
+            a.Ir[3 * p + d] = a.Ir_new[3 * p + d];
+        }
+}
+
+cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only) {
+    if (c.np == 0) return cudaSuccess;
+    if (init_only) return launch_volume(c, 1, c.Iu, c.Ir);
+    // scratch for the new integrals: the contact-force buffer (2 x 3 doubles
+    // per particle) is free until the contact kernel runs later in the step
+    double *Iu_new = c.Fc, *Ir_new = c.Fc + 3 * c.max_np;
+    cudaError_t e = launch_volume(c, 2, Iu_new, Ir_new);
+    if (e != cudaSuccess) return e;
+    SumArgs a{c.mX, c.mdV, c.mFacc, c.m_first, c.X, c.Fh, c.Th, c.Iu, c.Ir, Iu_new, Ir_new, c.nx, c.ny, c.nz};
+    count_launch(c, G_PART);
+    ibm_sum_kernel<<<c.np, PB, 0, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+// one-time rigid-body overwrite inside the particles at insertion (Sec. 3.1)
+template <int S>
+__global__ void rigid_overwrite_kernel(void *A, const uint8_t *flags, const int *owner, const double *X,
+                                       const double *U, const double *W, const double *R, int nx, int ny, int nz,
+                                       long long N, double F0, double F1, double F2) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R Rt;
+    const int p = blockIdx.x;
+    const int r = (int)ceil(R[p]) + 1;
+    const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
+        const int x = pwrap(bx + t % w, nx), y = pwrap(by + (t / w) % w, ny), z = pwrap(bz + t / (w * w), nz);
+        const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
+        if (!(flags[c] & FL_SOLID) || owner[c] != p) continue;
+        double rho, u[3];
+        cell_velocity<S>(A, (size_t)N, c, 0.0, 0.0, 0.0, rho, u);  // solid cells feel no body force
+        const double rx = pmimg(x - X[3 * p], nx), ry = pmimg(y - X[3 * p + 1], ny), rz = pmimg(z - X[3 * p + 2], nz);
+        const double uw[3] = {U[3 * p] + (W[3 * p + 1] * rz - W[3 * p + 2] * ry),
+                              U[3 * p + 1] + (W[3 * p + 2] * rx - W[3 * p] * rz),
+                              U[3 * p + 2] + (W[3 * p] * ry - W[3 * p + 1] * rx)};
+        const double u2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+        for (int i = 0; i < 19; i++) {
+            const double cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
+            const double feq = wgt(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+            Store<S>::st((T *)A + (size_t)i * N + c, Rt(feq - wgt(i)));
+        }
+    }
+    (void)F0; (void)F1; (void)F2;
+}
+
+cudaError_t launch_ibm_rigid_overwrite(Ctx &c) {
+    if (c.np == 0) return cudaSuccess;
+    count_launch(c, G_OTHER);
+    switch (c.storage) {
+#define RO(S) rigid_overwrite_kernel<S><<<c.np, 256, 0, c.stream>>>(c.fA, c.flags, c.owner, c.X, c.U, c.W, c.R, \
+                                                                      c.nx, c.ny, c.nz, c.N, 0, 0, 0)
+    case LBM_F64: RO(LBM_F64); break;
+    case LBM_F32: RO(LBM_F32); break;
+    case LBM_F16S: RO(LBM_F16S); break;
+    default: RO(LBM_BF16S); break;
+#undef RO
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb

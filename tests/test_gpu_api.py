@@ -1,0 +1,86 @@
+"""C-ABI behaviour on the GPU: error statuses, watchdog, capacities,
+profiling counters. Failures are made on the host (a NaN written into the
+uploaded populations, a too-small capacity); nothing faults the GPU."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_05448_gb300 import build, lbm as L
+    build.build()
+    L.load()
+    return L
+
+
+def test_watchdog_reports_nan(lbm):
+    n = 12
+    L = lbm.Lattice(n, n, n, 0.6, storage=lbm.F32)
+    f = np.tile(np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None], (1, n ** 3))
+    f[5, 100] = np.nan
+    L.set_populations(f)
+    L.step(3)
+    with pytest.raises(lbm.LbmError) as e:
+        L.stats()
+    assert e.value.status == lbm.LBM_EUNSTABLE
+    with pytest.raises(lbm.LbmError) as e:
+        L.step(1)
+    assert e.value.status == lbm.LBM_ESTATE
+    L.close()
+
+
+def test_bc_fixed_by_first_step(lbm):
+    L = lbm.Lattice(16, 16, 8, 0.6)
+    L.set_pipe(6.0)
+    L.step(2, lbm.BC_IBB)
+    with pytest.raises(lbm.LbmError) as e:
+        L.step(1, lbm.BC_IBM_B)
+    assert e.value.status == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LbmError) as e:
+        L.set_pipe(5.0)
+    assert e.value.status == lbm.LBM_ESTATE
+    L.close()
+
+
+def test_link_capacity_overflow_is_reported(lbm):
+    L = lbm.Lattice(24, 24, 4, 0.6, max_links=100)
+    with pytest.raises(lbm.LbmError) as e:
+        L.set_pipe(10.0)
+    assert e.value.status == lbm.LBM_ENOMEM
+    L.close()
+
+
+def test_invalid_arguments(lbm):
+    L = lbm.Lattice(16, 16, 16, 0.6, max_particles=1)
+    with pytest.raises(lbm.LbmError) as e:
+        L.add_spheres(np.array([[3.0, 3.0, 3.0], [8.0, 8, 8]]), 2.0)
+    assert e.value.status == lbm.LBM_ENOMEM
+    with pytest.raises(lbm.LbmError) as e:
+        L.add_spheres(np.array([[30.0, 3.0, 3.0]]), 2.0)
+    assert e.value.status == lbm.LBM_EINVAL
+    L.close()
+
+
+def test_profile_counts_launches_and_times(lbm):
+    L = lbm.Lattice(40, 40, 16, 0.6, storage=lbm.F32)
+    L.init_velocity(workloads.pipe_velocity(40, 40, 16, 17.0, 0.02, 0.05, seed=0))
+    L.set_pipe(17.0)
+    L.step(2, lbm.BC_IBB)
+    L.profile_enable(True)
+    L.step(10, lbm.BC_IBB)
+    p = L.profile(0)
+    assert p["launches"]["bulk"] == 10 and p["launches"]["ibb_boundary"] == 10
+    assert p["spans"]["bulk"] == 10 and p["ms"]["bulk"] > 0
+    # profile again after re-enabling: events are reused, destroy frees each once
+    L.profile_enable(True)
+    L.step(5, lbm.BC_IBB)
+    p = L.profile(0)
+    assert p["spans"]["bulk"] == 5
+    L.close()
