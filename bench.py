@@ -37,6 +37,7 @@ import workloads  # noqa: E402
 
 PIPE = workloads.PIPE_148
 PP = workloads.pipe_parameters(PIPE["radius"], PIPE["nu"], PIPE["re_tau"])
+NZ = PIPE["nz"]  # pipe length; --nz shortens it for profiler captures
 HBM_FALLBACK = 6800.0
 
 
@@ -50,7 +51,7 @@ def peaks():
 
 
 def pipe_field(nz=None):
-    nz = nz or PIPE["nz"]
+    nz = nz or NZ
     return workloads.pipe_velocity(PIPE["nx"], PIPE["ny"], nz, PIPE["radius"], PP["u_bulk"],
                                    PIPE["perturbation"], seed=0)
 
@@ -168,7 +169,7 @@ def e2e_pipe(lbm, torch, steps):
     """Same workload through the C ABI from host buffers: the initial field is
     uploaded from pinned host memory and the final velocity field read back,
     both inside the timed region."""
-    nx, ny, nz = PIPE["nx"], PIPE["ny"], PIPE["nz"]
+    nx, ny, nz = PIPE["nx"], PIPE["ny"], NZ
     N = nx * ny * nz
     u = pipe_field()
     host_in = torch.empty(3 * N, dtype=torch.float64, pin_memory=True)
@@ -245,12 +246,17 @@ def traffic_for(kernel_key):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nz", type=int, default=PIPE["nz"],
+                    help="pipe length in cells (default 438; shorter only for profiler captures)")
     args = ap.parse_args()
+    global NZ
+    NZ = args.nz
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -296,7 +302,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(dev)
-    main_res = run_case(lbm, torch, "pipe_ibb_f32", PIPE["nx"], PIPE["ny"], PIPE["nz"], PP["tau"], (0, 0, PP["g"]),
+    main_res = run_case(lbm, torch, "pipe_ibb_f32", PIPE["nx"], PIPE["ny"], NZ, PP["tau"], (0, 0, PP["g"]),
                         lbm.F32, lbm.RATES_SRT, lbm.BC_IBB, args.steps, args.warmup, setup)
     clk = clocks.stop()
     ms_total = main_res["ms"]
@@ -316,7 +322,7 @@ def main():
     if not args.no_variants and rank == 0:
         for name, storage, bc in (("pipe_ibm_b_f32", lbm.F32, lbm.BC_IBM_B), ("pipe_ibb_f16s", lbm.F16S, lbm.BC_IBB),
                                   ("pipe_ibb_bf16s", lbm.BF16S, lbm.BC_IBB)):
-            r = run_case(lbm, torch, name, PIPE["nx"], PIPE["ny"], PIPE["nz"], PP["tau"], (0, 0, PP["g"]),
+            r = run_case(lbm, torch, name, PIPE["nx"], PIPE["ny"], NZ, PP["tau"], (0, 0, PP["g"]),
                          storage, lbm.RATES_SRT, bc, args.steps, min(args.warmup, 10), pipe_setup(lbm))
             p = r["prof"]
             bms = p["ms"]["bulk"] / max(1, p["spans"]["bulk"])
@@ -336,7 +342,7 @@ def main():
                               "finite": r["finite"]}
 
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         e2e = e2e_pipe(lbm, torch, args.steps)
         e2e = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in e2e.items()}
     cpu = None
@@ -359,7 +365,7 @@ def main():
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "pipe D=146 L=438 in 148x148x438 D3Q19, FP32 populations, SRT, nu=0.0032, "
+            "config": {"workload": f"pipe D=146 L={NZ} in 148x148x{NZ} D3Q19, FP32 populations, SRT, nu=0.0032, "
                                    "Re_tau=180 body force, linear IBB wall",
                        "fluid_cells": main_res["fluid_cells"], "parallelism": f"replicas x{world}",
                        "l2": "no flush: populations 2x1.46 GB >> 129 MB L2"},
