@@ -187,6 +187,27 @@ typedef struct {
 } lbm_profile_t;
 lbm_status lbm_profile(lbm_ctx *ctx, int enable, lbm_profile_t *out);
 
+/* Kinetic energy and dissipation of a velocity field already in device
+ * memory, computed without allocating anything. The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, e.g. code
+ * running while a stream is captured into a CUDA graph, solvers whose
+ * device memory belongs to another framework's pool, or loops that must not
+ * pay cudaMalloc's implicit device synchronisation.
+ * u_dev: 3*N doubles (component-major, x fastest), N = nx*ny*nz, device.
+ * nu: kinematic viscosity. out_dev: 2 doubles on the device, receiving the
+ * box averages of 1/2 |u|^2 and 2 nu s_ij s_ij (periodic central
+ * differences), the same quantities lbm_stats reports as kinetic_energy and
+ * dissipation for an unmasked field. Launched on cuda_stream; asynchronous.
+ * Scratch: a fixed 512 KiB device array inside the library (held by every
+ * GPU that loads it until exit), shared by all calls: calls that overlap on
+ * the GPU race on it. N above lbm_field_energy_noalloc_max_cells()
+ * (134,217,728 = 512^3) is refused with LBM_ENOMEM; bad pointers or sizes
+ * give LBM_EINVAL. The first call on a device looks the scratch address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture. */
+lbm_status lbm_field_energy_noalloc(const double *u_dev, int nx, int ny, int nz, double nu, double *out_dev,
+                                    void *cuda_stream);
+long long lbm_field_energy_noalloc_max_cells(void);
+
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(int status);
 void lbm_destroy(lbm_ctx *ctx);

@@ -30,7 +30,8 @@ BC = {"none": BC_NONE, "ibb": BC_IBB, "ibm_u": BC_IBM_U, "ibm_b": BC_IBM_B}
 EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_init_velocity", "lbm_set_populations", "lbm_set_pipe",
     "lbm_add_spheres", "lbm_step", "lbm_stats", "lbm_get_field", "lbm_num_links", "lbm_get_links",
-    "lbm_get_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile", "lbm_last_error",
+    "lbm_get_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile",
+    "lbm_field_energy_noalloc", "lbm_field_energy_noalloc_max_cells", "lbm_last_error",
     "lbm_status_string", "lbm_destroy",
 ]
 NGROUPS = 8
@@ -115,6 +116,9 @@ def load(build_if_missing: bool = False):
         "lbm_num_markers": (ctypes.c_int, [_P, _L]),
         "lbm_get_markers": (ctypes.c_int, [_P, ctypes.c_longlong, _D, _D, _D, _I]),
         "lbm_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Profile)]),
+        "lbm_field_energy_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                    _P, _P]),
+        "lbm_field_energy_noalloc_max_cells": (ctypes.c_longlong, []),
         "lbm_last_error": (ctypes.c_char_p, [_P]),
         "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_destroy": (None, [_P]),
