@@ -23,7 +23,7 @@ __device__ __forceinline__ int dwrap(int a, int n) {
 // rho and u of the post-collision state: sum f c = rho u + F/2 after a Guo
 // collision with total force F (body force on fluid cells + IBM force).
 template <int S>
-__global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux, const double *sup_F, double *rho_o,
+__global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux, const void *sup_Fv, double *rho_o,
                              double *u_o, long long N, double F0, double F1, double F2, int ibb, int ibm,
                              long long max_sites) {
     typedef typename Store<S>::T T;
@@ -51,6 +51,8 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
     const bool fluid = !(fl & FL_SOLID);
     double Fx = fluid ? F0 : 0.0, Fy = fluid ? F1 : 0.0, Fz = fluid ? F2 : 0.0;
     if (ibm && (fl & FL_SUP) && aux[c] >= 0 && aux[c] < max_sites) {
+        typedef typename Store<S>::R Rt;
+        const Rt *sup_F = (const Rt *)sup_Fv;
         const int s = aux[c];
         Fx += sup_F[3 * s];
         Fy += sup_F[3 * s + 1];

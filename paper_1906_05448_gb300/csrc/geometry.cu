@@ -15,9 +15,10 @@ __device__ __forceinline__ double gmimg(double d, int n) {
     else if (d < -0.5 * n) d = __dadd_rn(d, (double)n);
     return d;
 }
+// wrap a coordinate in [-n, 2n) into [0, n)
 __device__ __forceinline__ int gwrap(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
+    a = a < 0 ? a + n : a;
+    return a >= n ? a - n : a;
 }
 // |d|^2 summed as ((dx^2 + dy^2) + dz^2)
 __device__ __forceinline__ double dist2(double dx, double dy, double dz) {
@@ -107,6 +108,12 @@ cudaError_t launch_sphere_mark(Ctx &c, bool clear_old) {
 }
 
 // ------------------------------------------------------------ refill ------
+// Caiazzo (2008) refill (Sec. 3.1) of a node that the particle p uncovered:
+// rho = mean over fluid neighbours, u = rigid-body velocity, and the
+// non-equilibrium part of the fluid neighbour best aligned with the outward
+// normal (ties: lowest direction index).
+// refill_collect_kernel lists the uncovered nodes (one block per particle);
+// refill_apply_kernel handles one node per warp, lane i on direction i.
 struct RefillArgs {
     void *B;
     const uint8_t *flags;
@@ -115,108 +122,131 @@ struct RefillArgs {
     int nx, ny, nz;
     long long N;
     double F[3];
+    long long *count;  // device counter of listed nodes
+    int *list, *list_pid;
+    long long cap;
 };
 
-template <typename R, int S>
-__device__ double load_f(const void *B, size_t idx) {
-    typedef typename Store<S>::T T;
-    const T *p = (const T *)B + idx;
-    if (S == LBM_F64) return *(const double *)p;
-    if (S == LBM_F32) return (double)*(const float *)p;
-    if (S == LBM_F16S) return (double)__half2float(*(const __half *)p) / (double)F16_SCALE;
-    return (double)__bfloat162float(*(const __nv_bfloat16 *)p);
-}
-
-// Caiazzo (2008) refill (Sec. 3.1) of a node that the particle p uncovered:
-// rho = mean over fluid neighbours, u = rigid-body velocity, and the
-// non-equilibrium part of the fluid neighbour best aligned with the outward
-// normal (ties: lowest direction index).
-template <int S>
-__global__ void refill_kernel(RefillArgs a) {
-    typedef typename Store<S>::T T;
-    typedef typename Store<S>::R Rt;
+__global__ void refill_collect_kernel(RefillArgs a) {
     const int p = blockIdx.x;
     const double *Xp = a.X + 3 * p;
     const int r = (int)ceil(a.R[p]) + 3;
     const int bx = (int)floor(Xp[0]) - r, by = (int)floor(Xp[1]) - r, bz = (int)floor(Xp[2]) - r;
     const int w = 2 * r + 2;
-    const int total = w * w * w;
-    const size_t N = (size_t)a.N;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
         const int x = gwrap(bx + t % w, a.nx), y = gwrap(by + (t / w) % w, a.ny), z = gwrap(bz + t / (w * w), a.nz);
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
         const uint8_t fl = a.flags[c];
         if (!(fl & FL_WAS_SOLID) || (fl & FL_SOLID) || a.aux[c] != p) continue;
-        double rv[3] = {gmimg((double)x - Xp[0], a.nx), gmimg((double)y - Xp[1], a.ny),
-                        gmimg((double)z - Xp[2], a.nz)};
-        const double *Up = a.U + 3 * p, *Wp = a.W + 3 * p;
-        double uw[3] = {Up[0] + (Wp[1] * rv[2] - Wp[2] * rv[1]), Up[1] + (Wp[2] * rv[0] - Wp[0] * rv[2]),
-                        Up[2] + (Wp[0] * rv[1] - Wp[1] * rv[0])};
-        const double l = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
-        double nrm[3] = {0, 0, 0};
-        if (l > 0) {
-            nrm[0] = rv[0] / l;
-            nrm[1] = rv[1] / l;
-            nrm[2] = rv[2] / l;
-        }
-        double rsum = 0.0, best = -1e300;
-        int cnt = 0;
-        long long bestc = -1;
-#pragma unroll 1
-        for (int i = 1; i < 19; i++) {
-            const long long nb = (long long)gwrap(x + cx(i), a.nx) +
-                                 (long long)a.nx * (gwrap(y + cy(i), a.ny) + (long long)a.ny * gwrap(z + cz(i), a.nz));
-            if (a.flags[nb] & (FL_WAS_SOLID | FL_SOLID)) continue;
-            double rr = 0.0;
-            for (int k = 0; k < 19; k++) rr += load_f<Rt, S>(a.B, k * N + nb) + wgt(k);
-            rsum += rr;
-            cnt++;
-            const double cl = sqrt((double)(cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)));
-            const double al = (nrm[0] * cx(i) + nrm[1] * cy(i) + nrm[2] * cz(i)) / cl;
-            if (al > best) {
-                best = al;
-                bestc = nb;
-            }
-        }
-        const double rho = cnt ? rsum / cnt : 1.0;
-        double fe_nb[19];
-        bool have = bestc >= 0;
-        if (have) {
-            double rn = 0.0, j[3] = {0, 0, 0};
-            for (int k = 0; k < 19; k++) {
-                const double fk = load_f<Rt, S>(a.B, k * N + bestc) + wgt(k);
-                fe_nb[k] = fk;
-                rn += fk;
-                j[0] += fk * cx(k);
-                j[1] += fk * cy(k);
-                j[2] += fk * cz(k);
-            }
-            const double un[3] = {(j[0] - 0.5 * a.F[0]) / rn, (j[1] - 0.5 * a.F[1]) / rn, (j[2] - 0.5 * a.F[2]) / rn};
-            const double un2 = un[0] * un[0] + un[1] * un[1] + un[2] * un[2];
-            for (int k = 0; k < 19; k++) {
-                const double cu = cx(k) * un[0] + cy(k) * un[1] + cz(k) * un[2];
-                fe_nb[k] -= wgt(k) * rn * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * un2);  // f_neq of neighbour
-            }
-        }
-        const double uw2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
-        for (int k = 0; k < 19; k++) {
-            const double cu = cx(k) * uw[0] + cy(k) * uw[1] + cz(k) * uw[2];
-            double f = wgt(k) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uw2);
-            if (have) f += fe_nb[k];
-            Store<S>::st((T *)a.B + k * N + c, Rt(f - wgt(k)));
+        const long long k = atomicAdd((unsigned long long *)a.count, 1ULL);
+        if (k < a.cap) {
+            a.list[k] = (int)c;
+            a.list_pid[k] = p;
         }
     }
 }
 
+template <int S>
+__global__ void __launch_bounds__(256) refill_apply_kernel(RefillArgs a) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R Rt;
+    const long long n = *a.count < a.cap ? *a.count : a.cap;
+    const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const size_t N = (size_t)a.N;
+    T *B = (T *)a.B;
+    const int c = a.list[k], p = a.list_pid[k];
+    const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+    const double rv0 = gmimg((double)x - a.X[3 * p], a.nx), rv1 = gmimg((double)y - a.X[3 * p + 1], a.ny),
+                 rv2 = gmimg((double)z - a.X[3 * p + 2], a.nz);
+    const double *Up = a.U + 3 * p, *Wp = a.W + 3 * p;
+    const Rt uw0 = Rt(Up[0] + (Wp[1] * rv2 - Wp[2] * rv1)), uw1 = Rt(Up[1] + (Wp[2] * rv0 - Wp[0] * rv2)),
+             uw2 = Rt(Up[2] + (Wp[0] * rv1 - Wp[1] * rv0));
+    const double l = sqrt(rv0 * rv0 + rv1 * rv1 + rv2 * rv2);
+    const Rt n0 = l > 0 ? Rt(rv0 / l) : Rt(0), n1 = l > 0 ? Rt(rv1 / l) : Rt(0), n2 = l > 0 ? Rt(rv2 / l) : Rt(0);
+    // lane i (1..18): neighbour x + c_i
+    Rt rho_i = 0, j0 = 0, j1 = 0, j2 = 0, al = Rt(-1e30);
+    int valid = 0;
+    long long nb = -1;
+    if (lane >= 1 && lane < 19) {
+        const int i = lane;
+        const int cxi = (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+                      : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+        const int cyi = (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+                      : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+        const int czi = (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+                      : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+        nb = (long long)gwrap(x + cxi, a.nx) + (long long)a.nx * (gwrap(y + cyi, a.ny) + (long long)a.ny * gwrap(z + czi, a.nz));
+        if (!(a.flags[nb] & (FL_WAS_SOLID | FL_SOLID))) {
+            valid = 1;
+            Rt r = 0;
+#pragma unroll
+            for (int q = 0; q < 19; q++) {
+                const Rt g = Store<S>::ld(B + q * N + nb);
+                r += g;
+                j0 += g * Rt(cx(q));
+                j1 += g * Rt(cy(q));
+                j2 += g * Rt(cz(q));
+            }
+            rho_i = Rt(1) + r;
+            const Rt cl = sqrt(Rt(cxi * cxi + cyi * cyi + czi * czi));
+            al = (n0 * Rt(cxi) + n1 * Rt(cyi) + n2 * Rt(czi)) / cl;
+        }
+    }
+    // mean density of the fluid neighbours, and the best-aligned one
+    Rt rsum = valid ? rho_i : Rt(0);
+    int cnt = valid;
+    Rt best = al;
+    int bl = valid ? lane : 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const Rt ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (ob > best || (ob == best && ol < bl)) {
+            best = ob;
+            bl = ol;
+        }
+    }
+    const Rt rho = cnt ? rsum / Rt(cnt) : Rt(1);
+    const bool have = bl < 32;
+    const int src = have ? bl : 0;
+    const Rt rn = __shfl_sync(0xffffffffu, rho_i, src), k0 = __shfl_sync(0xffffffffu, j0, src),
+             k1 = __shfl_sync(0xffffffffu, j1, src), k2 = __shfl_sync(0xffffffffu, j2, src);
+    const long long nbb = __shfl_sync(0xffffffffu, nb, src);
+    if (lane >= 19) return;
+    const int q = lane;
+    const Rt uu = uw0 * uw0 + uw1 * uw1 + uw2 * uw2;
+    const Rt cuw = Rt(cx(q)) * uw0 + Rt(cy(q)) * uw1 + Rt(cz(q)) * uw2;
+    Rt f = Rt(wgt(q)) * rho * (Rt(1) + Rt(3) * cuw + Rt(4.5) * cuw * cuw - Rt(1.5) * uu);
+    if (have) {
+        const Rt un0 = (k0 - Rt(0.5) * Rt(a.F[0])) / rn, un1 = (k1 - Rt(0.5) * Rt(a.F[1])) / rn,
+                 un2 = (k2 - Rt(0.5) * Rt(a.F[2])) / rn;
+        const Rt un = un0 * un0 + un1 * un1 + un2 * un2;
+        const Rt cun = Rt(cx(q)) * un0 + Rt(cy(q)) * un1 + Rt(cz(q)) * un2;
+        const Rt feq_nb = Rt(wgt(q)) * rn * (Rt(1) + Rt(3) * cun + Rt(4.5) * cun * cun - Rt(1.5) * un);
+        const Rt fnb = Store<S>::ld(B + q * N + nbb) + Rt(wgt(q));
+        f += fnb - feq_nb;
+    }
+    Store<S>::st(B + q * N + c, f - Rt(wgt(q)));
+}
+
 cudaError_t launch_refill(Ctx &c) {
     if (c.np == 0) return cudaSuccess;
-    count_launch(c, G_GEOM);
-    RefillArgs a{c.fB, c.flags, c.aux, c.X, c.U, c.W, c.R, c.nx, c.ny, c.nz, c.N, {c.F[0], c.F[1], c.F[2]}};
+    count_launch(c, G_GEOM, 3);
+    RefillArgs a{c.fB, c.flags, c.aux, c.X, c.U, c.W, c.R, c.nx, c.ny, c.nz, c.N, {c.F[0], c.F[1], c.F[2]},
+                 c.d_counts + 2, c.refill_list, c.refill_pid, c.max_refill};
+    cudaError_t e = cudaMemsetAsync(c.d_counts + 2, 0, sizeof(long long), c.stream);
+    if (e != cudaSuccess) return e;
+    refill_collect_kernel<<<c.np, 256, 0, c.stream>>>(a);
+    const unsigned nb = (unsigned)((c.max_refill * 32 + 255) / 256);
     switch (c.storage) {
-    case LBM_F64: refill_kernel<LBM_F64><<<c.np, 128, 0, c.stream>>>(a); break;
-    case LBM_F32: refill_kernel<LBM_F32><<<c.np, 128, 0, c.stream>>>(a); break;
-    case LBM_F16S: refill_kernel<LBM_F16S><<<c.np, 128, 0, c.stream>>>(a); break;
-    default: refill_kernel<LBM_BF16S><<<c.np, 128, 0, c.stream>>>(a); break;
+    case LBM_F64: refill_apply_kernel<LBM_F64><<<nb, 256, 0, c.stream>>>(a); break;
+    case LBM_F32: refill_apply_kernel<LBM_F32><<<nb, 256, 0, c.stream>>>(a); break;
+    case LBM_F16S: refill_apply_kernel<LBM_F16S><<<nb, 256, 0, c.stream>>>(a); break;
+    default: refill_apply_kernel<LBM_BF16S><<<nb, 256, 0, c.stream>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -453,18 +483,12 @@ __global__ void __launch_bounds__(CT) site_emit_kernel(SiteArgs a) {
             a.site_mask[s0] = mask[k];
             a.aux[c] = (int)s0;
             if (a.mode == 1) {
-                const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
+                // cell and direction only; link_geom_kernel fills in q, owner and scheme
                 long long lk = l0;
                 for (int l = 1; l < 19; l++) {
                     if (!((mask[k] >> l) & 1u)) continue;
-                    double q;
-                    int pid, sch;
-                    link_geometry(a, x, y, z, l, q, pid, sch);
                     a.link_cell[lk] = (int)c;
                     a.link_dir[lk] = (int8_t)l;
-                    a.link_scheme[lk] = (int8_t)sch;
-                    a.link_q[lk] = q;
-                    a.link_pid[lk] = pid;
                     lk++;
                 }
             }
@@ -473,6 +497,23 @@ __global__ void __launch_bounds__(CT) site_emit_kernel(SiteArgs a) {
         }
         l0 += nl_c;
         s0++;
+    }
+}
+
+// one thread per link: wall fraction q, owner and interpolation scheme
+__global__ void __launch_bounds__(256) link_geom_kernel(SiteArgs a) {
+    const long long nl = a.counts[1] < a.max_links ? a.counts[1] : a.max_links;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nl;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long c = a.link_cell[k];
+        const int l = a.link_dir[k];
+        const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
+        double q;
+        int pid, sch;
+        link_geometry(a, x, y, z, l, q, pid, sch);
+        a.link_scheme[k] = (int8_t)sch;
+        a.link_q[k] = q;
+        a.link_pid[k] = pid;
     }
 }
 
@@ -508,10 +549,18 @@ cudaError_t build_sites(Ctx &c, int mode) {
     a.max_links = c.max_links;
     a.status = c.d_status;
     const int nblk = (int)((c.N + TILE - 1) / TILE);
-    count_launch(c, G_GEOM, 3);
+    count_launch(c, G_GEOM, mode == 1 ? 4 : 3);
     site_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
     site_scan_kernel<<<1, CT, 0, c.stream>>>(a, nblk);
     site_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
+    if (mode == 1) {
+        long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
+        if (n > c.max_links) n = c.max_links;
+        long long nb = (n + 255) / 256;
+        if (nb < 1) nb = 1;
+        if (nb > 152LL * 64) nb = 152LL * 64;
+        link_geom_kernel<<<(unsigned)nb, 256, 0, c.stream>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -31,11 +31,15 @@ struct Plan {
     long long N, max_sites, max_links, max_markers;
     int max_np, nblk;
     size_t fA, fB, flags, owner, aux;
-    size_t site_cell, site_first, site_mask, sup_rho, sup_u, sup_F, sup_Fp;
+    size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_fin, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status;
+    size_t blk_sites, blk_links, counts, status, seg, refill;
+    long long max_refill;
+    long long max_seg;
+    size_t xy_start, xy_j, xy_w;
+    long long max_xy;
     size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
-    size_t mX, mUnit, mdV, mUs, mF, mFacc, mpid, mfirst;
+    size_t mX, mUnit, mdV, mUs, mF, mFacc, mFr, mB, mE, mpid, mfirst;
     size_t rho_f, u_f, partials, near_key, near_pid;
     size_t total;
 };
@@ -66,8 +70,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.site_cell = L.take(4 * ms);
     P.site_first = L.take(4 * ms);
     P.site_mask = L.take(4 * ms);
-    P.sup_rho = L.take(8 * ms);
-    P.sup_u = L.take(24 * ms);
+    P.sup_ru = L.take(32 * ms);
     P.sup_F = L.take(24 * ms);
     P.sup_Fp = L.take(24 * ms);
     P.link_cell = L.take(4 * ml);
@@ -78,9 +81,17 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.link_fin = L.take(8 * ml);
     P.link_dP = L.take(24 * ml);
     P.link_dT = L.take(24 * ml);
+    P.max_xy = 64LL * (g->nx + g->ny);
+    P.xy_start = L.take(4 * ((size_t)g->nx * g->ny + 1));
+    P.xy_j = L.take(4 * (size_t)P.max_xy);
+    P.xy_w = L.take(8 * (size_t)P.max_xy);
+    P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32);
+    P.seg = L.take(8 * (size_t)P.max_seg);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
-    P.counts = L.take(16);
+    P.counts = L.take(32);
+    P.max_refill = 256LL * (P.max_np > 0 ? P.max_np : 1);
+    P.refill = L.take(8 * (size_t)P.max_refill);
     P.status = L.take(16);
     P.pX = L.take(24 * np);
     P.pXold = L.take(24 * np);
@@ -103,6 +114,9 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.mUs = L.take(24 * mm);
     P.mF = L.take(24 * mm);
     P.mFacc = L.take(24 * mm);
+    P.mFr = L.take(24 * mm);
+    P.mB = L.take(12 * mm);
+    P.mE = L.take(24 * mm);
     P.mpid = L.take(4 * mm);
     P.mfirst = L.take(4 * (np + 1));
     P.rho_f = L.take(8 * n);
@@ -138,7 +152,8 @@ __global__ void fill_owner(int *p, long long n) {
     if (i < n) p[i] = NO_OWNER;
 }
 
-__global__ void dense_ibm_force(double *out, const double *sup_F, const int *site_cell, const long long *counts,
+template <typename R>
+__global__ void dense_ibm_force(double *out, const R *sup_F, const int *site_cell, const long long *counts,
                                 long long max_sites, long long N) {
     const long long ns = counts[0] < max_sites ? counts[0] : max_sites;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
@@ -292,6 +307,14 @@ void pspan(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b) {
 
 int marker_count(double RL) { return (int)std::floor(M_PI / 3.0 * (12.0 * RL * RL + 1.0) + 0.5); }
 
+// Peskin (2002) 4-point kernel, host copy for the static pipe weights
+double peskin_host(double r) {
+    const double a = std::fabs(r);
+    if (a <= 1.0) return (3.0 - 2.0 * a + std::sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
+    if (a <= 2.0) return (5.0 - 2.0 * a - std::sqrt(-7.0 + 12.0 * a - 4.0 * a * a)) * 0.125;
+    return 0.0;
+}
+
 // Lagrangian markers (Sec. 2.1: marker volume close to the cell volume).
 // Spheres: golden-spiral points at R_L = R - r_d, dV = pi (12 R_L^2 + 1) / (3 N_L).
 // Pipe: a ring of round(2 pi R_L) points at R_L = R + r_d in every z plane.
@@ -302,16 +325,52 @@ lbm_status build_markers(Ctx &c) {
     if (c.has_pipe) {
         const double RL = c.pipe_R + rd;
         const int nc = (int)std::floor(2.0 * M_PI * RL + 0.5);
+        std::vector<double> rx(nc), ry(nc);
+        for (int j = 0; j < nc; j++) {
+            const double th = 2.0 * M_PI * j / nc;
+            rx[j] = c.pipe_cx + RL * std::cos(th);
+            ry[j] = c.pipe_cy + RL * std::sin(th);
+        }
         for (int z = 0; z < c.nz; z++)
             for (int j = 0; j < nc; j++) {
-                const double th = 2.0 * M_PI * j / nc;
-                X.push_back(c.pipe_cx + RL * std::cos(th));
-                X.push_back(c.pipe_cy + RL * std::sin(th));
+                X.push_back(rx[j]);
+                X.push_back(ry[j]);
                 X.push_back((double)z);
                 dV.push_back(2.0 * M_PI * RL / nc);
                 pid.push_back(-1);
             }
         unit.assign(X.size(), 0.0);
+        // per (x, y) column: the ring markers covering it and their x-y weights
+        const long long nxy = (long long)c.nx * c.ny;
+        std::vector<std::vector<std::pair<int, double>>> lists((size_t)nxy);
+        for (int j = 0; j < nc; j++) {
+            const int bx = (int)std::floor(rx[j]) - 1, by = (int)std::floor(ry[j]) - 1;
+            for (int ky = 0; ky < 4; ky++)
+                for (int kx = 0; kx < 4; kx++) {
+                    const double w = peskin_host((double)(bx + kx) - rx[j]) * peskin_host((double)(by + ky) - ry[j]);
+                    if (w == 0.0) continue;
+                    const int xw = ((bx + kx) % c.nx + c.nx) % c.nx, yw = ((by + ky) % c.ny + c.ny) % c.ny;
+                    lists[(size_t)xw + (size_t)c.nx * yw].push_back({j, w});
+                }
+        }
+        std::vector<int> st((size_t)nxy + 1), jj;
+        std::vector<double> ww;
+        for (long long k = 0; k < nxy; k++) {
+            st[k] = (int)jj.size();
+            for (auto &e : lists[k]) {
+                jj.push_back(e.first);
+                ww.push_back(e.second);
+            }
+        }
+        st[nxy] = (int)jj.size();
+        if ((long long)jj.size() > c.pipe_max_xy) return fail(c, LBM_ENOMEM, "pipe marker lists exceed capacity");
+        CK(cudaMemcpy(c.pipe_xy_start, st.data(), sizeof(int) * st.size(), cudaMemcpyHostToDevice));
+        if (!jj.empty()) {
+            CK(cudaMemcpy(c.pipe_xy_j, jj.data(), sizeof(int) * jj.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c.pipe_xy_w, ww.data(), sizeof(double) * ww.size(), cudaMemcpyHostToDevice));
+        }
+        c.pipe_nc = nc;
+        c.pipe_dV = 2.0 * M_PI * RL / nc;
     } else {
         std::vector<double> R(c.np);
         CK(cudaMemcpy(R.data(), c.R, sizeof(double) * c.np, cudaMemcpyDeviceToHost));
@@ -358,6 +417,7 @@ lbm_status arm(Ctx &c, int bc) {
             lbm_status s = build_markers(c);
             if (s != LBM_OK) return s;
             CK(launch_markers_place(c));
+            CK(launch_marker_offsets(c));
             CK(launch_ibm_rigid_overwrite(c));
             CK(launch_ibm_particle_sums(c, true));
         }
@@ -421,10 +481,9 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.site_cell = (int *)(b + P.site_cell);
     c.site_first = (int *)(b + P.site_first);
     c.site_mask = (unsigned *)(b + P.site_mask);
-    c.sup_rho = (double *)(b + P.sup_rho);
-    c.sup_u = (double *)(b + P.sup_u);
-    c.sup_F = (double *)(b + P.sup_F);
-    c.sup_Fp = (double *)(b + P.sup_Fp);
+    c.sup_ru = b + P.sup_ru;
+    c.sup_F = b + P.sup_F;
+    c.sup_Fp = b + P.sup_Fp;
     c.max_links = P.max_links;
     c.link_cell = (int *)(b + P.link_cell);
     c.link_pid = (int *)(b + P.link_pid);
@@ -434,10 +493,20 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.link_fin = (double *)(b + P.link_fin);
     c.link_dP = (double *)(b + P.link_dP);
     c.link_dT = (double *)(b + P.link_dT);
+    c.pipe_xy_start = (int *)(b + P.xy_start);
+    c.pipe_xy_j = (int *)(b + P.xy_j);
+    c.pipe_xy_w = (double *)(b + P.xy_w);
+    c.pipe_max_xy = P.max_xy;
+    c.seg = (unsigned long long *)(b + P.seg);
+    c.max_seg = P.max_seg;
+    c.nseg = 0;
     c.nblk = P.nblk;
     c.blk_sites = (long long *)(b + P.blk_sites);
     c.blk_links = (long long *)(b + P.blk_links);
     c.d_counts = (long long *)(b + P.counts);
+    c.refill_list = (int *)(b + P.refill);
+    c.refill_pid = c.refill_list + P.max_refill;
+    c.max_refill = P.max_refill;
     c.d_status = (unsigned *)(b + P.status);
     c.max_np = P.max_np;
     c.X = (double *)(b + P.pX);
@@ -462,6 +531,9 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.mUs = (double *)(b + P.mUs);
     c.mF = (double *)(b + P.mF);
     c.mFacc = (double *)(b + P.mFacc);
+    c.mFr = b + P.mFr;
+    c.mB = (int *)(b + P.mB);
+    c.mE = b + P.mE;
     c.mpid = (int *)(b + P.mpid);
     c.m_first = (int *)(b + P.mfirst);
     c.rho_f = (double *)(b + P.rho_f);
@@ -491,7 +563,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     if ((e = cudaMemsetAsync(c.fB, 0, 19 * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.flags, 0, (size_t)c.N + 8, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.aux, 0xff, 4 * (size_t)c.N, c.stream)) != cudaSuccess) return bad(e, "memset");
-    if ((e = cudaMemsetAsync(c.d_counts, 0, 16, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.d_counts, 0, 32, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.d_status, 0, 16, c.stream)) != cudaSuccess) return bad(e, "memset");
     fill_owner<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.owner, c.N);
     if ((e = cudaGetLastError()) != cudaSuccess) return bad(e, "fill");
@@ -537,6 +609,26 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     lbm_status s = sync_all(c);
     if (s != LBM_OK) return s;
     c.nsites_hint = c.nsites;
+    c.nlinks_hint = c.nlinks;
+    // IBB sweep work list: each row's fluid extent cut into 32-cell segments
+    // (the solid margin outside the wall is never visited)
+    std::vector<uint8_t> fl((size_t)c.N);
+    CK(cudaMemcpy(fl.data(), c.flags, (size_t)c.N, cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> segs;
+    for (long long row = 0; row < (long long)c.ny * c.nz; row++) {
+        const uint8_t *r = fl.data() + row * c.nx;
+        int x0 = 0, x1 = c.nx - 1;
+        while (x0 < c.nx && (r[x0] & FL_SOLID)) x0++;
+        while (x1 >= x0 && (r[x1] & FL_SOLID)) x1--;
+        for (int x = x0; x <= x1; x += 32) {
+            const int len = (x1 - x + 1) < 32 ? (x1 - x + 1) : 32;
+            segs.push_back((unsigned long long)row | ((unsigned long long)x << 32) | ((unsigned long long)len << 48));
+        }
+    }
+    if ((long long)segs.size() <= c.max_seg && c.nx < 65536) {
+        CK(cudaMemcpy(c.seg, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice));
+        c.nseg = (long long)segs.size();
+    }
     return LBM_OK;
 }
 
@@ -559,6 +651,8 @@ lbm_status lbm_add_spheres(lbm_ctx *h, int n, const double *xyz, const double *r
         I[p] = 0.4 * m[p] * R[p] * R[p];
     }
     c.np = n;
+    c.max_radius = 0.0;
+    for (int p = 0; p < n; p++) c.max_radius = R[p] > c.max_radius ? R[p] : c.max_radius;
     c.fixed = fixed != 0;
     c.dens = density_ratio;
     const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
@@ -579,6 +673,8 @@ lbm_status lbm_add_spheres(lbm_ctx *h, int n, const double *xyz, const double *r
     lbm_status s = sync_all(c);
     if (s != LBM_OK) return s;
     c.nsites_hint = c.nsites;
+    // links move with the particles: size launches with headroom
+    c.nlinks_hint = c.nlinks + c.nlinks / 4 + 1024;
     return LBM_OK;
 }
 
@@ -602,12 +698,12 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
             CK(launch_stream_collide(c, bc));
             pspan(c, G_BULK, t0, pmark(c));
         } else if (bc == LBM_BC_IBB) {
-            CK(launch_stream_collide(c, bc));
+            CK(launch_ibb_links(c));
             t1 = pmark(c);
-            pspan(c, G_BULK, t0, t1);
-            CK(launch_boundary_collide(c));
+            pspan(c, G_BND, t0, t1);
+            CK(launch_stream_collide(c, bc));
             t0 = pmark(c);
-            pspan(c, G_BND, t1, t0);
+            pspan(c, G_BULK, t1, t0);
             if (c.np > 0) CK(launch_gimem(c));
             if (moving) CK(launch_particle_update(c));
             t1 = pmark(c);
@@ -641,6 +737,7 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
             pspan(c, G_PART, t0, t1);
             if (moving) {
                 CK(launch_markers_place(c));
+                CK(launch_marker_offsets(c));
                 CK(launch_sphere_mark(c, true));
                 CK(launch_finish_geometry(c));
             }
@@ -698,7 +795,14 @@ lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
         if (bytes < 3 * N * sizeof(double)) return fail(c, LBM_EINVAL, "destination too small");
         CK(cudaMemsetAsync(c.u_f, 0, 3 * N * sizeof(double), c.stream));
         if (c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B)
-            dense_ibm_force<<<1024, 256, 0, c.stream>>>(c.u_f, c.sup_F, c.site_cell, c.d_counts, c.max_sites, c.N);
+        {
+            if (c.storage == LBM_F64)
+                dense_ibm_force<double><<<1024, 256, 0, c.stream>>>(c.u_f, (const double *)c.sup_F, c.site_cell,
+                                                                     c.d_counts, c.max_sites, c.N);
+            else
+                dense_ibm_force<float><<<1024, 256, 0, c.stream>>>(c.u_f, (const float *)c.sup_F, c.site_cell,
+                                                                    c.d_counts, c.max_sites, c.N);
+        }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(dst, c.u_f, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         break;

@@ -16,7 +16,7 @@ namespace lbmgb {
 // ---------------------------------------------------------------- flags ----
 enum : uint8_t {
     FL_SOLID = 1,     // inside a particle / outside the pipe
-    FL_BND = 2,       // IBB: fluid cell with at least one boundary link
+    FL_BND = 2,       // IBB: fluid cell with at least one boundary link (sites list)
     FL_SUP = 4,       // IBM: cell handled by the compact forcing path
     FL_WAS_SOLID = 8, // transient during a geometry update
 };
@@ -242,19 +242,26 @@ struct Ctx {
     long long max_sites;
     int *site_cell, *site_first;
     unsigned *site_mask;
-    double *sup_rho, *sup_u;    // IBM: rho and u* per site
-    double *sup_F, *sup_Fp;     // IBM: accumulated force and force of the current pass
+    // IBM per site: (rho, u*) as 4 values, accumulated force, force of the
+    // current pass, in the storage's arithmetic type (double for FP64, else float)
+    void *sup_ru, *sup_F, *sup_Fp;
     // links
     long long max_links;
     int *link_cell, *link_pid;
     int8_t *link_dir, *link_scheme;
     double *link_q, *link_fin, *link_dP, *link_dT;
+    // row segments of the fluid extent (IBB walls with a solid margin)
+    unsigned long long *seg;
+    long long nseg, max_seg;
     // compaction scratch
     int nblk;
     long long *blk_sites, *blk_links;
-    long long *d_counts;  // [0] sites, [1] links
+    long long *d_counts;  // [0] sites, [1] links, [2] refill nodes
+    int *refill_list, *refill_pid;
+    long long max_refill;
     long long nsites, nlinks;   // host copies (valid after a sync)
     long long nsites_hint;      // launch sizing: a bound on the device count
+    long long nlinks_hint;
     // particles (FP64)
     int max_np, np, fixed;
     double dens;
@@ -263,8 +270,19 @@ struct Ctx {
     // markers
     long long max_markers, nm;
     double *mX, *mUnit, *mdV, *mUs, *mF, *mFacc;
+    void *mFr;  // marker forces of the pass in the arithmetic type (spreading)
+    int *mB;    // per marker: first stencil node floor(X) - 1 (3 ints, wrapped)
+    void *mE;   // per marker: X - floor(X) in the arithmetic type (3 values)
     int *mpid, *m_first;
     double rd;  // marker retraction (IBM-B: 0.4)
+    double max_radius;
+    // pipe IBM: ring markers per plane and, per (x, y) column, the ring
+    // markers whose 4x4 footprint covers it with their x-y weights
+    int pipe_nc;
+    double pipe_dV;
+    int *pipe_xy_start, *pipe_xy_j;
+    double *pipe_xy_w;
+    long long pipe_max_xy;
     // statistics scratch
     double *rho_f, *u_f, *partials;
     unsigned long long *near_key;
@@ -308,7 +326,7 @@ cudaError_t launch_init_equilibrium(Ctx &c, const double *u_dev, double rho0);
 cudaError_t launch_set_populations(Ctx &c, const double *f_dev);
 cudaError_t launch_get_populations(Ctx &c, double *f_dev);
 cudaError_t launch_stream_collide(Ctx &c, int bc);
-cudaError_t launch_boundary_collide(Ctx &c);
+cudaError_t launch_ibb_links(Ctx &c);
 cudaError_t launch_ibm_collide(Ctx &c);
 cudaError_t launch_pipe_flags(Ctx &c);
 cudaError_t launch_sphere_mark(Ctx &c, bool clear_old);
@@ -319,6 +337,7 @@ cudaError_t launch_gimem(Ctx &c);
 cudaError_t launch_release(Ctx &c);
 cudaError_t launch_particle_update(Ctx &c);
 cudaError_t launch_markers_place(Ctx &c);
+cudaError_t launch_marker_offsets(Ctx &c);
 cudaError_t launch_support_mark(Ctx &c);
 cudaError_t launch_ibm_passes(Ctx &c);
 cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only);

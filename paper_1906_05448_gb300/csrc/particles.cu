@@ -19,9 +19,10 @@ __device__ __forceinline__ double pmimg(double d, int n) {
     else if (d < -0.5 * n) d += n;
     return d;
 }
+// wrap a coordinate in [-n, 2n) into [0, n)
 __device__ __forceinline__ int pwrap(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
+    a = a < 0 ? a + n : a;
+    return a >= n ? a - n : a;
 }
 
 constexpr int PB = 256;  // threads per particle block
@@ -92,16 +93,19 @@ cudaError_t launch_gimem(Ctx &c) {
 
 // ----------------------------------------------------- solid fraction ----
 // Kempe et al. (2012): alpha = sum(-phi H(-phi)) / sum|phi| over the 8 cell
-// corners, phi = |x - X| - R (x relative to the particle, minimum image).
-__device__ double solid_fraction(double rx, double ry, double rz, double R) {
-    double num = 0.0, den = 0.0;
+// corners, phi = |x - X| - R (x relative to the particle, minimum image),
+// in the arithmetic type R of the storage.
+template <typename R>
+__device__ R solid_fraction(R rx, R ry, R rz, R Rp) {
+    R num = 0, den = 0;
     for (int m = 0; m < 8; m++) {
-        const double ax = rx + ((m & 1) ? 0.5 : -0.5), ay = ry + ((m & 2) ? 0.5 : -0.5), az = rz + ((m & 4) ? 0.5 : -0.5);
-        const double phi = sqrt(ax * ax + ay * ay + az * az) - R;
-        if (phi < 0.0) num += -phi;
+        const R ax = rx + ((m & 1) ? R(0.5) : R(-0.5)), ay = ry + ((m & 2) ? R(0.5) : R(-0.5)),
+                az = rz + ((m & 4) ? R(0.5) : R(-0.5));
+        const R phi = sqrt(ax * ax + ay * ay + az * az) - Rp;
+        if (phi < R(0)) num += -phi;
         den += fabs(phi);
     }
-    return den > 0.0 ? num / den : 0.0;
+    return den > R(0) ? num / den : R(0);
 }
 
 // velocity of the post-collision state of cell c: (sum f c - F/2) / rho
@@ -132,7 +136,7 @@ struct VolArgs {
     const void *A;
     const uint8_t *flags;
     const int *aux;
-    const double *sup_u;
+    const void *sup_ru;  // (rho, u*) per support site, arithmetic type of the storage
     const double *X, *R;
     double *out_u, *out_r;  // per particle (3): sum alpha u and sum alpha r x u (or averages)
     int nx, ny, nz;
@@ -144,32 +148,40 @@ struct VolArgs {
 
 template <int S>
 __global__ void __launch_bounds__(PB) volume_kernel(VolArgs a) {
+    typedef typename Store<S>::R Rt;
     __shared__ double sh[7 * PB];
     const int p = blockIdx.x;
     const double *Xp = a.X + 3 * p;
-    const double R = a.R[p];
-    const int r = (int)ceil(R) + 1;
+    const double Rp = a.R[p];
+    const int r = (int)ceil(Rp) + 1;
     const int bx = (int)floor(Xp[0]) - r, by = (int)floor(Xp[1]) - r, bz = (int)floor(Xp[2]) - r;
     const int w = 2 * r + 2;
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    // cell offsets relative to the particle: integer part exact, fraction in Rt
+    const double fx = Xp[0] - floor(Xp[0]), fy = Xp[1] - floor(Xp[1]), fz = Xp[2] - floor(Xp[2]);
+    Rt v[7] = {0, 0, 0, 0, 0, 0, 0};
+    const Rt *su = (const Rt *)a.sup_ru;
     for (int t = threadIdx.x; t < w * w * w; t += PB) {
-        const int x = pwrap(bx + t % w, a.nx), y = pwrap(by + (t / w) % w, a.ny), z = pwrap(bz + t / (w * w), a.nz);
-        const double rx = pmimg((double)x - Xp[0], a.nx), ry = pmimg((double)y - Xp[1], a.ny),
-                     rz = pmimg((double)z - Xp[2], a.nz);
-        const double al = solid_fraction(rx, ry, rz, R);
-        if (al <= 0.0) continue;
+        const int ix = t % w, iy = (t / w) % w, iz = t / (w * w);
+        const int x = pwrap(bx + ix, a.nx), y = pwrap(by + iy, a.ny), z = pwrap(bz + iz, a.nz);
+        const Rt rx = Rt(ix - r) - Rt(fx), ry = Rt(iy - r) - Rt(fy), rz = Rt(iz - r) - Rt(fz);
+        const Rt al = solid_fraction<Rt>(rx, ry, rz, Rt(Rp));
+        if (al <= Rt(0)) continue;
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
-        double u[3], rho;
+        Rt u[3];
         if (a.mode == 2) {
             const int s = a.aux[c];
             if (s < 0 || s >= a.max_sites) continue;
-            u[0] = a.sup_u[3 * s];
-            u[1] = a.sup_u[3 * s + 1];
-            u[2] = a.sup_u[3 * s + 2];
+            u[0] = su[4 * s + 1];
+            u[1] = su[4 * s + 2];
+            u[2] = su[4 * s + 3];
         } else {
+            double rho, ud[3];
             const bool fluid = a.mode == 0 ? true : !(a.flags[c] & FL_SOLID);
             cell_velocity<S>(a.A, (size_t)a.N, c, fluid ? a.F[0] : 0.0, fluid ? a.F[1] : 0.0, fluid ? a.F[2] : 0.0,
-                             rho, u);
+                             rho, ud);
+            u[0] = Rt(ud[0]);
+            u[1] = Rt(ud[1]);
+            u[2] = Rt(ud[2]);
         }
         v[0] += al * u[0];
         v[1] += al * u[1];
@@ -179,14 +191,16 @@ __global__ void __launch_bounds__(PB) volume_kernel(VolArgs a) {
         v[5] += al * (rx * u[1] - ry * u[0]);
         v[6] += al;
     }
-    block_sum<7>(v, sh);
+    double vd[7];
+    for (int k = 0; k < 7; k++) vd[k] = double(v[k]);
+    block_sum<7>(vd, sh);
     if (threadIdx.x == 0) {
         if (a.mode == 0) {
-            for (int d = 0; d < 3; d++) a.out_u[3 * p + d] = v[6] > 0.0 ? v[d] / v[6] : 0.0;
+            for (int d = 0; d < 3; d++) a.out_u[3 * p + d] = vd[6] > 0.0 ? vd[d] / vd[6] : 0.0;
         } else {
             for (int d = 0; d < 3; d++) {
-                a.out_u[3 * p + d] = v[d];
-                a.out_r[3 * p + d] = v[3 + d];
+                a.out_u[3 * p + d] = vd[d];
+                a.out_r[3 * p + d] = vd[3 + d];
             }
         }
     }
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(PB) volume_kernel(VolArgs a) {
 static cudaError_t launch_volume(Ctx &c, int mode, double *out_u, double *out_r) {
     if (c.np == 0) return cudaSuccess;
     count_launch(c, G_PART);
-    VolArgs a{c.fA, c.flags, c.aux, c.sup_u, c.X, c.R, out_u, out_r, c.nx, c.ny, c.nz, c.N,
+    VolArgs a{c.fA, c.flags, c.aux, c.sup_ru, c.X, c.R, out_u, out_r, c.nx, c.ny, c.nz, c.N,
               {c.F[0], c.F[1], c.F[2]}, mode, c.max_sites};
     switch (c.storage) {
     case LBM_F64: volume_kernel<LBM_F64><<<c.np, PB, 0, c.stream>>>(a); break;
@@ -219,14 +233,26 @@ struct EomArgs {
 // Normal-only soft-sphere contact (Sec. 3.1): for a gap below zeta = 1, a
 // spring-dashpot along the line of centres, k_n = m (pi^2 + ln^2 e)/Tc^2,
 // eta_n = -2 m ln e / Tc, m the reduced mass, e = 0.97, Tc = 10 steps.
-// Pair contributions are added in increasing partner index.
-__global__ void contact_kernel(EomArgs a) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per particle; lanes stride over partners, cull in FP32 with a
+// margin and evaluate the few close pairs in FP64 (each pair as (a < b));
+// the lane sums are reduced in a fixed butterfly order.
+__global__ void __launch_bounds__(256) contact_kernel(EomArgs a) {
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= a.np) return;
     const double zeta = 1.0, e = 0.97, Tc = 10.0, PI = 3.14159265358979323846;
+    const float hx = 0.5f * a.nx, hy = 0.5f * a.ny, hz = 0.5f * a.nz;
+    const float px = (float)a.X[3 * p], py = (float)a.X[3 * p + 1], pz = (float)a.X[3 * p + 2];
+    const float Rp = (float)a.R[p];
     double F[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < a.np; q++) {
+    for (int q = lane; q < a.np; q += 32) {
         if (q == p) continue;
+        float dx = px - (float)a.X[3 * q], dy = py - (float)a.X[3 * q + 1], dz = pz - (float)a.X[3 * q + 2];
+        dx = dx > hx ? dx - a.nx : (dx < -hx ? dx + a.nx : dx);
+        dy = dy > hy ? dy - a.ny : (dy < -hy ? dy + a.ny : dy);
+        dz = dz > hz ? dz - a.nz : (dz < -hz ? dz + a.nz : dz);
+        const float reach = Rp + (float)a.R[q] + (float)zeta + 0.01f;
+        if (dx * dx + dy * dy + dz * dz >= reach * reach) continue;
         const int ia = q < p ? q : p, ib = q < p ? p : q;  // pair evaluated as (a < b)
         const double d0 = pmimg(a.X[3 * ia] - a.X[3 * ib], a.nx), d1 = pmimg(a.X[3 * ia + 1] - a.X[3 * ib + 1], a.ny),
                      d2 = pmimg(a.X[3 * ia + 2] - a.X[3 * ib + 2], a.nz);
@@ -246,7 +272,11 @@ __global__ void contact_kernel(EomArgs a) {
         F[1] += sg * (Fm * n1);
         F[2] += sg * (Fm * n2);
     }
-    for (int d = 0; d < 3; d++) a.Fc[3 * p + d] = F[d];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int d = 0; d < 3; d++) F[d] += __shfl_xor_sync(0xffffffffu, F[d], o);
+    if (lane == 0)
+        for (int d = 0; d < 3; d++) a.Fc[3 * p + d] = F[d];
 }
 
 // U += ((F_h^n + F_h^{n-1})/2 + F_c)/m, W += (T^n + T^{n-1})/(2 I), X += U_new.
@@ -279,7 +309,7 @@ cudaError_t launch_particle_update(Ctx &c) {
               c.np, c.nx, c.ny, c.nz};
     const int tb = 128, nb = (c.np + tb - 1) / tb;
     count_launch(c, G_PART, 2);
-    contact_kernel<<<nb, tb, 0, c.stream>>>(a);
+    contact_kernel<<<(c.np * 32 + 255) / 256, 256, 0, c.stream>>>(a);
     eom_kernel<<<nb, tb, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
@@ -304,6 +334,30 @@ __global__ void markers_place_kernel(double *mX, const double *mUnit, const int 
         if (x < 0.0) x += n[d];
         mX[3 * l + d] = x;
     }
+}
+
+// per marker: first stencil node floor(X) - 1 (wrapped) and X - floor(X)
+template <typename R>
+__global__ void marker_offsets_kernel(const double *mX, int *mB, R *mE, long long nm, int nx, int ny, int nz) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nm) return;
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; d++) {
+        const double x = mX[3 * l + d], f = floor(x);
+        mB[3 * l + d] = pwrap((int)f - 1, n[d]);
+        mE[3 * l + d] = R(x - f);
+    }
+}
+
+cudaError_t launch_marker_offsets(Ctx &c) {
+    if (c.nm == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((c.nm + 255) / 256);
+    count_launch(c, G_GEOM);
+    if (c.storage == LBM_F64)
+        marker_offsets_kernel<double><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (double *)c.mE, c.nm, c.nx, c.ny, c.nz);
+    else
+        marker_offsets_kernel<float><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (float *)c.mE, c.nm, c.nx, c.ny, c.nz);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_markers_place(Ctx &c) {
@@ -365,12 +419,27 @@ cudaError_t launch_support_mark(Ctx &c) {
     return cudaGetLastError();
 }
 
+// Peskin (2002) 4-point kernel in the arithmetic type R of the storage
+template <typename R>
+__device__ __forceinline__ R peskin_r(R r) {
+    const R a = fabs(r);
+    if (a <= R(1)) return (R(3) - R(2) * a + sqrt(R(1) + R(4) * a - R(4) * a * a)) * R(0.125);
+    if (a <= R(2)) return (R(5) - R(2) * a - sqrt(R(-7) + R(12) * a - R(4) * a * a)) * R(0.125);
+    return R(0);
+}
+
+// Support-cell data (rho, u*, accumulated force, force of the pass) and the
+// marker forces used for spreading are held in R: double for FP64 storage,
+// float otherwise (FP64 arithmetic is slow on this GPU and would dominate).
 struct IbmArgs {
     const double *mX, *mdV;
     const int *mpid;
     double *mUs, *mF, *mFacc;
+    void *mFr;
+    const int *mB;
+    const void *mE;
     const int *aux;
-    double *sup_rho, *sup_u, *sup_F, *sup_Fp;
+    void *sup_ru, *sup_F, *sup_Fp;
     const double *X, *U, *W;
     long long nm;
     const long long *counts;
@@ -379,35 +448,46 @@ struct IbmArgs {
     int pass;
 };
 
-// interpolate U*_l = sum u* delta, rho_l = sum rho delta; F_l = 2 rho_l (U_d - U*_l)
-__global__ void ibm_interp_kernel(IbmArgs a) {
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Interpolation, one warp per marker: lane k takes stencil nodes k and k+32;
+// U*_l = sum u* delta, rho_l = sum rho delta (fixed butterfly reduction);
+// F_l = 2 rho_l (U_d - U*_l) in FP64.
+template <typename R>
+__global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
+    const long long l = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (l >= a.nm) return;
-    const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
-    const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
-    double ph0[4], ph1[4], ph2[4];
-    for (int k = 0; k < 4; k++) {
-        ph0[k] = peskin((double)(b0 + k) - X0);
-        ph1[k] = peskin((double)(b1 + k) - X1);
-        ph2[k] = peskin((double)(b2 + k) - X2);
+    const R *ru = (const R *)a.sup_ru;
+    const R *E = (const R *)a.mE + 3 * l;
+    const R e0 = E[0], e1 = E[1], e2 = E[2];  // X - floor(X)
+    const int b0 = a.mB[3 * l], b1 = a.mB[3 * l + 1], b2 = a.mB[3 * l + 2];  // floor(X) - 1, wrapped
+    R U0 = 0, U1 = 0, U2 = 0, rl = 0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int k = lane + 32 * h;
+        const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
+        const R w = peskin_r<R>(R(kx - 1) - e0) * peskin_r<R>(R(ky - 1) - e1) * peskin_r<R>(R(kz - 1) - e2);
+        const long long c = (long long)pwrap(b0 + kx, a.nx) +
+                            (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
+        const int s = a.aux[c];
+        if (s < 0 || s >= a.max_sites) continue;
+        const R *q = ru + 4 * (size_t)s;
+        rl += w * q[0];
+        U0 += w * q[1];
+        U1 += w * q[2];
+        U2 += w * q[3];
     }
-    double U0 = 0, U1 = 0, U2 = 0, rl = 0;
-    for (int kz = 0; kz < 4; kz++)
-        for (int ky = 0; ky < 4; ky++)
-            for (int kx = 0; kx < 4; kx++) {
-                const double wgt3 = ph0[kx] * ph1[ky] * ph2[kz];
-                const long long c = (long long)pwrap(b0 + kx, a.nx) +
-                                    (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
-                const int s = a.aux[c];
-                if (s < 0 || s >= a.max_sites) continue;
-                rl += wgt3 * a.sup_rho[s];
-                U0 += wgt3 * a.sup_u[3 * s];
-                U1 += wgt3 * a.sup_u[3 * s + 1];
-                U2 += wgt3 * a.sup_u[3 * s + 2];
-            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rl += __shfl_xor_sync(0xffffffffu, rl, o);
+        U0 += __shfl_xor_sync(0xffffffffu, U0, o);
+        U1 += __shfl_xor_sync(0xffffffffu, U1, o);
+        U2 += __shfl_xor_sync(0xffffffffu, U2, o);
+    }
+    if (lane != 0) return;
     double Ud[3] = {0, 0, 0};
     const int p = a.mpid[l];
     if (p >= 0) {
+        const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
         const double r0 = pmimg(X0 - a.X[3 * p], a.nx), r1 = pmimg(X1 - a.X[3 * p + 1], a.ny),
                      r2 = pmimg(X2 - a.X[3 * p + 2], a.nz);
         const double *Wp = a.W + 3 * p, *Up = a.U + 3 * p;
@@ -415,67 +495,227 @@ __global__ void ibm_interp_kernel(IbmArgs a) {
         Ud[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
         Ud[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
     }
-    const double Fl[3] = {2.0 * rl * (Ud[0] - U0), 2.0 * rl * (Ud[1] - U1), 2.0 * rl * (Ud[2] - U2)};
-    a.mUs[3 * l] = U0;
-    a.mUs[3 * l + 1] = U1;
-    a.mUs[3 * l + 2] = U2;
+    const double U[3] = {double(U0), double(U1), double(U2)};
+    R *mFr = (R *)a.mFr;
+    a.mUs[3 * l] = U[0];
+    a.mUs[3 * l + 1] = U[1];
+    a.mUs[3 * l + 2] = U[2];
     for (int d = 0; d < 3; d++) {
-        a.mF[3 * l + d] = Fl[d];
-        a.mFacc[3 * l + d] = a.pass == 0 ? Fl[d] : a.mFacc[3 * l + d] + Fl[d];
+        const double Fl = 2.0 * double(rl) * (Ud[d] - U[d]);
+        a.mF[3 * l + d] = Fl;
+        mFr[3 * l + d] = R(Fl);
+        a.mFacc[3 * l + d] = a.pass == 0 ? Fl : a.mFacc[3 * l + d] + Fl;
     }
 }
 
-// spread F(x) += F_l delta dV_l (one thread per stencil node)
+// generic spreading with global atomics (large particles only)
+template <typename R>
 __global__ void ibm_spread_kernel(IbmArgs a) {
     const long long l = (long long)blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
     if (l >= a.nm) return;
     const int k = threadIdx.x & 63;
     const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
-    const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
-    const int b0 = (int)floor(X0) - 1, b1 = (int)floor(X1) - 1, b2 = (int)floor(X2) - 1;
-    const double wgt3 = peskin((double)(b0 + kx) - X0) * peskin((double)(b1 + ky) - X1) * peskin((double)(b2 + kz) - X2);
-    const double sc = wgt3 * a.mdV[l];
+    const R *E = (const R *)a.mE + 3 * l;
+    const int b0 = a.mB[3 * l], b1 = a.mB[3 * l + 1], b2 = a.mB[3 * l + 2];
+    const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) * peskin_r<R>(R(kz - 1) - E[2]) *
+                R(a.mdV[l]);
     const long long c = (long long)pwrap(b0 + kx, a.nx) +
                         (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
     const int s = a.aux[c];
     if (s < 0 || s >= a.max_sites) return;
-    atomicAdd(a.sup_Fp + 3 * s, a.mF[3 * l] * sc);
-    atomicAdd(a.sup_Fp + 3 * s + 1, a.mF[3 * l + 1] * sc);
-    atomicAdd(a.sup_Fp + 3 * s + 2, a.mF[3 * l + 2] * sc);
+    const R *mFr = (const R *)a.mFr;
+    R *Fp = (R *)a.sup_Fp;
+    atomicAdd(Fp + 3 * s, mFr[3 * l] * w);
+    atomicAdd(Fp + 3 * s + 1, mFr[3 * l + 1] * w);
+    atomicAdd(Fp + 3 * s + 2, mFr[3 * l + 2] * w);
 }
 
 // u* += F/(2 rho); accumulate the IBM force; clear the pass buffer
+template <typename R>
 __global__ void ibm_update_kernel(IbmArgs a) {
     const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
+    R *ru = (R *)a.sup_ru, *sF = (R *)a.sup_F, *Fp = (R *)a.sup_Fp;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
-        const double ir = 0.5 / a.sup_rho[s];
+        const R ir = R(0.5) / ru[4 * s];
         for (int d = 0; d < 3; d++) {
-            const double f = a.sup_Fp[3 * s + d];
-            a.sup_u[3 * s + d] += f * ir;
-            a.sup_F[3 * s + d] = a.pass == 0 ? f : a.sup_F[3 * s + d] + f;
-            a.sup_Fp[3 * s + d] = 0.0;
+            const R f = Fp[3 * s + d];
+            ru[4 * s + 1 + d] += f * ir;
+            sF[3 * s + d] = a.pass == 0 ? f : sF[3 * s + d] + f;
+            Fp[3 * s + d] = R(0);
         }
     }
 }
 
-cudaError_t launch_ibm_passes(Ctx &c) {
-    IbmArgs a{c.mX, c.mdV, c.mpid, c.mUs, c.mF, c.mFacc, c.aux, c.sup_rho, c.sup_u, c.sup_F, c.sup_Fp,
+// Pipe wall: the ring of markers is the same in every z plane and sits at
+// integer z, so the z weights of the 4-point kernel are the constants
+// phi(0) = 1/2, phi(+-1) = 1/4 (phi(+-2) = 0). Each support cell gathers
+// from a fixed list of ring markers of its (x, y) column in the planes
+// z-1, z, z+1 -- no atomics, fixed order -- and applies the u* update.
+struct PipeSpreadArgs {
+    const int *site_cell;
+    const int *xy_start, *xy_j;
+    const double *xy_w;
+    const void *mFr;
+    void *sup_ru, *sup_F;
+    const long long *counts;
+    long long max_sites;
+    int nx, ny, nz, nc;
+    double dV;
+    int pass;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) ibm_spread_pipe_kernel(PipeSpreadArgs a) {
+    const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
+    const R *mFr = (const R *)a.mFr;
+    R *ru = (R *)a.sup_ru, *sF = (R *)a.sup_F;
+    const int nxy = a.nx * a.ny;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (long long)gridDim.x * blockDim.x) {
+        const int c = a.site_cell[s];
+        const int z = c / nxy, xy = c - z * nxy;
+        const int j0 = a.xy_start[xy], j1 = a.xy_start[xy + 1];
+        R F0 = 0, F1 = 0, F2 = 0;
+        for (int dz = -1; dz <= 1; dz++) {
+            int zm = z - dz;
+            zm = zm < 0 ? zm + a.nz : (zm >= a.nz ? zm - a.nz : zm);
+            const R wz = R(dz == 0 ? 0.5 : 0.25) * R(a.dV);
+            const R *Fp = mFr + 3 * (long long)zm * a.nc;
+            for (int k = j0; k < j1; k++) {
+                const R w = R(a.xy_w[k]) * wz;
+                const int j = a.xy_j[k];
+                F0 += Fp[3 * j] * w;
+                F1 += Fp[3 * j + 1] * w;
+                F2 += Fp[3 * j + 2] * w;
+            }
+        }
+        const R ir = R(0.5) / ru[4 * s];
+        ru[4 * s + 1] += F0 * ir;
+        ru[4 * s + 2] += F1 * ir;
+        ru[4 * s + 3] += F2 * ir;
+        sF[3 * s] = a.pass == 0 ? F0 : sF[3 * s] + F0;
+        sF[3 * s + 1] = a.pass == 0 ? F1 : sF[3 * s + 1] + F1;
+        sF[3 * s + 2] = a.pass == 0 ? F2 : sF[3 * s + 2] + F2;
+    }
+}
+
+// Spheres: one block per particle accumulates the spread force of its
+// markers in a shared-memory box around the particle, then adds the box to
+// the support cells (global atomics only where boxes of nearby particles
+// overlap).
+struct ParticleSpreadArgs {
+    const double *mX, *mdV;
+    const void *mFr;
+    const int *mB;
+    const void *mE;
+    const double *X, *R;
+    const int *m_first, *aux;
+    void *sup_Fp;
+    long long max_sites;
+    int nx, ny, nz;
+    double rd;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) ibm_spread_particle_kernel(ParticleSpreadArgs a, int W) {
+    extern __shared__ __align__(16) unsigned char box_raw[];
+    R *box = (R *)box_raw;  // W^3 x 3
+    const int p = blockIdx.x;
+    const int nbox = W * W * W;
+    for (int t = threadIdx.x; t < 3 * nbox; t += blockDim.x) box[t] = R(0);
+    __syncthreads();
+    const double RL = a.R[p] - a.rd;
+    const int h = (int)ceil(RL) + 2;
+    const double Xp0 = a.X[3 * p], Xp1 = a.X[3 * p + 1], Xp2 = a.X[3 * p + 2];
+    const int o0 = (int)floor(Xp0) - h, o1 = (int)floor(Xp1) - h, o2 = (int)floor(Xp2) - h;
+    const int l0 = a.m_first[p], l1 = a.m_first[p + 1];
+    const R *mFr = (const R *)a.mFr;
+    for (long long t = threadIdx.x; t < 64LL * (l1 - l0); t += blockDim.x) {
+        const int l = l0 + (int)(t >> 6), k = (int)(t & 63);
+        const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
+        const R *E = (const R *)a.mE + 3 * l;
+        const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) *
+                    peskin_r<R>(R(kz - 1) - E[2]) * R(a.mdV[l]);
+        // box-local node index; the marker base is wrapped, so unwrap the difference
+        int i0 = a.mB[3 * l] + kx - o0, i1 = a.mB[3 * l + 1] + ky - o1, i2 = a.mB[3 * l + 2] + kz - o2;
+        i0 = i0 < -a.nx / 2 ? i0 + a.nx : (i0 >= a.nx / 2 ? i0 - a.nx : i0);
+        i1 = i1 < -a.ny / 2 ? i1 + a.ny : (i1 >= a.ny / 2 ? i1 - a.ny : i1);
+        i2 = i2 < -a.nz / 2 ? i2 + a.nz : (i2 >= a.nz / 2 ? i2 - a.nz : i2);
+        if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= W || i1 >= W || i2 >= W) continue;
+        const int bi = i0 + W * (i1 + W * i2);
+        atomicAdd(&box[3 * bi], mFr[3 * l] * w);
+        atomicAdd(&box[3 * bi + 1], mFr[3 * l + 1] * w);
+        atomicAdd(&box[3 * bi + 2], mFr[3 * l + 2] * w);
+    }
+    __syncthreads();
+    R *Fp = (R *)a.sup_Fp;
+    for (int bi = threadIdx.x; bi < nbox; bi += blockDim.x) {
+        const R f0 = box[3 * bi], f1 = box[3 * bi + 1], f2 = box[3 * bi + 2];
+        if (f0 == R(0) && f1 == R(0) && f2 == R(0)) continue;
+        const int i0 = bi % W, i1 = (bi / W) % W, i2 = bi / (W * W);
+        const long long c = (long long)pwrap(o0 + i0, a.nx) +
+                            (long long)a.nx * (pwrap(o1 + i1, a.ny) + (long long)a.ny * pwrap(o2 + i2, a.nz));
+        const int s = a.aux[c];
+        if (s < 0 || s >= a.max_sites) continue;
+        atomicAdd(Fp + 3 * s, f0);
+        atomicAdd(Fp + 3 * s + 1, f1);
+        atomicAdd(Fp + 3 * s + 2, f2);
+    }
+}
+
+template <typename R>
+static cudaError_t ibm_passes_t(Ctx &c) {
+    IbmArgs a{c.mX, c.mdV, c.mpid, c.mUs, c.mF, c.mFacc, c.mFr, c.mB, c.mE, c.aux, c.sup_ru, c.sup_F, c.sup_Fp,
               c.X, c.U, c.W, c.nm, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, 0};
     long long ns = c.nsites_hint > 0 ? c.nsites_hint : c.max_sites;
     if (ns > c.max_sites) ns = c.max_sites;
     long long ub = (ns + 255) / 256;
     if (ub < 1) ub = 1;
     if (ub > 152 * 32) ub = 152 * 32;
-    count_launch(c, G_IBM, 3 * (1 + (c.nm > 0 ? 2 : 0)));
+    const bool pipe_gather = c.has_pipe && c.nm > 0 && c.pipe_nc > 0;
+    // sphere boxes in shared memory when they fit
+    const double RLmax = c.max_radius - c.rd;
+    const int W = 2 * (int)ceil(RLmax) + 6;
+    const size_t smem = 3 * sizeof(R) * (size_t)W * W * W;
+    const bool box_spread = !c.has_pipe && c.np > 0 && smem <= 200 * 1024;
+    if (box_spread) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(ibm_spread_particle_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+            attr_set = true;
+        }
+    }
     for (int pass = 0; pass < 3; pass++) {
         a.pass = pass;
         if (c.nm > 0) {
-            ibm_interp_kernel<<<(unsigned)((c.nm + 127) / 128), 128, 0, c.stream>>>(a);
-            ibm_spread_kernel<<<(unsigned)((c.nm + 3) / 4), 256, 0, c.stream>>>(a);
+            count_launch(c, G_IBM);
+            ibm_interp_warp_kernel<R><<<(unsigned)((c.nm * 32 + 255) / 256), 256, 0, c.stream>>>(a);
         }
-        ibm_update_kernel<<<(unsigned)ub, 256, 0, c.stream>>>(a);
+        if (pipe_gather) {
+            PipeSpreadArgs ps{c.site_cell, c.pipe_xy_start, c.pipe_xy_j, c.pipe_xy_w, c.mFr, c.sup_ru,
+                              c.sup_F, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, c.pipe_nc, c.pipe_dV, pass};
+            count_launch(c, G_IBM);
+            ibm_spread_pipe_kernel<R><<<(unsigned)ub, 256, 0, c.stream>>>(ps);
+            continue;
+        }
+        if (c.nm > 0) {
+            count_launch(c, G_IBM);
+            if (box_spread) {
+                ParticleSpreadArgs pa{c.mX, c.mdV, c.mFr, c.mB, c.mE, c.X, c.R, c.m_first, c.aux, c.sup_Fp,
+                                      c.max_sites, c.nx, c.ny, c.nz, c.rd};
+                ibm_spread_particle_kernel<R><<<c.np, 256, smem, c.stream>>>(pa, W);
+            } else {
+                ibm_spread_kernel<R><<<(unsigned)((c.nm + 3) / 4), 256, 0, c.stream>>>(a);
+            }
+        }
+        count_launch(c, G_IBM);
+        ibm_update_kernel<R><<<(unsigned)ub, 256, 0, c.stream>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_passes(Ctx &c) {
+    return c.storage == LBM_F64 ? ibm_passes_t<double>(c) : ibm_passes_t<float>(c);
 }
 
 // particle force/torque: -sum_l F_l dV_l (+ moment) plus the change of the

@@ -1,16 +1,18 @@
 // Fused pull-stream + collide sweeps (the dominant kernel of every step).
 //
+// ibb_links: one thread per boundary link (x_f, l), x_f + c_l solid. It
+//   evaluates the interpolated bounce-back (Bouzidi et al. 2001 quadratic /
+//   linear, single-node fallback; Sec. 3.1, Sec. 2.1) from post-collision
+//   values and stores the result in the solid node's slot of the population
+//   that streams back into x_f -- the layer of nodes outside the wall that
+//   holds the bounced populations (Sec. 2.1) -- so the sweep below pulls it
+//   like any other population. It also records the Galilean-invariant
+//   momentum exchange of the link (Wen et al. 2014, Sec. 3.1).
 // stream_collide_bulk: one thread per cell, threads along x so that every
-// population plane is read and written in coalesced rows; the 19 loads of a
-// cell are independent and issued together. Cells that need a boundary
-// treatment are left to the compact kernels below:
-//   IBB: solid cells are skipped, boundary cells go to boundary_collide;
+//   population plane is read and written in coalesced rows; the 19 loads of
+//   a cell are independent and issued together. IBB: solid cells are skipped.
 //   IBM: support cells only store rho and u* (first half of the direct
-//        forcing, Sec. 2.1) and are collided later by ibm_collide.
-// boundary_collide: interpolated bounce-back for the missing populations of
-//   a boundary cell (Bouzidi et al. 2001 quadratic/linear, single-node
-//   fallback; Sec. 3.1), then the same collision; it also records per link
-//   the Galilean-invariant momentum exchange (Wen et al. 2014, Sec. 3.1).
+//   forcing, Sec. 2.1) and are collided later by ibm_collide.
 // ibm_collide: collides support cells with the body force plus the IBM force
 //   accumulated over the forcing passes.
 #include "lbm_internal.cuh"
@@ -20,9 +22,11 @@ namespace lbmgb {
 struct SweepArgs {
     const void *A;
     void *B;
+    const unsigned long long *seg;  // optional row segments (see stream_collide_bulk)
+    long long nseg;
     const uint8_t *flags;
     const int *aux;
-    double *sup_rho, *sup_u;
+    void *sup_ru;  // (rho, u*) per support site, arithmetic type of the storage
     unsigned *status;
     long long max_sites;
     int nx, ny, nz;
@@ -38,33 +42,78 @@ __device__ __forceinline__ void watchdog(R rho, R ux, R uy, R uz, unsigned *stat
 }
 
 // BC: 0 periodic, 1 IBB, 2 IBM
+#ifndef LBM_BULK_MINB
+#define LBM_BULK_MINB 4
+#endif
+#ifndef LBM_BULK_PERSIST
+#define LBM_BULK_PERSIST 0
+#endif
+#ifndef LBM_BULK_SPEC
+#define LBM_BULK_SPEC 0
+#endif
+
+// Work items: without a segment list, one item = one row piece of
+// blockDim.x cells. With a segment list (IBB walls whose rows have a solid
+// margin, e.g. the pipe), one warp = one segment of up to 32 consecutive
+// cells inside the fluid extent of a row, so no lanes idle on the margin.
+// The block walks its items with a grid stride and loads the flag byte of
+// its next item before pulling the current one.
 template <int S, bool SRT, int BC, bool FORCE>
-__global__ void __launch_bounds__(256) stream_collide_bulk(SweepArgs a) {
+__global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
-    const int rows = a.ny * a.nz;
-    const int row = blockIdx.x * blockDim.y + threadIdx.y;
-    if (row >= rows) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int y = row % ny, z = row / ny;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    // row offsets of the source rows (y - c_y, z - c_z)
-    const int r00 = (y + ny * z) * nx;
-    const int rM0 = (ym + ny * z) * nx, rP0 = (yp + ny * z) * nx;
-    const int r0M = (y + ny * zm) * nx, r0P = (y + ny * zp) * nx;
-    const int rMM = (ym + ny * zm) * nx, rPP = (yp + ny * zp) * nx;
-    const int rMP = (ym + ny * zp) * nx, rPM = (yp + ny * zm) * nx;
+    const bool segs = a.nseg > 0;
+    const int ipr = (nx + blockDim.x - 1) / blockDim.x;  // items per row (no segment list)
+    const int lane = threadIdx.x & 31;
+    const long long items = segs ? a.nseg : (long long)ny * nz * ipr;
+    const long long stride = segs ? (long long)gridDim.x * (blockDim.x * blockDim.y / 32) : (long long)gridDim.x * blockDim.y;
     const T *__restrict__ A = (const T *)a.A;
     T *__restrict__ B = (T *)a.B;
     const size_t N = (size_t)a.N;
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-        const int c = r00 + x;
-        uint8_t fl = 0;
-        if (BC != 0) {
-            fl = a.flags[c];
-            if (BC == 1 && (fl & (FL_SOLID | FL_BND))) continue;
+    long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
+                       : (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    auto cell_of = [&](long long item, int &x, int &row) {
+        if (segs) {
+            // segment: row (bits 0-31), first x (32-47), length (48-55)
+            const unsigned long long sg = __ldg(a.seg + item);
+            row = (int)(sg & 0xffffffffULL);
+            const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
+            x = lane < len ? x0 + lane : nx;
+        } else {
+            row = (int)(item / ipr);
+            x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
         }
+    };
+    // segments cover fluid cells only: no flag byte is needed (IBB)
+    const bool read_flags = BC != 0 && !(BC == 1 && segs);
+    uint8_t fl_next = 0;
+    if (read_flags && w < items) {
+        int x, row;
+        cell_of(w, x, row);
+        if (x < nx) fl_next = a.flags[(size_t)row * nx + x];
+    }
+    for (; w < items; w += stride) {
+        int x, row;
+        cell_of(w, x, row);
+        const uint8_t fl = fl_next;
+        if (read_flags && w + stride < items) {
+            int x2, row2;
+            cell_of(w + stride, x2, row2);
+            if (x2 < nx) fl_next = a.flags[(size_t)row2 * nx + x2];
+        }
+        if (x >= nx) continue;
+        if (!LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
+        const int y = row % ny, z = row / ny;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        // row offsets of the source rows (y - c_y, z - c_z)
+        const int r00 = (y + ny * z) * nx;
+        const int rM0 = (ym + ny * z) * nx, rP0 = (yp + ny * z) * nx;
+        const int r0M = (y + ny * zm) * nx, r0P = (y + ny * zp) * nx;
+        const int rMM = (ym + ny * zm) * nx, rPP = (yp + ny * zp) * nx;
+        const int rMP = (ym + ny * zp) * nx, rPM = (yp + ny * zm) * nx;
+        const int c = r00 + x;
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         R g[19];
         // pull: f_i(x) = f*_i(x - c_i)
@@ -87,6 +136,7 @@ __global__ void __launch_bounds__(256) stream_collide_bulk(SweepArgs a) {
         g[16] = Store<S>::ld(A + 16 * N + rPP + x);
         g[17] = Store<S>::ld(A + 17 * N + rMP + x);
         g[18] = Store<S>::ld(A + 18 * N + rPM + x);
+        if (LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
         const bool fluid = !(fl & FL_SOLID);
         if (BC == 2 && (fl & FL_SUP)) {
             // first half of direct forcing: rho and u* = (sum f c + F_ext/2)/rho
@@ -104,41 +154,35 @@ __global__ void __launch_bounds__(256) stream_collide_bulk(SweepArgs a) {
             const R rho = R(1) + drho;
             const int s = a.aux[c];
             if (s < 0 || s >= a.max_sites) continue;
-            a.sup_rho[s] = double(rho);
-            a.sup_u[3 * s + 0] = double(jx / rho);
-            a.sup_u[3 * s + 1] = double(jy / rho);
-            a.sup_u[3 * s + 2] = double(jz / rho);
+            R *ru = (R *)a.sup_ru + 4 * (size_t)s;
+            const R ir = R(1) / rho;
+            ru[0] = rho;
+            ru[1] = jx * ir;
+            ru[2] = jy * ir;
+            ru[3] = jz * ir;
             continue;
         }
         R rho, ux, uy, uz;
-        if (FORCE && fluid)
-            collide<R, true, SRT>(g, R(a.F[0]), R(a.F[1]), R(a.F[2]), a.rt, rho, ux, uy, uz);
-        else
-            collide<R, false, SRT>(g, R(0), R(0), R(0), a.rt, rho, ux, uy, uz);
+        const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
+        collide<R, FORCE, SRT>(g, fs * R(a.F[0]), fs * R(a.F[1]), fs * R(a.F[2]), a.rt, rho, ux, uy, uz);
         watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
         for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
     }
 }
 
-// ------------------------------------------------------------ IBB cells ----
-struct BoundaryArgs {
-    const void *A;
-    void *B;
-    const int *site_cell, *site_first;
-    const unsigned *site_mask;
-    const int8_t *link_scheme;
-    const int *link_pid;
+// ------------------------------------------------------------ IBB links ----
+struct LinkArgs {
+    void *A;  // post-collision populations at t; ghost slots of solid nodes are written
+    const int *link_cell, *link_pid;
+    const int8_t *link_dir, *link_scheme;
     const double *link_q;
     double *link_fin, *link_dP, *link_dT;
     const double *X, *U, *W;
-    unsigned *status;
-    const long long *counts;  // [0]: number of sites (device)
-    long long max_sites;
+    const long long *counts;  // [1]: number of links (device)
+    long long max_links;
     int nx, ny, nz;
     long long N;
-    double F[3];
-    Rates rt;
 };
 
 __device__ __forceinline__ double mimg(double d, int n) {
@@ -148,103 +192,83 @@ __device__ __forceinline__ double mimg(double d, int n) {
 }
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-template <int S, bool SRT, bool FORCE>
-__global__ void __launch_bounds__(128) boundary_collide(BoundaryArgs a) {
+template <int S>
+__global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
-    const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns;
-         s += (long long)gridDim.x * blockDim.x) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int c = a.site_cell[s];
-    const int first = a.site_first[s];
-    const unsigned mask = a.site_mask[s];
-    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-    const T *__restrict__ A = (const T *)a.A;
-    T *__restrict__ B = (T *)a.B;
+    const long long nl = a.counts[1] < a.max_links ? a.counts[1] : a.max_links;
+    T *A = (T *)a.A;
     const size_t N = (size_t)a.N;
-    R g[19];
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-        const int l = opp(i);
-        if (i > 0 && ((mask >> l) & 1u)) {
-            // link l: x_f + c_l is solid; unknown population i = opp(l)
-            const int k = first + __popc(mask & ((1u << l) - 1u));
-            const int x1 = wrap(x + cx(i), nx), y1 = wrap(y + cy(i), ny), z1 = wrap(z + cz(i), nz);
-            const int x2 = wrap(x1 + cx(i), nx), y2 = wrap(y1 + cy(i), ny), z2 = wrap(z1 + cz(i), nz);
-            const int c1 = x1 + nx * (y1 + ny * z1), c2 = x2 + nx * (y2 + ny * z2);
-            const R fl0 = Store<S>::ld(A + l * N + c);   // f*_l(x_f)
-            const R fi0 = Store<S>::ld(A + i * N + c);   // f*_i(x_f)
-            const double q = a.link_q[k];
-            const int sch = a.link_scheme[k];
-            const int pid = a.link_pid[k];
-            double uw[3] = {0.0, 0.0, 0.0};
-            if (pid >= 0) {
-                const double r0 = mimg(x + q * cx(l) - a.X[3 * pid + 0], nx);
-                const double r1 = mimg(y + q * cy(l) - a.X[3 * pid + 1], ny);
-                const double r2 = mimg(z + q * cz(l) - a.X[3 * pid + 2], nz);
-                const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
-                uw[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
-                uw[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
-                uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
-            }
-            const R D = R(6.0 * wgt(l) * (cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]));
-            const R qq = R(q);
-            R v;
-            if (sch == 0) {
-                if (qq < R(0.5)) {
-                    const R fl1 = Store<S>::ld(A + l * N + c1), fl2 = Store<S>::ld(A + l * N + c2);
-                    v = qq * (R(1) + R(2) * qq) * fl0 + (R(1) - R(4) * qq * qq) * fl1 -
-                        qq * (R(1) - R(2) * qq) * fl2 + D;
-                } else {
-                    const R fi1 = Store<S>::ld(A + i * N + c1);
-                    const R d = R(1) / (qq * (R(2) * qq + R(1)));
-                    v = d * fl0 + (R(2) * qq - R(1)) / qq * fi0 - (R(2) * qq - R(1)) / (R(2) * qq + R(1)) * fi1 +
-                        d * D;
-                }
-            } else if (sch == 1) {
-                if (qq < R(0.5)) {
-                    const R fl1 = Store<S>::ld(A + l * N + c1);
-                    v = R(2) * qq * fl0 + (R(1) - R(2) * qq) * fl1 + D;
-                } else {
-                    const R h = R(1) / (R(2) * qq);
-                    v = h * fl0 + (R(2) * qq - R(1)) * h * fi0 + h * D;
-                }
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nl;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int c = a.link_cell[k];
+        const int l = a.link_dir[k];
+        const int sch = a.link_scheme[k];
+        const int pid = a.link_pid[k];
+        const double q = a.link_q[k];
+        const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+        const int lx = cx(l), ly = cy(l), lz = cz(l);
+        // solid node x_f + c_l, and fluid nodes x_f - c_l, x_f - 2 c_l
+        const int cb = wrap(x + lx, nx) + nx * (wrap(y + ly, ny) + ny * wrap(z + lz, nz));
+        const int x1 = wrap(x - lx, nx), y1 = wrap(y - ly, ny), z1 = wrap(z - lz, nz);
+        const int c1 = x1 + nx * (y1 + ny * z1);
+        const int c2 = wrap(x1 - lx, nx) + nx * (wrap(y1 - ly, ny) + ny * wrap(z1 - lz, nz));
+        const int i = opp(l);
+        const R fl0 = Store<S>::ld(A + (size_t)l * N + c);  // f*_l(x_f), toward the wall
+        const R fi0 = Store<S>::ld(A + (size_t)i * N + c);  // f*_ibar(x_f)
+        double uw[3] = {0.0, 0.0, 0.0};
+        if (pid >= 0) {
+            const double r0 = mimg(x + q * lx - a.X[3 * pid + 0], nx);
+            const double r1 = mimg(y + q * ly - a.X[3 * pid + 1], ny);
+            const double r2 = mimg(z + q * lz - a.X[3 * pid + 2], nz);
+            const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
+            uw[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
+            uw[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
+            uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
+        }
+        // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
+        const R D = R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2]));
+        const R qq = R(q);
+        R v;
+        if (sch == 0) {
+            if (qq < R(0.5)) {
+                const R fl1 = Store<S>::ld(A + (size_t)l * N + c1), fl2 = Store<S>::ld(A + (size_t)l * N + c2);
+                v = qq * (R(1) + R(2) * qq) * fl0 + (R(1) - R(4) * qq * qq) * fl1 - qq * (R(1) - R(2) * qq) * fl2 + D;
             } else {
-                v = fl0 + D;
+                const R fi1 = Store<S>::ld(A + (size_t)i * N + c1);
+                const R d = R(1) / (qq * (R(2) * qq + R(1)));
+                v = d * fl0 + (R(2) * qq - R(1)) / qq * fi0 - (R(2) * qq - R(1)) / (R(2) * qq + R(1)) * fi1 + d * D;
             }
-            g[i] = v;
-            a.link_fin[k] = double(v);
-            if (pid >= 0) {
-                // momentum exchange on the link, unshifted f = g + w (w_l = w_i)
-                const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
-                double dP[3];
-                dP[0] = (cx(l) - uw[0]) * fo - (cx(i) - uw[0]) * fi;
-                dP[1] = (cy(l) - uw[1]) * fo - (cy(i) - uw[1]) * fi;
-                dP[2] = (cz(l) - uw[2]) * fo - (cz(i) - uw[2]) * fi;
-                const double m0 = mimg(x + 0.5 * cx(l) - a.X[3 * pid + 0], nx);
-                const double m1 = mimg(y + 0.5 * cy(l) - a.X[3 * pid + 1], ny);
-                const double m2 = mimg(z + 0.5 * cz(l) - a.X[3 * pid + 2], nz);
-                a.link_dP[3 * k + 0] = dP[0];
-                a.link_dP[3 * k + 1] = dP[1];
-                a.link_dP[3 * k + 2] = dP[2];
-                a.link_dT[3 * k + 0] = m1 * dP[2] - m2 * dP[1];
-                a.link_dT[3 * k + 1] = m2 * dP[0] - m0 * dP[2];
-                a.link_dT[3 * k + 2] = m0 * dP[1] - m1 * dP[0];
+        } else if (sch == 1) {
+            if (qq < R(0.5)) {
+                const R fl1 = Store<S>::ld(A + (size_t)l * N + c1);
+                v = R(2) * qq * fl0 + (R(1) - R(2) * qq) * fl1 + D;
+            } else {
+                const R h = R(1) / (R(2) * qq);
+                v = h * fl0 + (R(2) * qq - R(1)) * h * fi0 + h * D;
             }
         } else {
-            const int xs = wrap(x - cx(i), nx), ys = wrap(y - cy(i), ny), zs = wrap(z - cz(i), nz);
-            g[i] = Store<S>::ld(A + i * N + (xs + nx * (ys + ny * zs)));
+            v = fl0 + D;
         }
-    }
-    R rho, ux, uy, uz;
-    if (FORCE)
-        collide<R, true, SRT>(g, R(a.F[0]), R(a.F[1]), R(a.F[2]), a.rt, rho, ux, uy, uz);
-    else
-        collide<R, false, SRT>(g, R(0), R(0), R(0), a.rt, rho, ux, uy, uz);
-    watchdog(rho, ux, uy, uz, a.status);
-#pragma unroll
-    for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
+        Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
+        a.link_fin[k] = double(v);
+        if (pid >= 0) {
+            // momentum exchange with unshifted f = g + w (w_l = w_ibar)
+            const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
+            const double dP0 = (lx - uw[0]) * fo - (-lx - uw[0]) * fi;
+            const double dP1 = (ly - uw[1]) * fo - (-ly - uw[1]) * fi;
+            const double dP2 = (lz - uw[2]) * fo - (-lz - uw[2]) * fi;
+            const double m0 = mimg(x + 0.5 * lx - a.X[3 * pid + 0], nx);
+            const double m1 = mimg(y + 0.5 * ly - a.X[3 * pid + 1], ny);
+            const double m2 = mimg(z + 0.5 * lz - a.X[3 * pid + 2], nz);
+            a.link_dP[3 * k + 0] = dP0;
+            a.link_dP[3 * k + 1] = dP1;
+            a.link_dP[3 * k + 2] = dP2;
+            a.link_dT[3 * k + 0] = m1 * dP2 - m2 * dP1;
+            a.link_dT[3 * k + 1] = m2 * dP0 - m0 * dP2;
+            a.link_dT[3 * k + 2] = m0 * dP1 - m1 * dP0;
+        }
     }
 }
 
@@ -254,7 +278,7 @@ struct IbmCollideArgs {
     void *B;
     const int *site_cell;
     const uint8_t *flags;
-    const double *sup_F;
+    const void *sup_F;  // arithmetic type of the storage
     unsigned *status;
     const long long *counts;
     long long max_sites;
@@ -284,9 +308,11 @@ __global__ void __launch_bounds__(128) ibm_collide(IbmCollideArgs a) {
         g[i] = Store<S>::ld(A + i * N + (xs + nx * (ys + ny * zs)));
     }
     const bool fluid = !(a.flags[c] & FL_SOLID);
-    const R Fx = R((fluid ? a.F[0] : 0.0) + a.sup_F[3 * s + 0]);
-    const R Fy = R((fluid ? a.F[1] : 0.0) + a.sup_F[3 * s + 1]);
-    const R Fz = R((fluid ? a.F[2] : 0.0) + a.sup_F[3 * s + 2]);
+    const R *sF = (const R *)a.sup_F;
+    const R fs = fluid ? R(1) : R(0);
+    const R Fx = fs * R(a.F[0]) + sF[3 * s + 0];
+    const R Fy = fs * R(a.F[1]) + sF[3 * s + 1];
+    const R Fz = fs * R(a.F[2]) + sF[3 * s + 2];
     R rho, ux, uy, uz;
     collide<R, true, SRT>(g, Fx, Fy, Fz, a.rt, rho, ux, uy, uz);
     watchdog(rho, ux, uy, uz, a.status);
@@ -315,8 +341,7 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     a.B = c.fB;
     a.flags = c.flags;
     a.aux = c.aux;
-    a.sup_rho = c.sup_rho;
-    a.sup_u = c.sup_u;
+    a.sup_ru = c.sup_ru;
     a.status = c.d_status;
     a.max_sites = c.max_sites;
     a.nx = c.nx;
@@ -325,12 +350,36 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     a.N = c.N;
     for (int d = 0; d < 3; d++) a.F[d] = c.F[d];
     a.rt = c.rt;
+    const bool segs = BC == 1 && c.nseg > 0;
+    a.seg = c.seg;
+    a.nseg = segs ? c.nseg : 0;
     int bx = ((c.nx + 31) / 32) * 32;
     if (bx > 256) bx = 256;
     int by = 256 / bx;
     if (by < 1) by = 1;
-    const int rows = c.ny * c.nz;
-    dim3 block(bx, by), grid((rows + by - 1) / by);
+    if (segs) {
+        bx = 256;  // 8 warps, one segment each
+        by = 1;
+    }
+    const long long items = segs ? c.nseg : (long long)c.ny * c.nz * ((c.nx + bx - 1) / bx);
+    long long nb = segs ? (items + 7) / 8 : (items + by - 1) / by;
+    if (LBM_BULK_PERSIST) {
+        // persistent grid: as many blocks as fit on the device at once
+        static int resident[4][2][3][2];
+        int &res = resident[S][SRT][BC][force ? 1 : 0];
+        if (res == 0) {
+            int per_sm = 0, dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (force)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true>, bx * by, 0);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false>, bx * by, 0);
+            res = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        }
+        if (nb > res) nb = res;
+    }
+    dim3 block(bx, by), grid((unsigned)nb);
     count_launch(c, G_BULK);
     if (force)
         stream_collide_bulk<S, SRT, BC, true><<<grid, block, 0, c.stream>>>(a);
@@ -364,53 +413,26 @@ cudaError_t launch_stream_collide(Ctx &c, int bc) {
 }
 
 template <int S>
-static cudaError_t launch_boundary_s(Ctx &c) {
-    if (c.max_sites == 0) return cudaSuccess;
-    BoundaryArgs a;
-    a.A = c.fA;
-    a.B = c.fB;
-    a.site_cell = c.site_cell;
-    a.site_first = c.site_first;
-    a.site_mask = c.site_mask;
-    a.link_scheme = c.link_scheme;
-    a.link_pid = c.link_pid;
-    a.link_q = c.link_q;
-    a.link_fin = c.link_fin;
-    a.link_dP = c.link_dP;
-    a.link_dT = c.link_dT;
-    a.X = c.X;
-    a.U = c.U;
-    a.W = c.W;
-    a.status = c.d_status;
-    a.counts = c.d_counts;
-    a.max_sites = c.max_sites;
-    a.nx = c.nx;
-    a.ny = c.ny;
-    a.nz = c.nz;
-    a.N = c.N;
-    for (int d = 0; d < 3; d++) a.F[d] = c.F[d];
-    a.rt = c.rt;
-    const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
-    const int tb = 128;
-    const unsigned nb = site_grid(c, tb);
-    const bool srt = c.rates == LBM_RATES_SRT;
+static cudaError_t launch_links_s(Ctx &c) {
+    if (c.max_links == 0) return cudaSuccess;
+    LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_fin, c.link_dP, c.link_dT,
+               c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N};
+    long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
+    if (n > c.max_links) n = c.max_links;
+    long long nb = (n + 255) / 256;
+    if (nb < 1) nb = 1;
+    if (nb > 152LL * 64) nb = 152LL * 64;
     count_launch(c, G_BND);
-    if (srt) {
-        if (force) boundary_collide<S, true, true><<<nb, tb, 0, c.stream>>>(a);
-        else boundary_collide<S, true, false><<<nb, tb, 0, c.stream>>>(a);
-    } else {
-        if (force) boundary_collide<S, false, true><<<nb, tb, 0, c.stream>>>(a);
-        else boundary_collide<S, false, false><<<nb, tb, 0, c.stream>>>(a);
-    }
+    ibb_links<S><<<(unsigned)nb, 256, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_boundary_collide(Ctx &c) {
+cudaError_t launch_ibb_links(Ctx &c) {
     switch (c.storage) {
-    case LBM_F64: return launch_boundary_s<LBM_F64>(c);
-    case LBM_F32: return launch_boundary_s<LBM_F32>(c);
-    case LBM_F16S: return launch_boundary_s<LBM_F16S>(c);
-    default: return launch_boundary_s<LBM_BF16S>(c);
+    case LBM_F64: return launch_links_s<LBM_F64>(c);
+    case LBM_F32: return launch_links_s<LBM_F32>(c);
+    case LBM_F16S: return launch_links_s<LBM_F16S>(c);
+    default: return launch_links_s<LBM_BF16S>(c);
     }
 }
 
