@@ -123,6 +123,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps, int bc);
 
 #define LBM_STATS_UNMASK 1   /* IBM: statistics on the raw virtual fluid inside particles */
 #define LBM_STATS_BINS 4     /* radial profiles around particles (Sec. 3.2) */
+#define LBM_STATS_CLOSURE 8  /* near-surface gradients from the learned closure (lbm_closure_set_weights) */
 #define LBM_NBINS 40
 
 typedef struct {
@@ -186,6 +187,64 @@ typedef struct {
     long long total_launches;         /* every kernel launched since create */
 } lbm_profile_t;
 lbm_status lbm_profile(lbm_ctx *ctx, int enable, lbm_profile_t *out);
+
+/* ---------------------------------------------------------------------
+ * Learned near-surface gradient closure. The paper finds that IBM cannot
+ * resolve the velocity gradients inside its diffused interface, so the
+ * local dissipation near particle surfaces comes out too low (Sec. 3.2,
+ * Sec. 4). A perceptron 85 -> 64 -> 64 -> 64 (ReLU) -> 9 maps the IBM
+ * velocity stencil around a near-surface node to its 9 velocity
+ * gradients; it is trained on pairs produced by the method itself (IBM
+ * features, IBB gradients from the same initial state). Tensor cores:
+ * BF16 operands, FP32 accumulation, FP32 master weights.
+ * Parameter vector (FP32, 14409 values): W1 (85x64, [in][out]), b1 (64),
+ * W2 (64x64), b2, W3 (64x64), b3, W4 (64x9), b4 (9).
+ * Features per node (85): u - u_rb at the 27 nodes x + (dx,dy,dz),
+ * dz, dy, dx in -1..1 (dz outermost), 3 components each, divided by
+ * u_scale; the distance to the nearest particle surface (lattice units);
+ * u - u_rb at the node again (3). u_rb: rigid-body velocity of the nearest
+ * particle. Outputs: du_a/dx_b at index 3a + b, times g_scale.
+ * --------------------------------------------------------------------- */
+#define LBM_MLP_NPARAM 14409
+
+/* Device workspace for the lbm_mlp_* calls (caller-owned, 256-byte aligned). */
+size_t lbm_mlp_workspace_bytes(void);
+int lbm_mlp_num_params(void);
+
+/* Y (n x 9) = network(X (n x 85)) for FP32 device arrays; w_dev: the FP32
+ * parameter vector on the device. Asynchronous on `stream`. */
+lbm_status lbm_mlp_forward(const float *X_dev, long long n, const float *w_dev, float *Y_dev, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/* Mean squared error over the n samples and 9 outputs and its gradient
+ * with respect to the parameters (grad_dev: 14409 floats). Synchronous when
+ * loss != NULL. */
+lbm_status lbm_mlp_loss_grad(const float *X_dev, const float *T_dev, long long n, const float *w_dev,
+                             float *grad_dev, double *loss, void *ws, size_t ws_bytes, void *stream);
+
+/* Adam (lr, beta = 0.9/0.999, eps = 1e-8) over consecutive mini-batches of
+ * the given (pre-shuffled) samples, `epochs` times; w_dev is updated in
+ * place. last_epoch_loss (nullable) receives the mean loss of the last
+ * epoch's batches (evaluated before each update). */
+lbm_status lbm_mlp_train(const float *X_dev, const float *T_dev, long long n, int epochs, int batch, double lr,
+                         float *w_dev, void *ws, size_t ws_bytes, void *stream, double *last_epoch_loss);
+
+/* Features of the near-surface fluid nodes (distance to the nearest
+ * surface in (0, 2]) of the current state into X_dev (capacity x 85) and
+ * their cell indices into cells_dev; *n receives the count (order not
+ * fixed). LBM_ENOMEM when more than `capacity` nodes exist. Syncs. */
+lbm_status lbm_closure_samples(lbm_ctx *ctx, double u_scale, float *X_dev, int *cells_dev, long long capacity,
+                               long long *n);
+
+/* Central-difference gradients of the current (rigid-body masked)
+ * velocity at the given cells, times g_scale, into T_dev (n x 9); NaN where
+ * the cell is solid in this state. Syncs. */
+lbm_status lbm_closure_targets(lbm_ctx *ctx, const int *cells_dev, long long n, double g_scale, float *T_dev);
+
+/* Weights (host FP32, 14409) and scales used by lbm_stats(LBM_STATS_CLOSURE):
+ * near-surface nodes then take their gradients, hence their dissipation,
+ * from the network. Needs max_particles > 0. */
+lbm_status lbm_closure_set_weights(lbm_ctx *ctx, const float *w_host, int n, double u_scale, double g_scale);
 
 /* Kinetic energy and dissipation of a velocity field already in device
  * memory, computed without allocating anything. The paper has no

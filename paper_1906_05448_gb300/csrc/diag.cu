@@ -161,12 +161,12 @@ __device__ __forceinline__ double cell_eps(const double *u, int x, int y, int z,
 
 // partials: ke, eps over all cells; ke, eps, count over fluid cells; pipe bulk
 __global__ void __launch_bounds__(SB) energy_kernel(const double *u, const uint8_t *flags, int nx, int ny, int nz,
-                                                    long long N, double nu, int pipe, double *part) {
+                                                    long long N, double nu, int pipe, double *part, const float *eps_o) {
     __shared__ double sh[7 * SB];
     double v[7] = {0, 0, 0, 0, 0, 0, 0};
     for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)SNB * SB) {
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
-        const double e = cell_eps(u, x, y, z, nx, ny, nz, N, nu);
+        const double e = (eps_o && eps_o[c] >= 0.f) ? (double)eps_o[c] : cell_eps(u, x, y, z, nx, ny, nz, N, nu);
         const double k = 0.5 * (u[c] * u[c] + u[N + c] * u[N + c] + u[2 * N + c] * u[2 * N + c]);
         v[0] += k;
         v[1] += e;
@@ -214,7 +214,7 @@ constexpr int NBIN = LBM_NBINS;
 
 __global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t *flags, const int *near_pid,
                                                   const double *X, const double *R, int nx, int ny, int nz,
-                                                  long long N, double nu, double *bpart) {
+                                                  long long N, double nu, double *bpart, const float *eps_o) {
     __shared__ double sk[NBIN], se[NBIN], sc[NBIN];
     for (int b = threadIdx.x; b < NBIN; b += SB) sk[b] = se[b] = sc[b] = 0.0;
     __syncthreads();
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t
         if (b < 0 || b >= NBIN) continue;
         const double k = 0.5 * (u[c] * u[c] + u[N + c] * u[N + c] + u[2 * N + c] * u[2 * N + c]);
         atomicAdd(&sk[b], k);
-        atomicAdd(&se[b], cell_eps(u, x, y, z, nx, ny, nz, N, nu));
+        atomicAdd(&se[b], (eps_o && eps_o[c] >= 0.f) ? (double)eps_o[c] : cell_eps(u, x, y, z, nx, ny, nz, N, nu));
         atomicAdd(&sc[b], 1.0);
     }
     __syncthreads();
@@ -254,6 +254,129 @@ __global__ void fill_i32(int *p, int v, long long n) {
     if (i < n) p[i] = v;
 }
 
+// ------------------------------------------------------ learned closure --
+// Near-surface fluid nodes (distance to the nearest particle surface in
+// (0, 2]) and their 85 features: the 27-point stencil of u - u_rb (u_rb the
+// rigid-body velocity of the nearest particle), scaled by 1/u_scale, the
+// signed distance / h, and u - u_rb at the node.
+__global__ void closure_sample_kernel(const double *u, const uint8_t *flags, const int *near_pid, const double *X,
+                                      const double *U, const double *W, const double *R, int nx, int ny, int nz,
+                                      long long N, double inv_us, float *feat, int *cells, long long *count,
+                                      long long cap) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        if (flags[c] & FL_SOLID) continue;
+        const int p = near_pid[c];
+        if (p == NO_OWNER) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double rx = dmimg(x - X[3 * p], nx), ry = dmimg(y - X[3 * p + 1], ny), rz = dmimg(z - X[3 * p + 2], nz);
+        const double d = sqrt(rx * rx + ry * ry + rz * rz) - R[p];
+        if (!(d > 0.0 && d <= 2.0)) continue;
+        const long long k = (long long)atomicAdd((unsigned long long *)count, 1ULL);
+        if (k >= cap) continue;
+        cells[k] = (int)c;
+        float *f = feat + k * 85;
+        int j = 0;
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const long long q = (long long)dwrap(x + dx, nx) + (long long)nx * (dwrap(y + dy, ny) + (long long)ny * dwrap(z + dz, nz));
+                    const double sx = rx + dx, sy = ry + dy, sz = rz + dz;
+                    const double ub0 = U[3 * p] + (W[3 * p + 1] * sz - W[3 * p + 2] * sy);
+                    const double ub1 = U[3 * p + 1] + (W[3 * p + 2] * sx - W[3 * p] * sz);
+                    const double ub2 = U[3 * p + 2] + (W[3 * p] * sy - W[3 * p + 1] * sx);
+                    f[j++] = (float)((u[q] - ub0) * inv_us);
+                    f[j++] = (float)((u[N + q] - ub1) * inv_us);
+                    f[j++] = (float)((u[2 * N + q] - ub2) * inv_us);
+                }
+        f[81] = (float)d;
+        f[82] = f[3 * 13];
+        f[83] = f[3 * 13 + 1];
+        f[84] = f[3 * 13 + 2];
+    }
+}
+
+// 9 velocity gradients du_a/dx_b (central differences) at listed cells,
+// scaled by g_scale; NaN where the cell is solid in this state
+__global__ void closure_target_kernel(const double *u, const uint8_t *flags, const int *cells, long long n, int nx,
+                                      int ny, int nz, long long N, double gs, float *T) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long c = cells[k];
+    float *t = T + k * 9;
+    if (flags[c] & FL_SOLID) {
+        for (int e = 0; e < 9; e++) t[e] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+    const long long nb[3][2] = {{dwrap(x + 1, nx) + (long long)nx * (y + (long long)ny * z), dwrap(x - 1, nx) + (long long)nx * (y + (long long)ny * z)},
+                                {x + (long long)nx * (dwrap(y + 1, ny) + (long long)ny * z), x + (long long)nx * (dwrap(y - 1, ny) + (long long)ny * z)},
+                                {x + (long long)nx * (y + (long long)ny * dwrap(z + 1, nz)), x + (long long)nx * (y + (long long)ny * dwrap(z - 1, nz))}};
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) t[3 * a + b] = (float)(0.5 * (u[a * N + nb[b][0]] - u[a * N + nb[b][1]]) * gs);
+}
+
+// dissipation 2 nu s_ij s_ij from predicted gradients (scaled by g_scale)
+__global__ void closure_eps_kernel(const float *Y, const int *cells, long long n, double inv_gs, double nu,
+                                   float *eps_o) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double g[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) g[a][b] = (double)Y[k * 9 + 3 * a + b] * inv_gs;
+    double ss = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            const double sab = 0.5 * (g[a][b] + g[b][a]);
+            ss += sab * sab;
+        }
+    eps_o[cells[k]] = (float)(2.0 * nu * ss);
+}
+
+__global__ void fill_f32(float *p, float v, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cudaError_t mlp_forward_device(const float *X, long long n, const float *w, void *pk_ws, float *Y, cudaStream_t s);
+
+static void near_surface(Ctx &c, const unsigned nb) {
+    count_launch(c, G_STATS, 4);
+    fill_u64<<<nb, 256, 0, c.stream>>>(c.near_key, ~0ULL, c.N);
+    fill_i32<<<nb, 256, 0, c.stream>>>(c.near_pid, NO_OWNER, c.N);
+    near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 0, c.near_pid);
+    near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 1, c.near_pid);
+}
+
+cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out) {
+    cudaError_t e;
+    if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+    near_surface(c, nb);
+    count_launch(c, G_STATS);
+    if ((e = cudaMemsetAsync(c.d_counts + 3, 0, sizeof(long long), c.stream)) != cudaSuccess) return e;
+    closure_sample_kernel<<<1024, 256, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.U, c.W, c.R, c.nx, c.ny, c.nz,
+                                                      c.N, 1.0 / u_scale, X, cells, c.d_counts + 3, cap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    long long n = 0;
+    if ((e = cudaMemcpyAsync(&n, c.d_counts + 3, sizeof(long long), cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    *n_out = n;
+    return cudaSuccess;
+}
+
+cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scale, float *T) {
+    cudaError_t e;
+    if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((c.N + 255) / 256);
+    count_launch(c, G_STATS, 2);
+    mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
+    if (n > 0)
+        closure_target_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(c.u_f, c.flags, cells, n, c.nx, c.ny,
+                                                                              c.nz, c.N, g_scale, T);
+    return cudaGetLastError();
+}
+
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     cudaError_t e;
     memset(o, 0, sizeof(*o));
@@ -264,18 +387,38 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     mass_kernel<<<SNB, SB, 0, c.stream>>>(c.rho_f, c.u_f, c.flags, c.N, ibb, c.partials);
     const bool mask = !(ibm && (flags & LBM_STATS_UNMASK));
     const unsigned nb = (unsigned)((c.N + 255) / 256);
-    if (mask) mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
     const double nu = (c.tau - 0.5) / 3.0;
-    energy_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.nx, c.ny, c.nz, c.N, nu, c.has_pipe, c.partials);
     const bool bins = (flags & LBM_STATS_BINS) && c.np > 0;
+    const bool closure = (flags & LBM_STATS_CLOSURE) && c.np > 0 && c.cl_ready && c.max_cl > 0;
+    const float *eps_o = nullptr;
+    if (bins || closure) near_surface(c, nb);
+    if (closure) {
+        // learned gradients at the near-surface nodes (unmasked velocity in)
+        count_launch(c, G_STATS, 4);
+        fill_f32<<<nb, 256, 0, c.stream>>>(c.cl_eps, -1.f, c.N);
+        if ((e = cudaMemsetAsync(c.d_counts + 3, 0, sizeof(long long), c.stream)) != cudaSuccess) return e;
+        closure_sample_kernel<<<1024, 256, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.U, c.W, c.R, c.nx, c.ny,
+                                                          c.nz, c.N, 1.0 / c.cl_uscale, c.cl_X, c.cl_cells,
+                                                          c.d_counts + 3, c.max_cl);
+        long long ncl = 0;
+        if ((e = cudaMemcpyAsync(&ncl, c.d_counts + 3, sizeof(long long), cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+        if (ncl > c.max_cl) ncl = c.max_cl;
+        if ((e = mlp_forward_device(c.cl_X, ncl, c.cl_w, c.cl_pk, c.cl_Y, c.stream)) != cudaSuccess) return e;
+        if (ncl > 0)
+            closure_eps_kernel<<<(unsigned)((ncl + 255) / 256), 256, 0, c.stream>>>(c.cl_Y, c.cl_cells, ncl,
+                                                                                 1.0 / c.cl_gscale, nu, c.cl_eps);
+        eps_o = c.cl_eps;
+        c.cl_last_n = ncl;
+    }
+    if (mask) mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
+    energy_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.nx, c.ny, c.nz, c.N, nu, c.has_pipe, c.partials, eps_o);
     double *bpart = c.partials + SNB * NP;
     if (bins) {
-        count_launch(c, G_STATS, 5);
-        fill_u64<<<nb, 256, 0, c.stream>>>(c.near_key, ~0ULL, c.N);
-        fill_i32<<<nb, 256, 0, c.stream>>>(c.near_pid, NO_OWNER, c.N);
-        near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 0, c.near_pid);
-        near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 1, c.near_pid);
-        bins_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N, nu, bpart);
+        count_launch(c, G_STATS);
+        bins_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N, nu, bpart,
+                                              eps_o);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::vector<double> part((size_t)SNB * NP), bp(bins ? (size_t)SNB * 3 * NBIN : 0);

@@ -41,6 +41,8 @@ struct Plan {
     size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
     size_t mX, mUnit, mdV, mUs, mF, mFacc, mFr, mB, mE, mpid, mfirst;
     size_t rho_f, u_f, partials, near_key, near_pid;
+    size_t cl_w, cl_pk, cl_X, cl_Y, cl_cells, cl_eps;
+    long long max_cl;
     size_t total;
 };
 
@@ -124,6 +126,13 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.partials = L.take(8 * stats_partials_doubles());
     P.near_key = L.take(8 * n);
     P.near_pid = L.take(4 * n);
+    P.max_cl = P.max_np > 0 ? 1500LL * P.max_np : 0;
+    P.cl_w = L.take(4 * 14409);
+    P.cl_pk = L.take(mlp_pack_bytes());
+    P.cl_X = L.take(4 * 85 * (size_t)P.max_cl);
+    P.cl_Y = L.take(4 * 9 * (size_t)P.max_cl);
+    P.cl_cells = L.take(4 * (size_t)P.max_cl);
+    P.cl_eps = L.take(P.max_cl > 0 ? 4 * n : 0);
     P.total = L.off;
     return true;
 }
@@ -541,6 +550,13 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.partials = (double *)(b + P.partials);
     c.near_key = (unsigned long long *)(b + P.near_key);
     c.near_pid = (int *)(b + P.near_pid);
+    c.cl_w = (float *)(b + P.cl_w);
+    c.cl_pk = b + P.cl_pk;
+    c.cl_X = (float *)(b + P.cl_X);
+    c.cl_Y = (float *)(b + P.cl_Y);
+    c.cl_cells = (int *)(b + P.cl_cells);
+    c.cl_eps = (float *)(b + P.cl_eps);
+    c.max_cl = P.max_cl;
     c.armed_bc = -1;
     c.pipe_cx = 0.5 * (c.nx - 1);
     c.pipe_cy = 0.5 * (c.ny - 1);
@@ -880,6 +896,39 @@ lbm_status lbm_get_markers(lbm_ctx *h, long long capacity, double *X, double *F,
     if (pid) CK(cudaMemcpyAsync(pid, c.mpid, 4 * c.nm, cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     return s;
+}
+
+lbm_status lbm_closure_set_weights(lbm_ctx *h, const float *w_host, int n, double u_scale, double g_scale) {
+    CTX_CHECK(h);
+    if (!w_host || n != 14409 || !(u_scale > 0) || !(g_scale > 0)) return fail(c, LBM_EINVAL, "bad closure weights");
+    if (c.max_cl == 0) return fail(c, LBM_EUNSUPPORTED, "closure needs max_particles > 0");
+    CK(cudaMemcpy(c.cl_w, w_host, sizeof(float) * n, cudaMemcpyHostToDevice));
+    c.cl_uscale = u_scale;
+    c.cl_gscale = g_scale;
+    c.cl_ready = 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_samples(lbm_ctx *h, double u_scale, float *X_dev, int *cells_dev, long long capacity,
+                               long long *n) {
+    CTX_CHECK(h);
+    if (!X_dev || !cells_dev || !n || capacity < 0 || !(u_scale > 0)) return fail(c, LBM_EINVAL, "bad arguments");
+    if (c.np == 0) return fail(c, LBM_ESTATE, "no particles");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK) return s;
+    CK(closure_samples(c, u_scale, X_dev, cells_dev, capacity, n));
+    if (*n > capacity) return fail(c, LBM_ENOMEM, "%lld near-surface nodes exceed capacity %lld", *n, capacity);
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_targets(lbm_ctx *h, const int *cells_dev, long long n, double g_scale, float *T_dev) {
+    CTX_CHECK(h);
+    if ((n > 0 && (!cells_dev || !T_dev)) || n < 0 || !(g_scale > 0)) return fail(c, LBM_EINVAL, "bad arguments");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK) return s;
+    CK(closure_targets(c, cells_dev, n, g_scale, T_dev));
+    CK(cudaStreamSynchronize(c.stream));
+    return LBM_OK;
 }
 
 lbm_status lbm_profile(lbm_ctx *h, int enable, lbm_profile_t *out) {

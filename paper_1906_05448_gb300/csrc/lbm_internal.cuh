@@ -300,6 +300,13 @@ struct Ctx {
     bool broken;
     bool initialised_pops;
     char err[256];
+    // learned closure: weights, scales and sample buffers
+    float *cl_w, *cl_X, *cl_Y, *cl_eps;
+    int *cl_cells;
+    void *cl_pk;
+    long long max_cl, cl_last_n;
+    double cl_uscale, cl_gscale;
+    int cl_ready;
     // profiling
     long long launches;                 // every kernel launched
     long long group_launches[LBM_NGROUPS];
@@ -344,4 +351,7 @@ cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only);
 cudaError_t launch_ibm_rigid_overwrite(Ctx &c);
 cudaError_t launch_macro(Ctx &c, int mask_mode);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);
+cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out);
+cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scale, float *T);
+size_t mlp_pack_bytes();
 }  // namespace lbmgb

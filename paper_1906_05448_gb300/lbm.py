@@ -19,7 +19,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 BC_NONE, BC_IBB, BC_IBM_U, BC_IBM_B = 0, 1, 2, 3
 F64, F32, F16S, BF16S = 0, 1, 2, 3
 RATES_SRT, RATES_DHUMIERES = 0, 1
-STATS_UNMASK, STATS_BINS = 1, 4
+STATS_UNMASK, STATS_BINS, STATS_CLOSURE = 1, 4, 8
 FIELD_RHO, FIELD_U, FIELD_POPS, FIELD_FLAGS, FIELD_IBM_FORCE = 0, 1, 2, 3, 4
 NBINS = 40
 
@@ -31,6 +31,8 @@ EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_init_velocity", "lbm_set_populations", "lbm_set_pipe",
     "lbm_add_spheres", "lbm_step", "lbm_stats", "lbm_get_field", "lbm_num_links", "lbm_get_links",
     "lbm_get_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile",
+    "lbm_mlp_workspace_bytes", "lbm_mlp_num_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train",
+    "lbm_closure_samples", "lbm_closure_targets", "lbm_closure_set_weights",
     "lbm_field_energy_noalloc", "lbm_field_energy_noalloc_max_cells", "lbm_last_error",
     "lbm_status_string", "lbm_destroy",
 ]
@@ -116,6 +118,15 @@ def load(build_if_missing: bool = False):
         "lbm_num_markers": (ctypes.c_int, [_P, _L]),
         "lbm_get_markers": (ctypes.c_int, [_P, ctypes.c_longlong, _D, _D, _D, _I]),
         "lbm_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Profile)]),
+        "lbm_mlp_workspace_bytes": (ctypes.c_size_t, []),
+        "lbm_mlp_num_params": (ctypes.c_int, []),
+        "lbm_mlp_forward": (ctypes.c_int, [_P, ctypes.c_longlong, _P, _P, _P, ctypes.c_size_t, _P]),
+        "lbm_mlp_loss_grad": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, _P, _D, _P, ctypes.c_size_t, _P]),
+        "lbm_mlp_train": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
+                                         _P, ctypes.c_size_t, _P, _D]),
+        "lbm_closure_samples": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, ctypes.c_longlong, _L]),
+        "lbm_closure_targets": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_double, _P]),
+        "lbm_closure_set_weights": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
         "lbm_field_energy_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                     _P, _P]),
         "lbm_field_energy_noalloc_max_cells": (ctypes.c_longlong, []),
@@ -278,6 +289,31 @@ class Lattice:
     def profile_enable(self, on=True):
         self._check(self.L.lbm_profile(self.h, 1 if on else 0, None))
 
+    # -- learned closure
+    def closure_samples(self, u_scale, capacity):
+        """Features (n, 85) and cells (n,) of the near-surface nodes, as torch
+        CUDA tensors (rows in no fixed order)."""
+        import torch
+        X = torch.empty((capacity, 85), dtype=torch.float32, device=self.workspace.device)
+        cells = torch.empty(capacity, dtype=torch.int32, device=self.workspace.device)
+        n = ctypes.c_longlong()
+        self._check(self.L.lbm_closure_samples(self.h, float(u_scale), ctypes.c_void_p(X.data_ptr()),
+                                               ctypes.c_void_p(cells.data_ptr()), capacity, ctypes.byref(n)))
+        return X[: n.value], cells[: n.value]
+
+    def closure_targets(self, cells, g_scale):
+        import torch
+        cells = cells.contiguous()
+        T = torch.empty((cells.numel(), 9), dtype=torch.float32, device=self.workspace.device)
+        self._check(self.L.lbm_closure_targets(self.h, ctypes.c_void_p(cells.data_ptr()), cells.numel(),
+                                               float(g_scale), ctypes.c_void_p(T.data_ptr())))
+        return T
+
+    def closure_set_weights(self, w, u_scale, g_scale):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.L.lbm_closure_set_weights(self.h, w.ctypes.data_as(_P), w.size, float(u_scale),
+                                                   float(g_scale)))
+
     def markers(self) -> dict:
         n = ctypes.c_longlong()
         self._check(self.L.lbm_num_markers(self.h, ctypes.byref(n)))
@@ -289,3 +325,67 @@ class Lattice:
         if n:
             self._check(self.L.lbm_get_markers(self.h, n, _dp(X), _dp(F), _dp(dV), pid.ctypes.data_as(_I)))
         return dict(X=X, F=F, dV=dV, pid=pid)
+
+
+# ------------------------------------------------------------- perceptron ---
+class MLP:
+    """Device workspace for the lbm_mlp_* entry points (torch CUDA tensors in,
+    torch CUDA tensors out)."""
+
+    def __init__(self, device=None):
+        import torch
+        self.L = load()
+        self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nbytes = int(self.L.lbm_mlp_workspace_bytes())
+        self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=self.dev)
+        self.nparam = int(self.L.lbm_mlp_num_params())
+
+    def _s(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream)
+
+    def _w(self, w):
+        import torch
+        if not isinstance(w, torch.Tensor):
+            w = torch.as_tensor(np.asarray(w, dtype=np.float32))
+        return w.to(self.dev, torch.float32).contiguous()
+
+    def forward(self, X, w):
+        import torch
+        X = X.to(self.dev, torch.float32).contiguous()
+        w = self._w(w)
+        Y = torch.empty((X.shape[0], 9), dtype=torch.float32, device=self.dev)
+        rc = self.L.lbm_mlp_forward(ctypes.c_void_p(X.data_ptr()), X.shape[0], ctypes.c_void_p(w.data_ptr()),
+                                    ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(self.ws.data_ptr()), self.nbytes,
+                                    self._s())
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T, w):
+        import torch
+        X = X.to(self.dev, torch.float32).contiguous()
+        T = T.to(self.dev, torch.float32).contiguous()
+        w = self._w(w)
+        g = torch.empty(self.nparam, dtype=torch.float32, device=self.dev)
+        loss = ctypes.c_double()
+        rc = self.L.lbm_mlp_loss_grad(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()), X.shape[0],
+                                      ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                      ctypes.byref(loss), ctypes.c_void_p(self.ws.data_ptr()), self.nbytes, self._s())
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, T, w, epochs, batch=4096, lr=1e-3):
+        """Returns (trained weights tensor, mean loss of the last epoch)."""
+        import torch
+        X = X.to(self.dev, torch.float32).contiguous()
+        T = T.to(self.dev, torch.float32).contiguous()
+        w = self._w(w).clone()
+        last = ctypes.c_double()
+        rc = self.L.lbm_mlp_train(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()), X.shape[0],
+                                  int(epochs), int(batch), float(lr), ctypes.c_void_p(w.data_ptr()),
+                                  ctypes.c_void_p(self.ws.data_ptr()), self.nbytes, self._s(), ctypes.byref(last))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_mlp_train")
+        return w, last.value
