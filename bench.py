@@ -166,6 +166,92 @@ def hit_setup(n, n_particles, seed=0):
     return dict(init=init, max_particles=n_particles)
 
 
+def precision_report(lbm, torch, n=64, n_particles=31, steps=200):
+    """Population storage precision against FP64 storage (which matches the
+    FP64 oracle to 1e-12) on the 64^3 particle-laden box: 31 spheres of
+    radius 4 (the 3.2 % volume fraction of the 512^3 / 16000-sphere case),
+    IBB, d'Humieres rates, tau = 0.51, 200 steps. Field errors are
+    max|x - x_ref| / max|x_ref|; statistics relative errors."""
+    u = workloads.hit_velocity(n, seed=0)
+    X = workloads.place_spheres((n, n, n), n_particles, 4.0, 1.0, seed=0)
+    res = {}
+    ref = None
+    for name, st in (("f64", lbm.F64), ("f32", lbm.F32), ("f16s", lbm.F16S), ("bf16s", lbm.BF16S)):
+        L = lbm.Lattice(n, n, n, 0.51, storage=st, rates=lbm.RATES_DHUMIERES, max_particles=n_particles)
+        L.init_velocity(u)
+        L.add_spheres(X, 4.0, density_ratio=5.0)
+        L.step(steps, lbm.BC_IBB)
+        rho, uu = L.macro()
+        stt = L.stats(lbm.STATS_BINS)
+        P = L.particles()
+        fl = L.flags()
+        L.close()
+        cur = dict(rho=rho, u=uu, st=stt, P=P, fluid=(fl & 1) == 0)
+        if ref is None:
+            ref = cur
+            continue
+        m = cur["fluid"] & ref["fluid"]
+
+        def fe(a, b):
+            return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+        res[name] = {
+            "e_rho": fe(cur["rho"][m] - 1.0, ref["rho"][m] - 1.0),
+            "e_u": fe(cur["u"][:, m], ref["u"][:, m]),
+            "ke_rel": abs(cur["st"]["kinetic_energy"] / ref["st"]["kinetic_energy"] - 1.0),
+            "eps_rel": abs(cur["st"]["dissipation"] / ref["st"]["dissipation"] - 1.0),
+            "particle_ke_rel": abs(cur["st"]["particle_ke"] / ref["st"]["particle_ke"] - 1.0),
+            "particle_ake_rel": abs(cur["st"]["particle_ake"] / max(ref["st"]["particle_ake"], 1e-300) - 1.0),
+        }
+        res[name] = {k: float("%.3g" % v) for k, v in res[name].items()}
+    res["config"] = f"{n}^3, {n_particles} spheres R=4, IBB, tau=0.51, {steps} steps; e_rho on rho-1"
+    return res
+
+
+def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
+    """Learned closure on the particle-laden 256^3 box (IBM-B): paired
+    IBB/IBM-B runs of seeds 0-7 give up to 1e6 training samples, seeds 8-9
+    are held out. Reports the near-surface (r/r_p in (1, 1.5]) dissipation
+    profile error against IBB for plain IBM-B and with the closure, and the
+    cost of one closure inference pass in the diagnostic."""
+    from paper_1906_05448_gb300 import closure
+    us, gs = 0.03, 4.0 / 0.03
+    t0 = time.perf_counter()
+    X, T = closure.paired_samples(n, n_particles, range(8), steps, us, gs)
+    t1 = time.perf_counter()
+    X, T = closure.shuffle(X, T, 0, limit=1000000)
+    mlp = lbm.MLP()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    w, last = mlp.train(X, T, closure.init_weights(0), epochs=20, batch=4096, lr=1e-3)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    e_plain, e_closure = closure.evaluate(n, n_particles, [8, 9], steps, w.cpu().numpy(), us, gs)
+    # inference cost: the tensor-core forward over one diagnostic's samples
+    (ibb, bcb), (ibm, bcm) = closure.hit_pair(n, n_particles, 8)
+    ibb.close()
+    ibm.step(steps, bcm)
+    Xs, _ = ibm.closure_samples(us, 1500 * n_particles)
+    ibm.close()
+    wt = w.to(Xs.device)
+    mlp.forward(Xs, wt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    for _ in range(10):
+        mlp.forward(Xs, wt)
+    e1.record()
+    torch.cuda.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 10
+    flops = 2.0 * (85 * 64 + 64 * 64 * 2 + 64 * 9) * Xs.shape[0]
+    return {"workload": f"{n}^3, {n_particles} spheres R=4, IBM-B vs IBB, {steps} steps, seeds 0-7 train / 8-9 eval",
+            "train_samples": int(X.shape[0]), "data_gen_s": round(t1 - t0, 1), "train_s": round(t3 - t2, 2),
+            "train_loss": round(last, 4), "zero_predictor_loss": round(float((T ** 2).mean()), 4),
+            "near_surface_eps_error_plain_ibm": round(e_plain, 4),
+            "near_surface_eps_error_closure": round(e_closure, 4),
+            "inference_samples": int(Xs.shape[0]), "inference_ms_per_diagnostic": round(inf_ms, 4),
+            "inference_tflops": round(flops / (inf_ms * 1e-3) / 1e12, 2)}
+
+
 def e2e_pipe(lbm, torch, steps):
     """Same workload through the C ABI from host buffers: the initial field is
     uploaded from pinned host memory and the final velocity field read back,
@@ -321,8 +407,8 @@ def main():
 
     variants = {}
     if not args.no_variants and rank == 0:
-        for name, storage, bc in (("pipe_ibm_b_f32", lbm.F32, lbm.BC_IBM_B), ("pipe_ibb_f16s", lbm.F16S, lbm.BC_IBB),
-                                  ("pipe_ibb_bf16s", lbm.BF16S, lbm.BC_IBB)):
+        for name, storage, bc in (("pipe_ibm_u_f32", lbm.F32, lbm.BC_IBM_U), ("pipe_ibm_b_f32", lbm.F32, lbm.BC_IBM_B),
+                                  ("pipe_ibb_f16s", lbm.F16S, lbm.BC_IBB), ("pipe_ibb_bf16s", lbm.BF16S, lbm.BC_IBB)):
             r = run_case(lbm, torch, name, PIPE["nx"], PIPE["ny"], NZ, PP["tau"], (0, 0, PP["g"]),
                          storage, lbm.RATES_SRT, bc, args.steps, min(args.warmup, 10), pipe_setup(lbm))
             p = r["prof"]
@@ -341,6 +427,12 @@ def main():
                               "group_ms_per_step": {k: round(v / r["steps"], 4) for k, v in p["ms"].items() if v > 0},
                               "launches_per_step": round(sum(p["launches"].values()) / r["steps"], 1),
                               "finite": r["finite"]}
+
+    precision = None
+    closure_res = None
+    if not args.no_variants and rank == 0:
+        precision = precision_report(lbm, torch)
+        closure_res = closure_report(lbm, torch)
 
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -382,6 +474,8 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "variants": variants,
+            "precision_vs_f64": precision,
+            "closure": closure_res,
         }
         print(json.dumps(line))
     if dist:

@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             v = fl0 + D;
         }
         Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
-        a.link_fin[k] = double(v);
         if (pid >= 0) {
+            a.link_fin[k] = double(v);
             // momentum exchange with unshifted f = g + w (w_l = w_ibar)
             const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
             const double dP0 = (lx - uw[0]) * fo - (-lx - uw[0]) * fi;
