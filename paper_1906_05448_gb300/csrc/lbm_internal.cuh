@@ -82,6 +82,27 @@ template <> struct Store<LBM_BF16S> {
 
 inline size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
 
+// Unsigned 32-bit division by a run-time constant with a multiply-high and
+// shifts (Granlund & Montgomery 1994), valid for every 32-bit dividend.
+struct FastDiv {
+    unsigned d, m, s;
+    FastDiv() : d(1), m(0), s(0) {}
+    explicit FastDiv(unsigned dd) : d(dd) {
+        unsigned l = 0;
+        while ((1ull << l) < dd) l++;
+        s = l;
+        m = (unsigned)((((1ull << l) - dd) << 32) / dd + 1);
+    }
+    __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
+#ifdef __CUDA_ARCH__
+        const unsigned t = __umulhi(n, m);
+#else
+        const unsigned t = (unsigned)(((unsigned long long)n * m) >> 32);
+#endif
+        return s == 0 ? n : (t + ((n - t) >> 1)) >> (s - 1);
+    }
+};
+
 // ------------------------------------------------------------ collision ----
 struct Rates {
     float s_e, s_eps, s_q, s_nu, s_pi, s_m;  // d'Humieres groups (s_nu = 1/tau)

@@ -24,6 +24,7 @@ struct SweepArgs {
     void *B;
     const unsigned long long *seg;  // optional row segments (see stream_collide_bulk)
     long long nseg;
+    FastDiv fd_ny;  // row -> (y, z)
     const uint8_t *flags;
     const int *aux;
     void *sup_ru;  // (rho, u*) per support site, arithmetic type of the storage
@@ -46,7 +47,7 @@ __device__ __forceinline__ void watchdog(R rho, R ux, R uy, R uz, unsigned *stat
 #define LBM_BULK_MINB 4
 #endif
 #ifndef LBM_BULK_PERSIST
-#define LBM_BULK_PERSIST 0
+#define LBM_BULK_PERSIST 2  // persistent grid: 0 never, 1 always, 2 for segment sweeps
 #endif
 #ifndef LBM_BULK_SPEC
 #define LBM_BULK_SPEC 0
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
         }
         if (x >= nx) continue;
         if (!LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
-        const int y = row % ny, z = row / ny;
+        const int z = (int)a.fd_ny.div((unsigned)row), y = row - z * ny;
         const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
         const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
         // row offsets of the source rows (y - c_y, z - c_z)
@@ -183,6 +184,7 @@ struct LinkArgs {
     long long max_links;
     int nx, ny, nz;
     long long N;
+    FastDiv dx, dxy;  // division by nx and nx*ny
 };
 
 __device__ __forceinline__ double mimg(double d, int n) {
@@ -192,7 +194,9 @@ __device__ __forceinline__ double mimg(double d, int n) {
 }
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-template <int S>
+// PART: some links belong to moving walls (particles); the pipe wall alone
+// needs neither the wall velocity nor the momentum exchange
+template <int S, bool PART>
 __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
@@ -205,9 +209,11 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         const int c = a.link_cell[k];
         const int l = a.link_dir[k];
         const int sch = a.link_scheme[k];
-        const int pid = a.link_pid[k];
+        const int pid = PART ? a.link_pid[k] : -1;
         const double q = a.link_q[k];
-        const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+        const unsigned zq = a.dxy.div((unsigned)c), rem = (unsigned)c - zq * (unsigned)(nx * ny);
+        const unsigned yq = a.dx.div(rem);
+        const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * (unsigned)nx);
         const int lx = cx(l), ly = cy(l), lz = cz(l);
         // solid node x_f + c_l, and fluid nodes x_f - c_l, x_f - 2 c_l
         const int cb = wrap(x + lx, nx) + nx * (wrap(y + ly, ny) + ny * wrap(z + lz, nz));
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         const R fl0 = Store<S>::ld(A + (size_t)l * N + c);  // f*_l(x_f), toward the wall
         const R fi0 = Store<S>::ld(A + (size_t)i * N + c);  // f*_ibar(x_f)
         double uw[3] = {0.0, 0.0, 0.0};
-        if (pid >= 0) {
+        if (PART && pid >= 0) {
             const double r0 = mimg(x + q * lx - a.X[3 * pid + 0], nx);
             const double r1 = mimg(y + q * ly - a.X[3 * pid + 1], ny);
             const double r2 = mimg(z + q * lz - a.X[3 * pid + 2], nz);
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             v = fl0 + D;
         }
         Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
-        if (pid >= 0) {
+        if (PART && pid >= 0) {
             a.link_fin[k] = double(v);
             // momentum exchange with unshifted f = g + w (w_l = w_ibar)
             const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
@@ -353,6 +359,7 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     const bool segs = BC == 1 && c.nseg > 0;
     a.seg = c.seg;
     a.nseg = segs ? c.nseg : 0;
+    a.fd_ny = FastDiv((unsigned)c.ny);
     int bx = ((c.nx + 31) / 32) * 32;
     if (bx > 256) bx = 256;
     int by = 256 / bx;
@@ -363,7 +370,7 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     }
     const long long items = segs ? c.nseg : (long long)c.ny * c.nz * ((c.nx + bx - 1) / bx);
     long long nb = segs ? (items + 7) / 8 : (items + by - 1) / by;
-    if (LBM_BULK_PERSIST) {
+    if (LBM_BULK_PERSIST == 1 || (LBM_BULK_PERSIST == 2 && segs)) {
         // persistent grid: as many blocks as fit on the device at once
         static int resident[4][2][3][2];
         int &res = resident[S][SRT][BC][force ? 1 : 0];
@@ -416,14 +423,16 @@ template <int S>
 static cudaError_t launch_links_s(Ctx &c) {
     if (c.max_links == 0) return cudaSuccess;
     LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_fin, c.link_dP, c.link_dT,
-               c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N};
+               c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N,
+               FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny))};
     long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
     if (n > c.max_links) n = c.max_links;
     long long nb = (n + 255) / 256;
     if (nb < 1) nb = 1;
     if (nb > 152LL * 64) nb = 152LL * 64;
     count_launch(c, G_BND);
-    ibb_links<S><<<(unsigned)nb, 256, 0, c.stream>>>(a);
+    if (c.np > 0) ibb_links<S, true><<<(unsigned)nb, 256, 0, c.stream>>>(a);
+    else ibb_links<S, false><<<(unsigned)nb, 256, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
