@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/lbm.h): workspace layout, set-up
 // of the geometry, the per-step kernel sequence and host-side checks.
 #include "lbm_internal.cuh"
+#include "segments.h"
 
 #include <cmath>
 #include <ctime>
@@ -10,6 +11,10 @@
 #include <algorithm>
 #include <utility>
 #include <vector>
+
+#ifndef LBM_SEG_SECTOR
+#define LBM_SEG_SECTOR 1  // 1: sweep segments complete the 32-byte sectors at the ends of fluid runs
+#endif
 
 namespace lbmgb {
 size_t stats_partials_doubles();
@@ -87,7 +92,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.xy_start = L.take(4 * ((size_t)g->nx * g->ny + 1));
     P.xy_j = L.take(4 * (size_t)P.max_xy);
     P.xy_w = L.take(8 * (size_t)P.max_xy);
-    P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32);
+    P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32 + 1);
     P.seg = L.take(8 * (size_t)P.max_seg);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
@@ -626,22 +631,15 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     if (s != LBM_OK) return s;
     c.nsites_hint = c.nsites;
     c.nlinks_hint = c.nlinks;
-    // IBB sweep work list: each row's fluid extent cut into 32-cell segments
-    // (the solid margin outside the wall is never visited)
+    // IBB sweep work list (segments of fluid runs, see segments.h)
     std::vector<uint8_t> fl((size_t)c.N);
     CK(cudaMemcpy(fl.data(), c.flags, (size_t)c.N, cudaMemcpyDeviceToHost));
+    // cells per 32-byte sector; 16-bit storage is not widened (its 16-cell
+    // sectors add more zero lanes than the full-sector stores save)
+    const long long sec = (LBM_SEG_SECTOR && storage_bytes(c.storage) >= 4) ? 32 / (long long)storage_bytes(c.storage) : 1;
     std::vector<unsigned long long> segs;
-    for (long long row = 0; row < (long long)c.ny * c.nz; row++) {
-        const uint8_t *r = fl.data() + row * c.nx;
-        int x0 = 0, x1 = c.nx - 1;
-        while (x0 < c.nx && (r[x0] & FL_SOLID)) x0++;
-        while (x1 >= x0 && (r[x1] & FL_SOLID)) x1--;
-        for (int x = x0; x <= x1; x += 32) {
-            const int len = (x1 - x + 1) < 32 ? (x1 - x + 1) : 32;
-            segs.push_back((unsigned long long)row | ((unsigned long long)x << 32) | ((unsigned long long)len << 48));
-        }
-    }
-    if ((long long)segs.size() <= c.max_seg && c.nx < 65536) {
+    const bool seg_ok = build_sweep_segments(fl.data(), c.nx, c.ny, c.nz, FL_SOLID, sec, segs);
+    if (seg_ok && (long long)segs.size() <= c.max_seg) {
         CK(cudaMemcpy(c.seg, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice));
         c.nseg = (long long)segs.size();
     }

@@ -33,8 +33,18 @@ struct SweepArgs {
     int nx, ny, nz;
     long long N;
     double F[3];
+    float Fs[3];  // F in single precision (a double-to-single conversion per cell is costly on GB300)
     Rates rt;
 };
+
+// body force component in the arithmetic type R
+template <typename R, typename Args>
+__device__ __forceinline__ R body_force(const Args &a, int d) {
+    if constexpr (sizeof(R) == 8)
+        return R(a.F[d]);
+    else
+        return R(a.Fs[d]);
+}
 
 template <typename R>
 __device__ __forceinline__ void watchdog(R rho, R ux, R uy, R uz, unsigned *status) {
@@ -64,7 +74,7 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const bool segs = a.nseg > 0;
+    const bool segs = a.nseg > 0;  // one warp per item
     const int ipr = (nx + blockDim.x - 1) / blockDim.x;  // items per row (no segment list)
     const int lane = threadIdx.x & 31;
     const long long items = segs ? a.nseg : (long long)ny * nz * ipr;
@@ -74,17 +84,15 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
     const size_t N = (size_t)a.N;
     long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
                        : (long long)blockIdx.x * blockDim.y + threadIdx.y;
-    auto cell_of = [&](long long item, int &x, int &row) {
-        if (segs) {
-            // segment: row (bits 0-31), first x (32-47), length (48-55)
-            const unsigned long long sg = __ldg(a.seg + item);
-            row = (int)(sg & 0xffffffffULL);
-            const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
-            x = lane < len ? x0 + lane : nx;
-        } else {
-            row = (int)(item / ipr);
-            x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
-        }
+    // segment: row (bits 0-31), x of lane 0 plus the leading zero lanes
+    // (32-47), lanes (48-55), leading (56-59) and trailing (60-63)
+    // zero-writing lanes; the
+    // descriptor of the next item is loaded one iteration ahead
+    unsigned long long sg_next = 0;
+    if (segs && w < items) sg_next = __ldg(a.seg + w);
+    auto cell_of = [&](long long item, int &x, int &row) {  // without a segment list
+        row = (int)(item / ipr);
+        x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
     };
     // segments cover fluid cells only: no flag byte is needed (IBB)
     const bool read_flags = BC != 0 && !(BC == 1 && segs);
@@ -96,12 +104,33 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
     }
     for (; w < items; w += stride) {
         int x, row;
-        cell_of(w, x, row);
+        bool zero = false;
+        if (segs) {
+            const unsigned long long sg = sg_next;
+            if (w + stride < items) sg_next = __ldg(a.seg + w + stride);
+            row = (int)(sg & 0xffffffffULL);
+            const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
+            const int fa = (int)((sg >> 56) & 15), zt = (int)(sg >> 60);
+            if (lane >= len) continue;
+            x = x0 - fa + lane;
+            // lanes on the solid cells that complete the 32-byte sectors at
+            // either end of a fluid run write zeros (full-sector stores; the
+            // slots are dead or rewritten as ghosts before they are read)
+            zero = lane < fa || lane >= len - zt;
+        } else {
+            cell_of(w, x, row);
+        }
         const uint8_t fl = fl_next;
         if (read_flags && w + stride < items) {
             int x2, row2;
             cell_of(w + stride, x2, row2);
             if (x2 < nx) fl_next = a.flags[(size_t)row2 * nx + x2];
+        }
+        if (zero) {
+            const long long cz = (long long)row * nx + x;
+#pragma unroll
+            for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + cz, R(0));
+            continue;
         }
         if (x >= nx) continue;
         if (!LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
@@ -148,9 +177,9 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
             R jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
             R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
             if (FORCE && fluid) {
-                jx += R(0.5) * R(a.F[0]);
-                jy += R(0.5) * R(a.F[1]);
-                jz += R(0.5) * R(a.F[2]);
+                jx += R(0.5) * body_force<R>(a, 0);
+                jy += R(0.5) * body_force<R>(a, 1);
+                jz += R(0.5) * body_force<R>(a, 2);
             }
             const R rho = R(1) + drho;
             const int s = a.aux[c];
@@ -165,7 +194,7 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
         }
         R rho, ux, uy, uz;
         const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
-        collide<R, FORCE, SRT>(g, fs * R(a.F[0]), fs * R(a.F[1]), fs * R(a.F[2]), a.rt, rho, ux, uy, uz);
+        collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt, rho, ux, uy, uz);
         watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
         for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
@@ -234,7 +263,8 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
         }
         // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
-        const R D = R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2]));
+        // (zero at a fixed wall: skip its FP64 arithmetic)
+        const R D = (PART && pid >= 0) ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
         const R qq = R(q);
         R v;
         if (sch == 0) {
@@ -291,6 +321,7 @@ struct IbmCollideArgs {
     int nx, ny, nz;
     long long N;
     double F[3];
+    float Fs[3];
     Rates rt;
 };
 
@@ -316,9 +347,9 @@ __global__ void __launch_bounds__(128) ibm_collide(IbmCollideArgs a) {
     const bool fluid = !(a.flags[c] & FL_SOLID);
     const R *sF = (const R *)a.sup_F;
     const R fs = fluid ? R(1) : R(0);
-    const R Fx = fs * R(a.F[0]) + sF[3 * s + 0];
-    const R Fy = fs * R(a.F[1]) + sF[3 * s + 1];
-    const R Fz = fs * R(a.F[2]) + sF[3 * s + 2];
+    const R Fx = fs * body_force<R>(a, 0) + sF[3 * s + 0];
+    const R Fy = fs * body_force<R>(a, 1) + sF[3 * s + 1];
+    const R Fz = fs * body_force<R>(a, 2) + sF[3 * s + 2];
     R rho, ux, uy, uz;
     collide<R, true, SRT>(g, Fx, Fy, Fz, a.rt, rho, ux, uy, uz);
     watchdog(rho, ux, uy, uz, a.status);
@@ -354,7 +385,10 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     a.ny = c.ny;
     a.nz = c.nz;
     a.N = c.N;
-    for (int d = 0; d < 3; d++) a.F[d] = c.F[d];
+    for (int d = 0; d < 3; d++) {
+        a.F[d] = c.F[d];
+        a.Fs[d] = (float)c.F[d];
+    }
     a.rt = c.rt;
     const bool segs = BC == 1 && c.nseg > 0;
     a.seg = c.seg;
@@ -461,7 +495,10 @@ static cudaError_t launch_ibm_s(Ctx &c) {
     a.ny = c.ny;
     a.nz = c.nz;
     a.N = c.N;
-    for (int d = 0; d < 3; d++) a.F[d] = c.F[d];
+    for (int d = 0; d < 3; d++) {
+        a.F[d] = c.F[d];
+        a.Fs[d] = (float)c.F[d];
+    }
     a.rt = c.rt;
     const int tb = 128;
     const unsigned nb = site_grid(c, tb);

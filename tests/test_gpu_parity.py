@@ -158,6 +158,27 @@ def test_moving_spheres_ibb_f64(lbm):
     _links_equal(g2.links(), o2.links())
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_pipe_ibb_150_steps(lbm, storage, tol):
+    """Pipe wall by interpolated bounce-back: rows of up to 43 fluid cells,
+    i.e. two ragged sweep segments per row, plus the z-periodic ends."""
+    nx, ny, nz, R = 47, 46, 12, 21.5
+    g, o = pair(lbm, (nz, ny, nx), 0.6, force=(0, 0, 2e-6),
+                storage=lbm.F64 if storage == "f64" else lbm.F32)
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.02, perturbation=0.1, seed=4)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.set_pipe(R)
+    g.step(150, lbm.BC_IBB)
+    o.step(150, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0  # solid cells hold ghost values on the GPU
+    assert rel(g.populations()[:, fluid], o.populations()[:, fluid]) < tol
+    rg, ug = g.macro()
+    ro, uo = o.macro()
+    assert rel(ug[:, fluid], uo[:, fluid]) < tol
+    assert rel(rg[fluid], ro[fluid]) < tol
+
+
 @pytest.mark.parametrize("bc", ["ibm_u", "ibm_b"])
 def test_pipe_ibm_f64(lbm, bc):
     shape = (4, 26, 27)
