@@ -12,6 +12,9 @@
 #include <utility>
 #include <vector>
 
+#ifndef LBM_STATIC_LINKS
+#define LBM_STATIC_LINKS 1  // 1: static-wall links regrouped by direction for the ghost pass
+#endif
 #ifndef LBM_SEG_SECTOR
 #define LBM_SEG_SECTOR 1  // 1: sweep segments complete the 32-byte sectors at the ends of fluid runs
 #endif
@@ -38,7 +41,7 @@ struct Plan {
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_fin, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status, seg, refill;
+    size_t blk_sites, blk_links, counts, status, seg, slink, refill;
     long long max_refill;
     long long max_seg;
     size_t xy_start, xy_j, xy_w;
@@ -94,6 +97,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.xy_w = L.take(8 * (size_t)P.max_xy);
     P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32 + 1);
     P.seg = L.take(8 * (size_t)P.max_seg);
+    P.slink = L.take(8 * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
     P.counts = L.take(32);
@@ -512,6 +516,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.pipe_xy_w = (double *)(b + P.xy_w);
     c.pipe_max_xy = P.max_xy;
     c.seg = (unsigned long long *)(b + P.seg);
+    c.slink = (uint2 *)(b + P.slink);
+    c.static_links = 0;
     c.max_seg = P.max_seg;
     c.nseg = 0;
     c.nblk = P.nblk;
@@ -642,6 +648,40 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     if (seg_ok && (long long)segs.size() <= c.max_seg) {
         CK(cudaMemcpy(c.seg, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice));
         c.nseg = (long long)segs.size();
+    }
+    // the wall is static: regroup its links by direction (cell order kept
+    // inside a group) so that neighbouring threads of the ghost pass touch
+    // neighbouring cells of one population plane
+    if (LBM_STATIC_LINKS && c.storage != LBM_F64 && c.nlinks > 0 && c.nlinks <= c.max_links && c.N < (1LL << 30)) {
+        const size_t nl = (size_t)c.nlinks;
+        std::vector<int> lcell(nl);
+        std::vector<int8_t> ldir(nl), lsch(nl);
+        std::vector<double> lq(nl);
+        CK(cudaMemcpy(lcell.data(), c.link_cell, 4 * nl, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ldir.data(), c.link_dir, nl, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(lsch.data(), c.link_scheme, nl, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(lq.data(), c.link_q, 8 * nl, cudaMemcpyDeviceToHost));
+        int cnt[19] = {0};
+        bool ok = true;
+        for (size_t k = 0; k < nl; k++) {
+            if (ldir[k] < 0 || ldir[k] > 18 || lsch[k] < 0 || lsch[k] > 3) ok = false;
+            else cnt[ldir[k]]++;
+        }
+        if (ok) {
+            c.slink_off[0] = 0;
+            for (int l = 0; l < 19; l++) c.slink_off[l + 1] = c.slink_off[l] + cnt[l];
+            int pos[19];
+            for (int l = 0; l < 19; l++) pos[l] = c.slink_off[l];
+            std::vector<uint2> pk(nl);
+            for (size_t k = 0; k < nl; k++) {
+                const float qf = (float)lq[k];
+                unsigned qb;
+                std::memcpy(&qb, &qf, 4);
+                pk[pos[ldir[k]]++] = make_uint2((unsigned)lcell[k] | ((unsigned)lsch[k] << 30), qb);
+            }
+            CK(cudaMemcpy(c.slink, pk.data(), 8 * nl, cudaMemcpyHostToDevice));
+            c.static_links = 1;
+        }
     }
     return LBM_OK;
 }

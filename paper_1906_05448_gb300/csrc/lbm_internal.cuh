@@ -288,6 +288,11 @@ struct Ctx {
     // row segments of the fluid extent (IBB walls with a solid margin)
     unsigned long long *seg;
     long long nseg, max_seg;
+    // static wall (pipe) links regrouped by direction for the ghost pass:
+    // x = cell | scheme << 30, y = bits of q rounded to FP32
+    uint2 *slink;
+    int slink_off[20];  // first link of each direction, and the total
+    int static_links;   // 1: the ghost pass uses slink (FP32-arithmetic storages)
     // compaction scratch
     int nblk;
     long long *blk_sites, *blk_links;

@@ -17,6 +17,8 @@
 //   accumulated over the forcing passes.
 #include "lbm_internal.cuh"
 
+#include <algorithm>
+
 namespace lbmgb {
 
 struct SweepArgs {
@@ -201,6 +203,48 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
     }
 }
 
+__device__ __forceinline__ double mimg(double d, int n) {
+    if (d > 0.5 * n) d -= n;
+    else if (d < -0.5 * n) d += n;
+    return d;
+}
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Population bounced back into the fluid node x_f along ibar = opp(l) at time
+// t + 1 from post-collision values at t (Sec. 2.1): quadratic (sch 0) or
+// linear (sch 1) interpolated bounce-back, split at q = 1/2, or the halfway
+// rule (sch 2) where the interpolation nodes are not fluid. fl0 = f*_l(x_f),
+// fi0 = f*_ibar(x_f); c1 = x_f - c_l, c2 = x_f - 2 c_l; D = moving-wall term.
+template <int S>
+__device__ __forceinline__ typename Store<S>::R ibb_value(const typename Store<S>::T *A, size_t N, int l, int i,
+                                                          int sch, typename Store<S>::R qq, int c1, int c2,
+                                                          typename Store<S>::R D, typename Store<S>::R fl0,
+                                                          typename Store<S>::R fi0) {
+    typedef typename Store<S>::R R;
+    R v;
+    if (sch == 0) {
+        if (qq < R(0.5)) {
+            const R fl1 = Store<S>::ld(A + (size_t)l * N + c1), fl2 = Store<S>::ld(A + (size_t)l * N + c2);
+            v = qq * (R(1) + R(2) * qq) * fl0 + (R(1) - R(4) * qq * qq) * fl1 - qq * (R(1) - R(2) * qq) * fl2 + D;
+        } else {
+            const R fi1 = Store<S>::ld(A + (size_t)i * N + c1);
+            const R d = R(1) / (qq * (R(2) * qq + R(1)));
+            v = d * fl0 + (R(2) * qq - R(1)) / qq * fi0 - (R(2) * qq - R(1)) / (R(2) * qq + R(1)) * fi1 + d * D;
+        }
+    } else if (sch == 1) {
+        if (qq < R(0.5)) {
+            const R fl1 = Store<S>::ld(A + (size_t)l * N + c1);
+            v = R(2) * qq * fl0 + (R(1) - R(2) * qq) * fl1 + D;
+        } else {
+            const R h = R(1) / (R(2) * qq);
+            v = h * fl0 + (R(2) * qq - R(1)) * h * fi0 + h * D;
+        }
+    } else {
+        v = fl0 + D;
+    }
+    return v;
+}
+
 // ------------------------------------------------------------ IBB links ----
 struct LinkArgs {
     void *A;  // post-collision populations at t; ghost slots of solid nodes are written
@@ -216,12 +260,6 @@ struct LinkArgs {
     FastDiv dx, dxy;  // division by nx and nx*ny
 };
 
-__device__ __forceinline__ double mimg(double d, int n) {
-    if (d > 0.5 * n) d -= n;
-    else if (d < -0.5 * n) d += n;
-    return d;
-}
-__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // PART: some links belong to moving walls (particles); the pipe wall alone
 // needs neither the wall velocity nor the momentum exchange
@@ -265,28 +303,7 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
         // (zero at a fixed wall: skip its FP64 arithmetic)
         const R D = (PART && pid >= 0) ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
-        const R qq = R(q);
-        R v;
-        if (sch == 0) {
-            if (qq < R(0.5)) {
-                const R fl1 = Store<S>::ld(A + (size_t)l * N + c1), fl2 = Store<S>::ld(A + (size_t)l * N + c2);
-                v = qq * (R(1) + R(2) * qq) * fl0 + (R(1) - R(4) * qq * qq) * fl1 - qq * (R(1) - R(2) * qq) * fl2 + D;
-            } else {
-                const R fi1 = Store<S>::ld(A + (size_t)i * N + c1);
-                const R d = R(1) / (qq * (R(2) * qq + R(1)));
-                v = d * fl0 + (R(2) * qq - R(1)) / qq * fi0 - (R(2) * qq - R(1)) / (R(2) * qq + R(1)) * fi1 + d * D;
-            }
-        } else if (sch == 1) {
-            if (qq < R(0.5)) {
-                const R fl1 = Store<S>::ld(A + (size_t)l * N + c1);
-                v = R(2) * qq * fl0 + (R(1) - R(2) * qq) * fl1 + D;
-            } else {
-                const R h = R(1) / (R(2) * qq);
-                v = h * fl0 + (R(2) * qq - R(1)) * h * fi0 + h * D;
-            }
-        } else {
-            v = fl0 + D;
-        }
+        const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, D, fl0, fi0);
         Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
         if (PART && pid >= 0) {
             a.link_fin[k] = double(v);
@@ -373,7 +390,7 @@ static unsigned site_grid(const Ctx &c, int tb) {
 
 template <int S, bool SRT, int BC>
 static cudaError_t launch_bulk_t(Ctx &c, bool force) {
-    SweepArgs a;
+    SweepArgs a{};
     a.A = c.fA;
     a.B = c.fB;
     a.flags = c.flags;
@@ -453,9 +470,67 @@ cudaError_t launch_stream_collide(Ctx &c, int bc) {
     }
 }
 
+// Ghost pass of a static wall (no particle links), FP32 arithmetic: links
+// regrouped by direction, blockIdx.y = direction l, so l, c_l and ibar are
+// uniform over the block and neighbouring threads touch neighbouring cells.
+struct StaticLinkArgs {
+    void *A;
+    const uint2 *slink;  // x = cell | scheme << 30, y = FP32 bits of q
+    int off[20];
+    int nx, ny, nz;
+    long long N;
+    FastDiv dx, dxy;
+};
+
+template <int S>
+__global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R R;
+    const int l = blockIdx.y;
+    const int k0 = a.off[l], k1 = a.off[l + 1];
+    T *A = (T *)a.A;
+    const size_t N = (size_t)a.N;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int lx = cx(l), ly = cy(l), lz = cz(l), i = opp(l);
+    for (int k = k0 + blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += gridDim.x * blockDim.x) {
+        const uint2 m = __ldg(a.slink + k);
+        const int c = (int)(m.x & 0x3fffffffu), sch = (int)(m.x >> 30);
+        const R qq = R(__uint_as_float(m.y));
+        const unsigned zq = a.dxy.div((unsigned)c), rem = (unsigned)c - zq * (unsigned)(nx * ny);
+        const unsigned yq = a.dx.div(rem);
+        const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * (unsigned)nx);
+        const int cb = wrap(x + lx, nx) + nx * (wrap(y + ly, ny) + ny * wrap(z + lz, nz));
+        const int x1 = wrap(x - lx, nx), y1 = wrap(y - ly, ny), z1 = wrap(z - lz, nz);
+        const int c1 = x1 + nx * (y1 + ny * z1);
+        const int c2 = wrap(x1 - lx, nx) + nx * (wrap(y1 - ly, ny) + ny * wrap(z1 - lz, nz));
+        const R fl0 = Store<S>::ld(A + (size_t)l * N + c), fi0 = Store<S>::ld(A + (size_t)i * N + c);
+        const R v = ibb_value<S>(A, N, l, i, sch, qq, c1, c2, R(0), fl0, fi0);
+        Store<S>::st(A + (size_t)i * N + cb, v);
+    }
+}
+
 template <int S>
 static cudaError_t launch_links_s(Ctx &c) {
     if (c.max_links == 0) return cudaSuccess;
+    if (c.static_links && c.np == 0 && S != LBM_F64) {
+        StaticLinkArgs a;
+        a.A = c.fA;
+        a.slink = c.slink;
+        for (int l = 0; l < 20; l++) a.off[l] = c.slink_off[l];
+        a.nx = c.nx;
+        a.ny = c.ny;
+        a.nz = c.nz;
+        a.N = c.N;
+        a.dx = FastDiv((unsigned)c.nx);
+        a.dxy = FastDiv((unsigned)(c.nx * c.ny));
+        int most = 0;
+        for (int l = 0; l < 19; l++) most = std::max(most, c.slink_off[l + 1] - c.slink_off[l]);
+        unsigned nbx = (unsigned)((most + 255) / 256);
+        if (nbx < 1) nbx = 1;
+        count_launch(c, G_BND);
+        ibb_links_static<S><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        return cudaGetLastError();
+    }
     LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_fin, c.link_dP, c.link_dT,
                c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N,
                FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny))};

@@ -84,3 +84,13 @@ def test_profile_counts_launches_and_times(lbm):
     p = L.profile(0)
     assert p["spans"]["bulk"] == 5
     L.close()
+    # moving spheres: link pass with momentum exchange
+    S = lbm.Lattice(24, 24, 24, 0.6, storage=lbm.F32, max_particles=1)
+    S.init_velocity(np.zeros((3, 24, 24, 24)))
+    S.add_spheres(np.array([[11.5, 12.0, 12.5]]), 4.0)
+    S.step(1, lbm.BC_IBB)
+    S.profile_enable(True)
+    S.step(4, lbm.BC_IBB)
+    p = S.profile(0)
+    assert p["launches"]["bulk"] == 4 and p["launches"]["ibb_boundary"] == 4
+    S.close()

@@ -117,3 +117,4 @@ def test_segments_cover_fluid_once(harness, name, make, sec):
         seg = np.arange(s0, min(s0 + sec, N))
         if len(seg) == sec:
             assert written[seg].all(), (name, s0)
+
