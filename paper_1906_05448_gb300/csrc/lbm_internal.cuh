@@ -118,6 +118,72 @@ __host__ __device__ __forceinline__ R guo_term(int i, R ux, R uy, R uz, R Fx, R 
     return R(wgt(i)) * (R(3) * a + R(9) * cu * b);
 }
 
+// BGK with a uniform body force in FP32, force factors folded on the host:
+// g*_i = g_i + omega (w_i P_i - g_i) + (1 - omega/2) w_i [3 c_i.F - 3 u.F
+// + 9 (c_i.u)(c_i.F)] with P_i = drho - 1.5 rho u^2 + 3 rho c_i.u
+// + 4.5 rho (c_i.u)^2: the same BGK + Guo step as collide<float, FORCE,
+// true> in fewer operations (the relaxation keeps its association).
+struct SrtK {
+    float om;     // omega
+    float K[19];  // 3 (1 - omega/2) w_i c_i.F
+    float L[19];  // 9 (1 - omega/2) w_i c_i.F
+    float cw[19]; // (1 - omega/2) w_i
+    float hF[3];  // F / 2
+    float F3[3];  // 3 F
+};
+
+inline SrtK make_srt_k(double omega, const double F[3]) {
+    SrtK k;
+    k.om = (float)omega;
+    const double c1 = 1.0 - 0.5 * omega;
+    for (int i = 0; i < 19; i++) {
+        const double cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
+        k.K[i] = (float)(3.0 * c1 * wgt(i) * cF);
+        k.L[i] = (float)(9.0 * c1 * wgt(i) * cF);
+        k.cw[i] = (float)(c1 * wgt(i));
+    }
+    for (int d = 0; d < 3; d++) {
+        k.hF[d] = (float)(0.5 * F[d]);
+        k.F3[d] = (float)(3.0 * F[d]);
+    }
+    return k;
+}
+
+template <bool FORCE>
+__device__ __forceinline__ void collide_srt_k(float g[19], const SrtK &k, float &rho_o, float &ux_o, float &uy_o,
+                                              float &uz_o) {
+    float drho = g[0];
+#pragma unroll
+    for (int i = 1; i < 19; i++) drho += g[i];
+    float jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
+    float jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
+    float jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
+    const float rho = 1.0f + drho;
+    const float irho = 1.0f / rho;
+    if (FORCE) {
+        jx += k.hF[0];
+        jy += k.hF[1];
+        jz += k.hF[2];
+    }
+    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+    uz_o = uz;
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    const float base = drho - 1.5f * rho * u2;
+    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
+    const float uF3 = FORCE ? ux * k.F3[0] + uy * k.F3[1] + uz * k.F3[2] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 19; i++) {
+        const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
+        const float P = fmaf(cu, fmaf(r45, cu, r3), base);
+        float v = fmaf(k.om, fmaf(float(wgt(i)), P, -g[i]), g[i]);
+        if (FORCE) v = fmaf(k.L[i], cu, v) + fmaf(-k.cw[i], uF3, k.K[i]);
+        g[i] = v;
+    }
+}
+
 // Collide one cell in place. g: shifted populations in, post-collision out.
 // F: total force on the cell. Returns rho and u = (sum f c + F/2)/rho.
 // The moment transform is the d'Humieres D3Q19 basis evaluated through

@@ -37,6 +37,7 @@ struct SweepArgs {
     double F[3];
     float Fs[3];  // F in single precision (a double-to-single conversion per cell is costly on GB300)
     Rates rt;
+    SrtK sk;  // folded BGK factors (FP32 arithmetic, uniform force)
 };
 
 // body force component in the arithmetic type R
@@ -63,6 +64,9 @@ __device__ __forceinline__ void watchdog(R rho, R ux, R uy, R uz, unsigned *stat
 #endif
 #ifndef LBM_BULK_SPEC
 #define LBM_BULK_SPEC 0
+#endif
+#ifndef LBM_SRT_FOLDED
+#define LBM_SRT_FOLDED 1
 #endif
 
 // Work items: without a segment list, one item = one row piece of
@@ -196,7 +200,11 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
         }
         R rho, ux, uy, uz;
         const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
-        collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt, rho, ux, uy, uz);
+        if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
+            collide_srt_k<FORCE>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
+        else
+            collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt,
+                                   rho, ux, uy, uz);
         watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
         for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
@@ -407,6 +415,7 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
         a.Fs[d] = (float)c.F[d];
     }
     a.rt = c.rt;
+    a.sk = make_srt_k(c.rt.d_nu, c.F);
     const bool segs = BC == 1 && c.nseg > 0;
     a.seg = c.seg;
     a.nseg = segs ? c.nseg : 0;
