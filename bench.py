@@ -106,6 +106,19 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------ replica timing ----
+def max_over_ranks(torch, dist, ms, device):
+    """Slowest rank's time: every replica waits for it."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(fluid_cells, steps, world, ms_max):
+    """Whole-job rate: the cells of all replicas over the slowest time."""
+    return fluid_cells * steps * world / (ms_max * 1e-3) / 1e6
+
+
 # ------------------------------------------------------------- GPU runs ----
 def run_case(lbm, torch, name, nx, ny, nz, tau, force, storage, rates, bc, steps, warmup, setup, fluid_cells=None,
              profile=True):
@@ -131,20 +144,23 @@ def run_case(lbm, torch, name, nx, ny, nz, tau, force, storage, rates, bc, steps
     prof = L.profile(0) if profile else None
     st = L.stats(0)
     ok = bool(np.isfinite(st["kinetic_energy"]))
-    bulk_cells = None
+    # algorithmic bytes of one sweep launch: every visited cell reads and
+    # writes 19 populations; the flag byte is read where the sweep needs it
+    # (the pipe's IBB sweep walks fluid-run segments and reads no flags)
+    sb = {lbm.F64: 8, lbm.F32: 4}.get(storage, 2)
+    N = nx * ny * nz
     if bc == lbm.BC_IBB:
-        fl = L.flags()
-        bulk_cells = int(np.count_nonzero(fl & 3 == 0))
+        fluid = int(np.count_nonzero((L.flags() & 1) == 0))
+        bulk_bytes = 2 * 19 * sb * fluid + (0 if setup.get("segments") else N)
     elif bc in (lbm.BC_IBM_U, lbm.BC_IBM_B):
-        fl = L.flags()
-        bulk_cells = int(np.count_nonzero(fl & 4 == 0))
+        bulk_bytes = 2 * 19 * sb * N + N
     else:
-        bulk_cells = nx * ny * nz
+        bulk_bytes = 2 * 19 * sb * N
     L.close()
     del L
     torch.cuda.empty_cache()
     return dict(name=name, ms=ms, steps=steps, mlups=fluid_cells * steps / (ms * 1e-3) / 1e6, fluid_cells=fluid_cells,
-                bulk_cells=bulk_cells, ncells=nx * ny * nz, prof=prof, finite=ok)
+                bulk_bytes=bulk_bytes, ncells=N, prof=prof, finite=ok)
 
 
 def pipe_setup(lbm, storage=None):
@@ -153,7 +169,7 @@ def pipe_setup(lbm, storage=None):
     def init(L):
         L.init_velocity(u)
         L.set_pipe(PIPE["radius"])
-    return dict(init=init)
+    return dict(init=init, segments=True)
 
 
 def hit_setup(n, n_particles, seed=0):
@@ -308,8 +324,10 @@ def cpu_baseline(target_seconds=12.0):
 
 
 def source_hash():
+    """Hash of the sweep kernel's sources (kernel, device header, segment
+    list): a recorded DRAM traffic figure is used only while it matches."""
     h = hashlib.sha256()
-    for f in ("lbm_internal.cuh", "stream_collide.cu"):
+    for f in ("sweep.cu", "lbm_device.cuh", "segments.h"):
         with open(os.path.join(ROOT, "paper_1906_05448_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -394,14 +412,12 @@ def main():
     clk = clocks.stop()
     ms_total = main_res["ms"]
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(torch, dist, ms_total, "cuda")
         dist.barrier()
-    value = main_res["fluid_cells"] * args.steps * world / (ms_total * 1e-3) / 1e6
+    value = job_mlups(main_res["fluid_cells"], args.steps, world, ms_total)
     prof = main_res["prof"]
     bulk_ms = prof["ms"]["bulk"] / max(1, prof["spans"]["bulk"])
-    bulk_bytes = 2 * 19 * 4 * main_res["bulk_cells"] + main_res["ncells"]  # populations + flag byte per cell
+    bulk_bytes = main_res["bulk_bytes"]  # 2 x 19 x 4 B per fluid cell
     achieved = bulk_bytes / (bulk_ms * 1e-3) / 1e9
     launches = sum(prof["launches"].values())
 
@@ -413,9 +429,8 @@ def main():
                          storage, lbm.RATES_SRT, bc, args.steps, min(args.warmup, 10), pipe_setup(lbm))
             p = r["prof"]
             bms = p["ms"]["bulk"] / max(1, p["spans"]["bulk"])
-            sb = 4 if storage == lbm.F32 else 2
             variants[name] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms"] / r["steps"], 4),
-                              "bulk_kernel_gbs": round((2 * 19 * sb * r["bulk_cells"] + r["ncells"]) / (bms * 1e-3) / 1e9, 1),
+                              "bulk_kernel_gbs": round(r["bulk_bytes"] / (bms * 1e-3) / 1e9, 1),
                               "group_ms_per_step": {k: round(v / r["steps"], 4) for k, v in p["ms"].items() if v > 0},
                               "finite": r["finite"]}
         hs = hit_setup(256, 2000)

@@ -35,34 +35,33 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
         u_o[c] = u_o[N + c] = u_o[2 * N + c] = 0.0;
         return;
     }
+    // arithmetic type of the storage (FP32 for the 32- and 16-bit layouts)
+    typedef typename Store<S>::R R;
     const T *P = (const T *)A;
-    double r = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+    R r = R(0), j0 = R(0), j1 = R(0), j2 = R(0);
+#pragma unroll
     for (int i = 0; i < 19; i++) {
-        double g;
-        if (S == LBM_F64) g = *(const double *)(P + i * N + c);
-        else if (S == LBM_F32) g = *(const float *)(P + i * N + c);
-        else if (S == LBM_F16S) g = (double)__half2float(*(const __half *)(P + i * N + c)) / (double)F16_SCALE;
-        else g = (double)__bfloat162float(*(const __nv_bfloat16 *)(P + i * N + c));
+        const R g = Store<S>::ld(P + (size_t)i * N + c);
         r += g;
-        j0 += g * cx(i);
-        j1 += g * cy(i);
-        j2 += g * cz(i);
+        j0 += g * R(cx(i));
+        j1 += g * R(cy(i));
+        j2 += g * R(cz(i));
     }
     const bool fluid = !(fl & FL_SOLID);
-    double Fx = fluid ? F0 : 0.0, Fy = fluid ? F1 : 0.0, Fz = fluid ? F2 : 0.0;
+    R Fx = fluid ? R(F0) : R(0), Fy = fluid ? R(F1) : R(0), Fz = fluid ? R(F2) : R(0);
     if (ibm && (fl & FL_SUP) && aux[c] >= 0 && aux[c] < max_sites) {
-        typedef typename Store<S>::R Rt;
-        const Rt *sup_F = (const Rt *)sup_Fv;
+        const R *sup_F = (const R *)sup_Fv;
         const int s = aux[c];
         Fx += sup_F[3 * s];
         Fy += sup_F[3 * s + 1];
         Fz += sup_F[3 * s + 2];
     }
-    const double rho = 1.0 + r;
-    rho_o[c] = rho;
-    u_o[c] = (j0 - 0.5 * Fx) / rho;
-    u_o[N + c] = (j1 - 0.5 * Fy) / rho;
-    u_o[2 * N + c] = (j2 - 0.5 * Fz) / rho;
+    const R rho = R(1) + r;
+    const R ir = R(1) / rho;
+    rho_o[c] = double(rho);
+    u_o[c] = double((j0 - R(0.5) * Fx) * ir);
+    u_o[N + c] = double((j1 - R(0.5) * Fy) * ir);
+    u_o[2 * N + c] = double((j2 - R(0.5) * Fz) * ir);
 }
 
 cudaError_t launch_macro(Ctx &c, int /*mask_mode*/) {

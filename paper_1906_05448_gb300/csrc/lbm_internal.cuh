@@ -1,7 +1,6 @@
-// Internal definitions of the GB300 lattice Boltzmann library: context,
-// D3Q19 constants, population storage formats and the device collision.
-// The method is the D3Q19 MRT LBM with Guo forcing of Peng et al.,
-// arXiv:1906.05448 (Sec. 2.1, Sec. 3.1); see lbm.h for the public ABI.
+// Internal definitions of the GB300 lattice Boltzmann library: the context
+// that the C ABI hands out, profiling groups and the launcher prototypes.
+// Device-side definitions are in lbm_device.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,319 +9,9 @@
 #include <stdint.h>
 
 #include "lbm.h"
+#include "lbm_device.cuh"
 
 namespace lbmgb {
-
-// ---------------------------------------------------------------- flags ----
-enum : uint8_t {
-    FL_SOLID = 1,     // inside a particle / outside the pipe
-    FL_BND = 2,       // IBB: fluid cell with at least one boundary link (sites list)
-    FL_SUP = 4,       // IBM: cell handled by the compact forcing path
-    FL_WAS_SOLID = 8, // transient during a geometry update
-};
-
-constexpr int NO_OWNER = 0x7fffffff;
-
-// --------------------------------------------------------------- D3Q19 -----
-// Velocity order (same as lbm.h): rest, +-x, +-y, +-z, then the edges in
-// (+,+)/(-,-), (+,-)/(-,+) pairs for xy, xz, yz. Opposites are adjacent.
-__host__ __device__ constexpr int cx(int i) {
-    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
-         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
-}
-__host__ __device__ constexpr int cy(int i) {
-    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
-         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
-}
-__host__ __device__ constexpr int cz(int i) {
-    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
-         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
-}
-__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
-__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
-
-// ------------------------------------------------------------- storage -----
-// Populations are stored shifted, g_i = f_i - w_i, which keeps the stored
-// numbers small and the rounding of the stored state well below that of f.
-template <int S> struct Store;
-template <> struct Store<LBM_F64> {
-    typedef double T;
-    typedef double R;  // arithmetic type
-    static __device__ __forceinline__ double ld(const T *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(T *p, double v) { *p = v; }
-};
-#ifndef LBM_STORE_CS
-#define LBM_STORE_CS 0
-#endif
-template <> struct Store<LBM_F32> {
-    typedef float T;
-    typedef float R;
-    static __device__ __forceinline__ float ld(const T *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(T *p, float v) {
-        if (LBM_STORE_CS) __stcs(p, v);
-        else *p = v;
-    }
-};
-// FP16 holds g * 2^10 so that small departures from w_i stay normal numbers.
-constexpr float F16_SCALE = 1024.0f;
-template <> struct Store<LBM_F16S> {
-    typedef __half T;
-    typedef float R;
-    static __device__ __forceinline__ float ld(const T *p) {
-        return __half2float(__ldg(p)) * (1.0f / F16_SCALE);
-    }
-    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
-};
-template <> struct Store<LBM_BF16S> {
-    typedef __nv_bfloat16 T;
-    typedef float R;
-    static __device__ __forceinline__ float ld(const T *p) { return __bfloat162float(__ldg(p)); }
-    static __device__ __forceinline__ void st(T *p, float v) { *p = __float2bfloat16_rn(v); }
-};
-
-inline size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
-
-// Unsigned 32-bit division by a run-time constant with a multiply-high and
-// shifts (Granlund & Montgomery 1994), valid for every 32-bit dividend.
-struct FastDiv {
-    unsigned d, m, s;
-    FastDiv() : d(1), m(0), s(0) {}
-    explicit FastDiv(unsigned dd) : d(dd) {
-        unsigned l = 0;
-        while ((1ull << l) < dd) l++;
-        s = l;
-        m = (unsigned)((((1ull << l) - dd) << 32) / dd + 1);
-    }
-    __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
-#ifdef __CUDA_ARCH__
-        const unsigned t = __umulhi(n, m);
-#else
-        const unsigned t = (unsigned)(((unsigned long long)n * m) >> 32);
-#endif
-        return s == 0 ? n : (t + ((n - t) >> 1)) >> (s - 1);
-    }
-};
-
-// ------------------------------------------------------------ collision ----
-struct Rates {
-    float s_e, s_eps, s_q, s_nu, s_pi, s_m;  // d'Humieres groups (s_nu = 1/tau)
-    double d_e, d_eps, d_q, d_nu, d_pi, d_m;
-};
-
-// Guo forcing term F_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F.
-template <typename R>
-__host__ __device__ __forceinline__ R guo_term(int i, R ux, R uy, R uz, R Fx, R Fy, R Fz) {
-    const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
-    const R a = (R(cx(i)) - ux) * Fx + (R(cy(i)) - uy) * Fy + (R(cz(i)) - uz) * Fz;
-    const R b = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
-    return R(wgt(i)) * (R(3) * a + R(9) * cu * b);
-}
-
-// BGK with a uniform body force in FP32, force factors folded on the host:
-// g*_i = g_i + omega (w_i P_i - g_i) + (1 - omega/2) w_i [3 c_i.F - 3 u.F
-// + 9 (c_i.u)(c_i.F)] with P_i = drho - 1.5 rho u^2 + 3 rho c_i.u
-// + 4.5 rho (c_i.u)^2: the same BGK + Guo step as collide<float, FORCE,
-// true> in fewer operations (the relaxation keeps its association).
-struct SrtK {
-    float om;     // omega
-    float K[19];  // 3 (1 - omega/2) w_i c_i.F
-    float L[19];  // 9 (1 - omega/2) w_i c_i.F
-    float cw[19]; // (1 - omega/2) w_i
-    float hF[3];  // F / 2
-    float F3[3];  // 3 F
-};
-
-inline SrtK make_srt_k(double omega, const double F[3]) {
-    SrtK k;
-    k.om = (float)omega;
-    const double c1 = 1.0 - 0.5 * omega;
-    for (int i = 0; i < 19; i++) {
-        const double cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        k.K[i] = (float)(3.0 * c1 * wgt(i) * cF);
-        k.L[i] = (float)(9.0 * c1 * wgt(i) * cF);
-        k.cw[i] = (float)(c1 * wgt(i));
-    }
-    for (int d = 0; d < 3; d++) {
-        k.hF[d] = (float)(0.5 * F[d]);
-        k.F3[d] = (float)(3.0 * F[d]);
-    }
-    return k;
-}
-
-template <bool FORCE>
-__device__ __forceinline__ void collide_srt_k(float g[19], const SrtK &k, float &rho_o, float &ux_o, float &uy_o,
-                                              float &uz_o) {
-    float drho = g[0];
-#pragma unroll
-    for (int i = 1; i < 19; i++) drho += g[i];
-    float jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
-    float jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
-    float jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
-    const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
-    if (FORCE) {
-        jx += k.hF[0];
-        jy += k.hF[1];
-        jz += k.hF[2];
-    }
-    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
-    rho_o = rho;
-    ux_o = ux;
-    uy_o = uy;
-    uz_o = uz;
-    const float u2 = ux * ux + uy * uy + uz * uz;
-    const float base = drho - 1.5f * rho * u2;
-    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-    const float uF3 = FORCE ? ux * k.F3[0] + uy * k.F3[1] + uz * k.F3[2] : 0.0f;
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-        const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-        const float P = fmaf(cu, fmaf(r45, cu, r3), base);
-        float v = fmaf(k.om, fmaf(float(wgt(i)), P, -g[i]), g[i]);
-        if (FORCE) v = fmaf(k.L[i], cu, v) + fmaf(-k.cw[i], uF3, k.K[i]);
-        g[i] = v;
-    }
-}
-
-// Collide one cell in place. g: shifted populations in, post-collision out.
-// F: total force on the cell. Returns rho and u = (sum f c + F/2)/rho.
-// The moment transform is the d'Humieres D3Q19 basis evaluated through
-// opposite-pair sums (even moments) and differences (odd moments); the
-// inverse uses the orthogonality of the basis (row norms below).
-template <typename R, bool FORCE, bool SRT>
-__host__ __device__ __forceinline__ void collide(R g[19], R Fx, R Fy, R Fz, const Rates &rt, R &rho_o, R &ux_o,
-                                                 R &uy_o, R &uz_o) {
-    R drho = g[0];
-#pragma unroll
-    for (int i = 1; i < 19; i++) drho += g[i];
-    R jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
-    R jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
-    R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
-    const R rho = R(1) + drho;
-    const R irho = R(1) / rho;
-    if (FORCE) {
-        jx += R(0.5) * Fx;
-        jy += R(0.5) * Fy;
-        jz += R(0.5) * Fz;
-    }
-    const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
-    rho_o = rho;
-    ux_o = ux;
-    uy_o = uy;
-    uz_o = uz;
-    const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
-    if constexpr (SRT) {
-        // BGK: g* = g - w (g - g_eq) + (1 - w/2) F_i with g_eq = f_eq - w;
-        // with F_i = w_i [3 c.F - 3 u.F + 9 (c.u)(c.F)] the force term costs a
-        // few operations per direction once u.F is known.
-        const R om = (sizeof(R) == 8) ? R(rt.d_nu) : R(rt.s_nu);
-        const R c1 = R(1) - R(0.5) * om;
-        const R base = drho - rho * R(1.5) * u2;  // direction-independent part of g_eq / w
-        const R r3 = R(3) * rho, r45 = R(4.5) * rho;
-        const R uF3 = FORCE ? R(3) * (ux * Fx + uy * Fy + uz * Fz) : R(0);
-#pragma unroll
-        for (int i = 0; i < 19; i++) {
-            const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
-            const R geq = R(wgt(i)) * (base + cu * (r3 + r45 * cu));
-            R v = g[i] + om * (geq - g[i]);
-            if (FORCE) {
-                const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
-                v += (c1 * R(wgt(i))) * (R(3) * cF - uF3 + R(9) * cu * cF);
-            }
-            g[i] = v;
-        }
-    } else {
-    // MRT: g* = g + F_i - M^-1 S (M (g + F_i/2) - (m_eq - M w)).
-    R Fi[19];
-    if (FORCE) {
-#pragma unroll
-        for (int i = 0; i < 19; i++) Fi[i] = guo_term<R>(i, ux, uy, uz, Fx, Fy, Fz);
-    }
-    R h[19];
-#pragma unroll
-    for (int i = 0; i < 19; i++) h[i] = FORCE ? g[i] + R(0.5) * Fi[i] : g[i];
-    const R Sx = h[1] + h[2], Sy = h[3] + h[4], Sz = h[5] + h[6];
-    const R Sa = h[7] + h[8], Sb = h[9] + h[10], Sc = h[11] + h[12], Sd = h[13] + h[14];
-    const R Se = h[15] + h[16], Sf = h[17] + h[18];
-    const R Dx = h[1] - h[2], Dy = h[3] - h[4], Dz = h[5] - h[6];
-    const R Da = h[7] - h[8], Db = h[9] - h[10], Dc = h[11] - h[12], Dd = h[13] - h[14];
-    const R De = h[15] - h[16], Df = h[17] - h[18];
-    const R A = Sx + Sy + Sz;
-    const R Exy = Sa + Sb, Exz = Sc + Sd, Eyz = Se + Sf;
-    const R E = Exy + Exz + Eyz;
-    const R pxx = R(2) * Sx - Sy - Sz + Exy + Exz - R(2) * Eyz;      // 3 p_xx
-    const R pixx = R(-2) * (R(2) * Sx - Sy - Sz) + Exy + Exz - R(2) * Eyz;
-    const R pww = Sy - Sz + Exy - Exz;
-    const R piww = R(-2) * (Sy - Sz) + Exy - Exz;
-    const R mee = R(-30) * h[0] - R(11) * A + R(8) * E;
-    const R mep = R(12) * h[0] - R(4) * A + E;
-    const R pxy = Sa - Sb, pyz = Se - Sf, pxz = Sc - Sd;
-    const R qx = R(-4) * Dx + Da + Db + Dc + Dd;
-    const R qy = R(-4) * Dy + Da - Db + De + Df;
-    const R qz = R(-4) * Dz + Dc - Dd + De - Df;
-    const R mx = (Da + Db) - (Dc + Dd);
-    const R my = (De + Df) - (Da - Db);
-    const R mz = (Dc - Dd) - (De - Df);
-    // equilibrium moments minus those of w (rho = 1, u = 0)
-    const R eq_e = R(-11) * drho + R(19) * rho * u2;
-    const R eq_ep = R(3) * drho - R(5.5) * rho * u2;
-    const R tx = R(2) * uxx - uyy - uzz;
-    const R eq_pxx = rho * tx, eq_pixx = R(-0.5) * rho * tx;
-    const R eq_pww = rho * (uyy - uzz), eq_piww = R(-0.5) * rho * (uyy - uzz);
-    const R eq_q = R(-2.0 / 3.0) * rho;
-    const bool dbl = sizeof(R) == 8;
-    const R se = dbl ? R(rt.d_e) : R(rt.s_e), sep = dbl ? R(rt.d_eps) : R(rt.s_eps);
-    const R sq = dbl ? R(rt.d_q) : R(rt.s_q), snu = dbl ? R(rt.d_nu) : R(rt.s_nu);
-    const R spi = dbl ? R(rt.d_pi) : R(rt.s_pi), sm = dbl ? R(rt.d_m) : R(rt.s_m);
-    // relaxed departures divided by the squared row norms of the basis
-    const R a_e = se * (mee - eq_e) * R(1.0 / 2394.0);
-    const R a_ep = sep * (mep - eq_ep) * R(1.0 / 252.0);
-    const R a_pxx = snu * (pxx - eq_pxx) * R(1.0 / 36.0);
-    const R a_pixx = spi * (pixx - eq_pixx) * R(1.0 / 72.0);
-    const R a_pww = snu * (pww - eq_pww) * R(1.0 / 12.0);
-    const R a_piww = spi * (piww - eq_piww) * R(1.0 / 24.0);
-    const R a_pxy = snu * (pxy - rho * ux * uy) * R(0.25);
-    const R a_pyz = snu * (pyz - rho * uy * uz) * R(0.25);
-    const R a_pxz = snu * (pxz - rho * ux * uz) * R(0.25);
-    const R a_qx = sq * (qx - eq_q * ux) * R(1.0 / 40.0);
-    const R a_qy = sq * (qy - eq_q * uy) * R(1.0 / 40.0);
-    const R a_qz = sq * (qz - eq_q * uz) * R(1.0 / 40.0);
-    const R a_mx = sm * mx * R(0.125), a_my = sm * my * R(0.125), a_mz = sm * mz * R(0.125);
-    // back-transform: even and odd parts per opposite pair
-    const R c0 = R(-30) * a_e + R(12) * a_ep;
-    const R ax = R(-11) * a_e - R(4) * a_ep;                 // common to the 6 axis directions
-    const R ed = R(8) * a_e + a_ep;                          // common to the 12 edges
-    const R evx = ax + R(2) * a_pxx - R(4) * a_pixx;
-    const R evy = ax - a_pxx + R(2) * a_pixx + a_pww - R(2) * a_piww;
-    const R evz = ax - a_pxx + R(2) * a_pixx - a_pww + R(2) * a_piww;
-    const R exy = ed + a_pxx + a_pixx + a_pww + a_piww;
-    const R exz = ed + a_pxx + a_pixx - a_pww - a_piww;
-    const R eyz = ed - R(2) * a_pxx - R(2) * a_pixx;
-    const R evA = exy + a_pxy, evB = exy - a_pxy;
-    const R evC = exz + a_pxz, evD = exz - a_pxz;
-    const R evE = eyz + a_pyz, evF = eyz - a_pyz;
-    const R odx = R(-4) * a_qx, ody = R(-4) * a_qy, odz = R(-4) * a_qz;
-    const R odA = a_qx + a_qy + a_mx - a_my;
-    const R odB = a_qx - a_qy + a_mx + a_my;
-    const R odC = a_qx + a_qz - a_mx + a_mz;
-    const R odD = a_qx - a_qz - a_mx - a_mz;
-    const R odE = a_qy + a_qz + a_my - a_mz;
-    const R odF = a_qy - a_qz + a_my + a_mz;
-    R corr[19];
-    corr[0] = c0;
-    corr[1] = evx + odx;  corr[2] = evx - odx;
-    corr[3] = evy + ody;  corr[4] = evy - ody;
-    corr[5] = evz + odz;  corr[6] = evz - odz;
-    corr[7] = evA + odA;  corr[8] = evA - odA;
-    corr[9] = evB + odB;  corr[10] = evB - odB;
-    corr[11] = evC + odC; corr[12] = evC - odC;
-    corr[13] = evD + odD; corr[14] = evD - odD;
-    corr[15] = evE + odE; corr[16] = evE - odE;
-    corr[17] = evF + odF; corr[18] = evF - odF;
-#pragma unroll
-    for (int i = 0; i < 19; i++) g[i] = FORCE ? g[i] + Fi[i] - corr[i] : g[i] - corr[i];
-    }
-}
 
 // ------------------------------------------------------------ context -----
 struct Ctx {

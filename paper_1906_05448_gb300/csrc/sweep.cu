@@ -1,0 +1,272 @@
+// Fused pull-stream + collide sweep: the dominant kernel of every step.
+//
+// stream_collide_bulk: one thread per cell, threads along x so that every
+// population plane is read and written in coalesced rows; the 19 loads of a
+// cell are independent and issued together. IBB: solid cells are never
+// swept (the pipe's fluid runs are listed as segments, see segments.h).
+// IBM: support cells only store rho and u* (first half of the direct
+// forcing, Sec. 2.1) and are collided later by ibm_collide.
+#include "lbm_internal.cuh"
+
+namespace lbmgb {
+
+struct SweepArgs {
+    const void *A;
+    void *B;
+    const unsigned long long *seg;  // optional row segments (see stream_collide_bulk)
+    long long nseg;
+    FastDiv fd_ny;  // row -> (y, z)
+    const uint8_t *flags;
+    const int *aux;
+    void *sup_ru;  // (rho, u*) per support site, arithmetic type of the storage
+    unsigned *status;
+    long long max_sites;
+    int nx, ny, nz;
+    long long N;
+    double F[3];
+    float Fs[3];  // F in single precision (a double-to-single conversion per cell is costly on GB300)
+    Rates rt;
+    SrtK sk;  // folded BGK factors (FP32 arithmetic, uniform force)
+};
+
+// BC: 0 periodic, 1 IBB, 2 IBM
+#ifndef LBM_BULK_MINB
+#define LBM_BULK_MINB 4
+#endif
+#ifndef LBM_BULK_PERSIST
+#define LBM_BULK_PERSIST 2  // persistent grid: 0 never, 1 always, 2 for segment sweeps
+#endif
+#ifndef LBM_BULK_SPEC
+#define LBM_BULK_SPEC 0
+#endif
+#ifndef LBM_SRT_FOLDED
+#define LBM_SRT_FOLDED 1
+#endif
+
+// Work items: without a segment list, one item = one row piece of
+// blockDim.x cells. With a segment list (IBB walls whose rows have a solid
+// margin, e.g. the pipe), one warp = one segment of up to 32 consecutive
+// cells inside the fluid extent of a row, so no lanes idle on the margin.
+// The block walks its items with a grid stride and loads the flag byte of
+// its next item before pulling the current one.
+template <int S, bool SRT, int BC, bool FORCE>
+__global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepArgs a) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R R;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool segs = a.nseg > 0;  // one warp per item
+    const int ipr = (nx + blockDim.x - 1) / blockDim.x;  // items per row (no segment list)
+    const int lane = threadIdx.x & 31;
+    const long long items = segs ? a.nseg : (long long)ny * nz * ipr;
+    const long long stride = segs ? (long long)gridDim.x * (blockDim.x * blockDim.y / 32) : (long long)gridDim.x * blockDim.y;
+    const T *__restrict__ A = (const T *)a.A;
+    T *__restrict__ B = (T *)a.B;
+    const size_t N = (size_t)a.N;
+    long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
+                       : (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    // segment: row (bits 0-31), x of lane 0 plus the leading zero lanes
+    // (32-47), lanes (48-55), leading (56-59) and trailing (60-63)
+    // zero-writing lanes; the
+    // descriptor of the next item is loaded one iteration ahead
+    unsigned long long sg_next = 0;
+    if (segs && w < items) sg_next = __ldg(a.seg + w);
+    auto cell_of = [&](long long item, int &x, int &row) {  // without a segment list
+        row = (int)(item / ipr);
+        x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
+    };
+    // segments cover fluid cells only: no flag byte is needed (IBB)
+    const bool read_flags = BC != 0 && !(BC == 1 && segs);
+    uint8_t fl_next = 0;
+    if (read_flags && w < items) {
+        int x, row;
+        cell_of(w, x, row);
+        if (x < nx) fl_next = a.flags[(size_t)row * nx + x];
+    }
+    for (; w < items; w += stride) {
+        int x, row;
+        bool zero = false;
+        if (segs) {
+            const unsigned long long sg = sg_next;
+            if (w + stride < items) sg_next = __ldg(a.seg + w + stride);
+            row = (int)(sg & 0xffffffffULL);
+            const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
+            const int fa = (int)((sg >> 56) & 15), zt = (int)(sg >> 60);
+            if (lane >= len) continue;
+            x = x0 - fa + lane;
+            // lanes on the solid cells that complete the 32-byte sectors at
+            // either end of a fluid run write zeros (full-sector stores; the
+            // slots are dead or rewritten as ghosts before they are read)
+            zero = lane < fa || lane >= len - zt;
+        } else {
+            cell_of(w, x, row);
+        }
+        const uint8_t fl = fl_next;
+        if (read_flags && w + stride < items) {
+            int x2, row2;
+            cell_of(w + stride, x2, row2);
+            if (x2 < nx) fl_next = a.flags[(size_t)row2 * nx + x2];
+        }
+        if (zero) {
+            const long long cz = (long long)row * nx + x;
+#pragma unroll
+            for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + cz, R(0));
+            continue;
+        }
+        if (x >= nx) continue;
+        if (!LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
+        const int z = (int)a.fd_ny.div((unsigned)row), y = row - z * ny;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        // row offsets of the source rows (y - c_y, z - c_z)
+        const int r00 = (y + ny * z) * nx;
+        const int rM0 = (ym + ny * z) * nx, rP0 = (yp + ny * z) * nx;
+        const int r0M = (y + ny * zm) * nx, r0P = (y + ny * zp) * nx;
+        const int rMM = (ym + ny * zm) * nx, rPP = (yp + ny * zp) * nx;
+        const int rMP = (ym + ny * zp) * nx, rPM = (yp + ny * zm) * nx;
+        const int c = r00 + x;
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        R g[19];
+        // pull: f_i(x) = f*_i(x - c_i)
+        g[0] = Store<S>::ld(A + c);
+        g[1] = Store<S>::ld(A + 1 * N + r00 + xm);
+        g[2] = Store<S>::ld(A + 2 * N + r00 + xp);
+        g[3] = Store<S>::ld(A + 3 * N + rM0 + x);
+        g[4] = Store<S>::ld(A + 4 * N + rP0 + x);
+        g[5] = Store<S>::ld(A + 5 * N + r0M + x);
+        g[6] = Store<S>::ld(A + 6 * N + r0P + x);
+        g[7] = Store<S>::ld(A + 7 * N + rM0 + xm);
+        g[8] = Store<S>::ld(A + 8 * N + rP0 + xp);
+        g[9] = Store<S>::ld(A + 9 * N + rP0 + xm);
+        g[10] = Store<S>::ld(A + 10 * N + rM0 + xp);
+        g[11] = Store<S>::ld(A + 11 * N + r0M + xm);
+        g[12] = Store<S>::ld(A + 12 * N + r0P + xp);
+        g[13] = Store<S>::ld(A + 13 * N + r0P + xm);
+        g[14] = Store<S>::ld(A + 14 * N + r0M + xp);
+        g[15] = Store<S>::ld(A + 15 * N + rMM + x);
+        g[16] = Store<S>::ld(A + 16 * N + rPP + x);
+        g[17] = Store<S>::ld(A + 17 * N + rMP + x);
+        g[18] = Store<S>::ld(A + 18 * N + rPM + x);
+        if (LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
+        const bool fluid = !(fl & FL_SOLID);
+        if (BC == 2 && (fl & FL_SUP)) {
+            // first half of direct forcing: rho and u* = (sum f c + F_ext/2)/rho
+            R drho = g[0];
+#pragma unroll
+            for (int i = 1; i < 19; i++) drho += g[i];
+            R jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
+            R jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
+            R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
+            if (FORCE && fluid) {
+                jx += R(0.5) * body_force<R>(a, 0);
+                jy += R(0.5) * body_force<R>(a, 1);
+                jz += R(0.5) * body_force<R>(a, 2);
+            }
+            const R rho = R(1) + drho;
+            const int s = a.aux[c];
+            if (s < 0 || s >= a.max_sites) continue;
+            R *ru = (R *)a.sup_ru + 4 * (size_t)s;
+            const R ir = R(1) / rho;
+            ru[0] = rho;
+            ru[1] = jx * ir;
+            ru[2] = jy * ir;
+            ru[3] = jz * ir;
+            continue;
+        }
+        R rho, ux, uy, uz;
+        const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
+        if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
+            collide_srt_k<FORCE>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
+        else
+            collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt,
+                                   rho, ux, uy, uz);
+        watchdog(rho, ux, uy, uz, a.status);
+#pragma unroll
+        for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
+    }
+}
+
+// ------------------------------------------------------------- launchers ---
+template <int S, bool SRT, int BC>
+static cudaError_t launch_bulk_t(Ctx &c, bool force) {
+    SweepArgs a{};
+    a.A = c.fA;
+    a.B = c.fB;
+    a.flags = c.flags;
+    a.aux = c.aux;
+    a.sup_ru = c.sup_ru;
+    a.status = c.d_status;
+    a.max_sites = c.max_sites;
+    a.nx = c.nx;
+    a.ny = c.ny;
+    a.nz = c.nz;
+    a.N = c.N;
+    for (int d = 0; d < 3; d++) {
+        a.F[d] = c.F[d];
+        a.Fs[d] = (float)c.F[d];
+    }
+    a.rt = c.rt;
+    a.sk = make_srt_k(c.rt.d_nu, c.F);
+    const bool segs = BC == 1 && c.nseg > 0;
+    a.seg = c.seg;
+    a.nseg = segs ? c.nseg : 0;
+    a.fd_ny = FastDiv((unsigned)c.ny);
+    int bx = ((c.nx + 31) / 32) * 32;
+    if (bx > 256) bx = 256;
+    int by = 256 / bx;
+    if (by < 1) by = 1;
+    if (segs) {
+        bx = 256;  // 8 warps, one segment each
+        by = 1;
+    }
+    const long long items = segs ? c.nseg : (long long)c.ny * c.nz * ((c.nx + bx - 1) / bx);
+    long long nb = segs ? (items + 7) / 8 : (items + by - 1) / by;
+    if (LBM_BULK_PERSIST == 1 || (LBM_BULK_PERSIST == 2 && segs)) {
+        // persistent grid: as many blocks as fit on the device at once
+        static int resident[4][2][3][2];
+        int &res = resident[S][SRT][BC][force ? 1 : 0];
+        if (res == 0) {
+            int per_sm = 0, dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (force)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true>, bx * by, 0);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false>, bx * by, 0);
+            res = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        }
+        if (nb > res) nb = res;
+    }
+    dim3 block(bx, by), grid((unsigned)nb);
+    count_launch(c, G_BULK);
+    if (force)
+        stream_collide_bulk<S, SRT, BC, true><<<grid, block, 0, c.stream>>>(a);
+    else
+        stream_collide_bulk<S, SRT, BC, false><<<grid, block, 0, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t launch_bulk_s(Ctx &c, int bc, bool force) {
+    const bool srt = c.rates == LBM_RATES_SRT;
+    const int m = bc == LBM_BC_NONE ? 0 : (bc == LBM_BC_IBB ? 1 : 2);
+    if (srt) {
+        if (m == 0) return launch_bulk_t<S, true, 0>(c, force);
+        if (m == 1) return launch_bulk_t<S, true, 1>(c, force);
+        return launch_bulk_t<S, true, 2>(c, force);
+    }
+    if (m == 0) return launch_bulk_t<S, false, 0>(c, force);
+    if (m == 1) return launch_bulk_t<S, false, 1>(c, force);
+    return launch_bulk_t<S, false, 2>(c, force);
+}
+
+cudaError_t launch_stream_collide(Ctx &c, int bc) {
+    const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
+    switch (c.storage) {
+    case LBM_F64: return launch_bulk_s<LBM_F64>(c, bc, force);
+    case LBM_F32: return launch_bulk_s<LBM_F32>(c, bc, force);
+    case LBM_F16S: return launch_bulk_s<LBM_F16S>(c, bc, force);
+    default: return launch_bulk_s<LBM_BF16S>(c, bc, force);
+    }
+}
+
+}  // namespace lbmgb
