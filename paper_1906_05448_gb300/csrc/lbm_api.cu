@@ -96,7 +96,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.xy_j = L.take(4 * (size_t)P.max_xy);
     P.xy_w = L.take(8 * (size_t)P.max_xy);
     P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32 + 1);
-    P.seg = L.take(8 * (size_t)P.max_seg);
+    P.seg = L.take(16 * (size_t)P.max_seg);
     P.slink = L.take(8 * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
@@ -515,7 +515,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.pipe_xy_j = (int *)(b + P.xy_j);
     c.pipe_xy_w = (double *)(b + P.xy_w);
     c.pipe_max_xy = P.max_xy;
-    c.seg = (unsigned long long *)(b + P.seg);
+    c.seg = (uint4 *)(b + P.seg);
     c.slink = (uint2 *)(b + P.slink);
     c.static_links = 0;
     c.max_seg = P.max_seg;
@@ -645,9 +645,12 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     const long long sec = (LBM_SEG_SECTOR && storage_bytes(c.storage) >= 4) ? 32 / (long long)storage_bytes(c.storage) : 1;
     std::vector<unsigned long long> segs;
     const bool seg_ok = build_sweep_segments(fl.data(), c.nx, c.ny, c.nz, FL_SOLID, sec, segs);
-    if (seg_ok && (long long)segs.size() <= c.max_seg) {
-        CK(cudaMemcpy(c.seg, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice));
-        c.nseg = (long long)segs.size();
+    std::vector<SweepItem> items;
+    if (seg_ok) pack_sweep_items(segs, items);
+    if (seg_ok && (long long)items.size() <= c.max_seg) {
+        static_assert(sizeof(SweepItem) == sizeof(uint4), "warp item layout");
+        CK(cudaMemcpy(c.seg, items.data(), sizeof(SweepItem) * items.size(), cudaMemcpyHostToDevice));
+        c.nseg = (long long)items.size();
     }
     // the wall is static: regroup its links by direction (cell order kept
     // inside a group) so that neighbouring threads of the ghost pass touch

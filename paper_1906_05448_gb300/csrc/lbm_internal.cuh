@@ -41,7 +41,7 @@ struct Ctx {
     int8_t *link_dir, *link_scheme;
     double *link_q, *link_fin, *link_dP, *link_dT;
     // row segments of the fluid extent (IBB walls with a solid margin)
-    unsigned long long *seg;
+    uint4 *seg;  // warp items of the pipe sweep (segments.h)
     long long nseg, max_seg;
     // static wall (pipe) links regrouped by direction for the ghost pass:
     // x = cell | scheme << 30, y = bits of q rounded to FP32

@@ -63,4 +63,56 @@ inline bool build_sweep_segments(const uint8_t *flags, int nx, int ny, int nz, i
     return true;
 }
 
+// Warp items of the sweep: up to two pieces of fluid runs (possibly of two
+// rows) share one warp, so that few lanes idle on short runs. A piece is
+// (row, word) with word = x of its lane 0 plus its leading zero lanes
+// (bits 0-15) | lanes (16-23) | leading zero lanes (24-27) | trailing zero
+// lanes (28-31); lanes 0 means no piece. Lanes [0, lanes_a) take piece a,
+// the next lanes_b lanes piece b. Pieces longer than the lanes left in a
+// warp are split; the zero lanes follow their cells.
+struct SweepItem {
+    unsigned row_a, word_a, row_b, word_b;
+};
+
+inline unsigned sweep_word(int x_lane0, int lanes, int lead, int trail) {
+    return (unsigned)(x_lane0 + lead) | ((unsigned)lanes << 16) | ((unsigned)lead << 24) | ((unsigned)trail << 28);
+}
+
+inline void pack_sweep_items(const std::vector<unsigned long long> &segs, std::vector<SweepItem> &items) {
+    items.clear();
+    SweepItem cur{0u, 0u, 0u, 0u};
+    int used = 0, parts = 0;
+    auto flush = [&]() {
+        if (parts > 0) items.push_back(cur);
+        cur = SweepItem{0u, 0u, 0u, 0u};
+        used = 0;
+        parts = 0;
+    };
+    for (const unsigned long long sg : segs) {
+        const unsigned row = (unsigned)(sg & 0xffffffffULL);
+        const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
+        const int fa = (int)((sg >> 56) & 15), zt = (int)(sg >> 60);
+        const int xl0 = x0 - fa;  // x of the piece's lane 0
+        for (int off = 0; off < len;) {
+            if (parts == 2 || used == 32) flush();
+            const int t = len - off < 32 - used ? len - off : 32 - used;
+            int lead = fa - off, trail = off + t - (len - zt);
+            lead = lead < 0 ? 0 : (lead > t ? t : lead);
+            trail = trail < 0 ? 0 : (trail > t ? t : trail);
+            const unsigned w = sweep_word(xl0 + off, t, lead, trail);
+            if (parts == 0) {
+                cur.row_a = row;
+                cur.word_a = w;
+            } else {
+                cur.row_b = row;
+                cur.word_b = w;
+            }
+            parts++;
+            used += t;
+            off += t;
+        }
+    }
+    flush();
+}
+
 }  // namespace lbmgb

@@ -13,7 +13,7 @@ namespace lbmgb {
 struct SweepArgs {
     const void *A;
     void *B;
-    const unsigned long long *seg;  // optional row segments (see stream_collide_bulk)
+    const uint4 *seg;  // optional warp items of fluid-run pieces (segments.h)
     long long nseg;
     FastDiv fd_ny;  // row -> (y, z)
     const uint8_t *flags;
@@ -30,9 +30,16 @@ struct SweepArgs {
 };
 
 // BC: 0 periodic, 1 IBB, 2 IBM
+// Resident blocks of 256 threads per SM the register allocation aims at
+// (measured per variant: the BGK box and the 16-bit pipe sweep fit 5 blocks
+// without spilling; the FP32 pipe sweep and MRT are fastest at 4).
 #ifndef LBM_BULK_MINB
-#define LBM_BULK_MINB 4
+#define LBM_BULK_MINB 0  // 0: per variant below
 #endif
+constexpr int bulk_min_blocks(int S, bool SRT, int BC) {
+    return LBM_BULK_MINB > 0 ? LBM_BULK_MINB
+                             : (!SRT || BC == 2 || S == LBM_F64) ? 4 : (BC == 0 ? 5 : (S == LBM_F32 ? 4 : 5));
+}
 #ifndef LBM_BULK_PERSIST
 #define LBM_BULK_PERSIST 2  // persistent grid: 0 never, 1 always, 2 for segment sweeps
 #endif
@@ -50,7 +57,7 @@ struct SweepArgs {
 // The block walks its items with a grid stride and loads the flag byte of
 // its next item before pulling the current one.
 template <int S, bool SRT, int BC, bool FORCE>
-__global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepArgs a) {
+__global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_collide_bulk(SweepArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -64,11 +71,9 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
     const size_t N = (size_t)a.N;
     long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
                        : (long long)blockIdx.x * blockDim.y + threadIdx.y;
-    // segment: row (bits 0-31), x of lane 0 plus the leading zero lanes
-    // (32-47), lanes (48-55), leading (56-59) and trailing (60-63)
-    // zero-writing lanes; the
-    // descriptor of the next item is loaded one iteration ahead
-    unsigned long long sg_next = 0;
+    // warp item: up to two pieces of fluid runs (row, word), see segments.h;
+    // the next item is loaded one iteration ahead
+    uint4 sg_next = make_uint4(0u, 0u, 0u, 0u);
     if (segs && w < items) sg_next = __ldg(a.seg + w);
     auto cell_of = [&](long long item, int &x, int &row) {  // without a segment list
         row = (int)(item / ipr);
@@ -86,17 +91,20 @@ __global__ void __launch_bounds__(256, LBM_BULK_MINB) stream_collide_bulk(SweepA
         int x, row;
         bool zero = false;
         if (segs) {
-            const unsigned long long sg = sg_next;
+            const uint4 sg = sg_next;
             if (w + stride < items) sg_next = __ldg(a.seg + w + stride);
-            row = (int)(sg & 0xffffffffULL);
-            const int x0 = (int)((sg >> 32) & 0xffff), len = (int)((sg >> 48) & 0xff);
-            const int fa = (int)((sg >> 56) & 15), zt = (int)(sg >> 60);
-            if (lane >= len) continue;
-            x = x0 - fa + lane;
+            const int la = (int)((sg.y >> 16) & 0xff);
+            const bool pa = lane < la;
+            const unsigned wd = pa ? sg.y : sg.w;
+            row = (int)(pa ? sg.x : sg.z);
+            const int lp = pa ? lane : lane - la;  // lane within the piece
+            const int len = (int)((wd >> 16) & 0xff), lead = (int)((wd >> 24) & 15), trail = (int)(wd >> 28);
+            if (lp >= len) continue;
+            x = (int)(wd & 0xffff) - lead + lp;
             // lanes on the solid cells that complete the 32-byte sectors at
             // either end of a fluid run write zeros (full-sector stores; the
             // slots are dead or rewritten as ghosts before they are read)
-            zero = lane < fa || lane >= len - zt;
+            zero = lp < lead || lp >= len - trail;
         } else {
             cell_of(w, x, row);
         }

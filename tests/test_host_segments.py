@@ -1,8 +1,9 @@
 """Host logic of the IBB sweep work list (segments.h), compiled with g++.
 
 Checks on seeded solid patterns: every fluid cell is swept by exactly one
-fluid lane, zero lanes sit on solid cells only, nothing leaves the grid, and
-every 32-byte sector holding a fluid cell is written whole.
+fluid lane, zero lanes sit on solid cells only, nothing leaves the grid,
+every 32-byte sector holding a fluid cell is written whole, and two pieces
+per warp keep the warps nearly full.
 """
 import os
 import shutil
@@ -29,8 +30,10 @@ int main(int argc, char **argv) {
     std::fclose(f);
     std::vector<unsigned long long> segs;
     if (!lbmgb::build_sweep_segments(fl.data(), nx, ny, nz, 1, sec, segs)) return 4;
+    std::vector<lbmgb::SweepItem> items;
+    lbmgb::pack_sweep_items(segs, items);
     FILE *o = std::fopen(argv[6], "wb");
-    std::fwrite(segs.data(), 8, segs.size(), o);
+    std::fwrite(items.data(), sizeof(lbmgb::SweepItem), items.size(), o);
     std::fclose(o);
     return 0;
 }
@@ -55,22 +58,29 @@ def run(harness, flags, sec):
     fin, fout = d / "fl.bin", d / "seg.bin"
     flags.astype(np.uint8).tofile(fin)
     subprocess.run([str(exe), str(nx), str(ny), str(nz), str(sec), str(fin), str(fout)], check=True)
-    return np.fromfile(fout, dtype=np.uint64)
+    return np.fromfile(fout, dtype=np.uint32).reshape(-1, 4)
 
 
-def decode(segs, nx):
-    """Per lane: global cell index and whether it is a zero lane."""
+def decode(items, nx):
+    """Per lane of every warp item: global cell index and whether it is a
+    zero lane."""
     cells, zero = [], []
-    for s in segs.tolist():
-        row = s & 0xffffffff
-        x0 = (s >> 32) & 0xffff
-        n = (s >> 48) & 0xff
-        fa = (s >> 56) & 15
-        zt = s >> 60
-        assert 1 <= n <= 32 and fa + zt <= n
-        for lane in range(n):
-            cells.append(row * nx + x0 - fa + lane)
-            zero.append(lane < fa or lane >= n - zt)
+    for k, (row_a, wa, row_b, wb) in enumerate(items.tolist()):
+        used = parts = 0
+        for row, w in ((row_a, wa), (row_b, wb)):
+            n = (w >> 16) & 0xff
+            if n == 0:
+                continue
+            x0, lead, trail = w & 0xffff, (w >> 24) & 15, w >> 28
+            assert lead + trail <= n
+            for lp in range(n):
+                cells.append(row * nx + x0 - lead + lp)
+                zero.append(lp < lead or lp >= n - trail)
+            used += n
+            parts += 1
+        assert 1 <= used <= 32
+        # the packer closes a warp only when it is full or holds two pieces
+        assert used == 32 or parts == 2 or k == len(items) - 1
     return np.array(cells, dtype=np.int64), np.array(zero, dtype=bool)
 
 
@@ -98,7 +108,8 @@ def test_segments_cover_fluid_once(harness, name, make, sec):
     nz, ny, nx = fl.shape
     N = fl.size
     flat = fl.reshape(-1)
-    cells, zero = decode(run(harness, np.ascontiguousarray(fl), sec), nx)
+    items = run(harness, np.ascontiguousarray(fl), sec)
+    cells, zero = decode(items, nx)
     assert np.all((cells >= 0) & (cells < N))
     fluid_lanes = cells[~zero]
     # every fluid cell exactly once, no solid cell as a fluid lane
