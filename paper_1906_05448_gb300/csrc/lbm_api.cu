@@ -47,7 +47,7 @@ struct Plan {
     size_t xy_start, xy_j, xy_w;
     long long max_xy;
     size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
-    size_t mX, mUnit, mdV, mUs, mF, mFacc, mFr, mB, mE, mpid, mfirst;
+    size_t mX, mUnit, mdV, mUd, mFaccR, mFacc, mFr, mB, mE, mpid, mfirst;
     size_t rho_f, u_f, partials, near_key, near_pid;
     size_t cl_w, cl_pk, cl_X, cl_Y, cl_cells, cl_eps;
     long long max_cl;
@@ -122,8 +122,8 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.mX = L.take(24 * mm);
     P.mUnit = L.take(24 * mm);
     P.mdV = L.take(8 * mm);
-    P.mUs = L.take(24 * mm);
-    P.mF = L.take(24 * mm);
+    P.mUd = L.take(24 * mm);
+    P.mFaccR = L.take(24 * mm);
     P.mFacc = L.take(24 * mm);
     P.mFr = L.take(24 * mm);
     P.mB = L.take(12 * mm);
@@ -548,8 +548,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.mX = (double *)(b + P.mX);
     c.mUnit = (double *)(b + P.mUnit);
     c.mdV = (double *)(b + P.mdV);
-    c.mUs = (double *)(b + P.mUs);
-    c.mF = (double *)(b + P.mF);
+    c.mUd = b + P.mUd;
+    c.mFaccR = b + P.mFaccR;
     c.mFacc = (double *)(b + P.mFacc);
     c.mFr = b + P.mFr;
     c.mB = (int *)(b + P.mB);

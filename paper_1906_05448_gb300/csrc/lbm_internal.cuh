@@ -64,7 +64,8 @@ struct Ctx {
     int *has_prev;
     // markers
     long long max_markers, nm;
-    double *mX, *mUnit, *mdV, *mUs, *mF, *mFacc;
+    double *mX, *mUnit, *mdV, *mFacc;
+    void *mUd, *mFaccR;  // desired marker velocity, pass force sum (arithmetic type of the storage)
     void *mFr;  // marker forces of the pass in the arithmetic type (spreading)
     int *mB;    // per marker: first stencil node floor(X) - 1 (3 ints, wrapped)
     void *mE;   // per marker: X - floor(X) in the arithmetic type (3 values)

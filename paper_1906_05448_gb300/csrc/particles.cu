@@ -336,9 +336,12 @@ __global__ void markers_place_kernel(double *mX, const double *mUnit, const int 
     }
 }
 
-// per marker: first stencil node floor(X) - 1 (wrapped) and X - floor(X)
+// per marker: first stencil node floor(X) - 1 (wrapped), X - floor(X), and
+// the desired velocity U_d = U_p + Omega_p x (X_l - X_p) of the rigid body
+// (zero for the pipe's ring markers), evaluated in FP64 once per step
 template <typename R>
-__global__ void marker_offsets_kernel(const double *mX, int *mB, R *mE, long long nm, int nx, int ny, int nz) {
+__global__ void marker_offsets_kernel(const double *mX, int *mB, R *mE, R *mUd, const int *mpid, const double *X,
+                                      const double *U, const double *W, long long nm, int nx, int ny, int nz) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nm) return;
     const int n[3] = {nx, ny, nz};
@@ -347,6 +350,17 @@ __global__ void marker_offsets_kernel(const double *mX, int *mB, R *mE, long lon
         mB[3 * l + d] = pwrap((int)f - 1, n[d]);
         mE[3 * l + d] = R(x - f);
     }
+    double Ud[3] = {0.0, 0.0, 0.0};
+    const int p = mpid[l];
+    if (p >= 0) {
+        const double r0 = pmimg(mX[3 * l] - X[3 * p], nx), r1 = pmimg(mX[3 * l + 1] - X[3 * p + 1], ny),
+                     r2 = pmimg(mX[3 * l + 2] - X[3 * p + 2], nz);
+        const double *Wp = W + 3 * p, *Up = U + 3 * p;
+        Ud[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
+        Ud[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
+        Ud[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
+    }
+    for (int d = 0; d < 3; d++) mUd[3 * l + d] = R(Ud[d]);
 }
 
 cudaError_t launch_marker_offsets(Ctx &c) {
@@ -354,9 +368,11 @@ cudaError_t launch_marker_offsets(Ctx &c) {
     const unsigned nb = (unsigned)((c.nm + 255) / 256);
     count_launch(c, G_GEOM);
     if (c.storage == LBM_F64)
-        marker_offsets_kernel<double><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (double *)c.mE, c.nm, c.nx, c.ny, c.nz);
+        marker_offsets_kernel<double><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (double *)c.mE, (double *)c.mUd, c.mpid,
+                                                                c.X, c.U, c.W, c.nm, c.nx, c.ny, c.nz);
     else
-        marker_offsets_kernel<float><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (float *)c.mE, c.nm, c.nx, c.ny, c.nz);
+        marker_offsets_kernel<float><<<nb, 256, 0, c.stream>>>(c.mX, c.mB, (float *)c.mE, (float *)c.mUd, c.mpid,
+                                                               c.X, c.U, c.W, c.nm, c.nx, c.ny, c.nz);
     return cudaGetLastError();
 }
 
@@ -434,8 +450,9 @@ __device__ __forceinline__ R peskin_r(R r) {
 struct IbmArgs {
     const double *mX, *mdV;
     const int *mpid;
-    double *mUs, *mF, *mFacc;
-    void *mFr;
+    double *mFacc;        // per-step marker force (sum of the passes), FP64
+    const void *mUd;      // desired velocity U_d at the marker (R)
+    void *mFaccR, *mFr;   // running sum of the passes' forces, force of this pass (R)
     const int *mB;
     const void *mE;
     const int *aux;
@@ -445,12 +462,12 @@ struct IbmArgs {
     const long long *counts;
     long long max_sites;
     int nx, ny, nz;
-    int pass;
+    int pass, last;
 };
 
 // Interpolation, one warp per marker: lane k takes stencil nodes k and k+32;
 // U*_l = sum u* delta, rho_l = sum rho delta (fixed butterfly reduction);
-// F_l = 2 rho_l (U_d - U*_l) in FP64.
+// F_l = 2 rho_l (U_d - U*_l).
 template <typename R>
 __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
     const long long l = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -484,27 +501,17 @@ __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
         U2 += __shfl_xor_sync(0xffffffffu, U2, o);
     }
     if (lane != 0) return;
-    double Ud[3] = {0, 0, 0};
-    const int p = a.mpid[l];
-    if (p >= 0) {
-        const double X0 = a.mX[3 * l], X1 = a.mX[3 * l + 1], X2 = a.mX[3 * l + 2];
-        const double r0 = pmimg(X0 - a.X[3 * p], a.nx), r1 = pmimg(X1 - a.X[3 * p + 1], a.ny),
-                     r2 = pmimg(X2 - a.X[3 * p + 2], a.nz);
-        const double *Wp = a.W + 3 * p, *Up = a.U + 3 * p;
-        Ud[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
-        Ud[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
-        Ud[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
-    }
-    const double U[3] = {double(U0), double(U1), double(U2)};
-    R *mFr = (R *)a.mFr;
-    a.mUs[3 * l] = U[0];
-    a.mUs[3 * l + 1] = U[1];
-    a.mUs[3 * l + 2] = U[2];
+    // F_l = 2 rho_l (U_d - U*_l) in the storage's arithmetic type; U_d was
+    // evaluated once per step (marker_offsets_kernel)
+    const R *Ud = (const R *)a.mUd + 3 * l;
+    const R U[3] = {U0, U1, U2};
+    R *mFr = (R *)a.mFr, *acc = (R *)a.mFaccR;
     for (int d = 0; d < 3; d++) {
-        const double Fl = 2.0 * double(rl) * (Ud[d] - U[d]);
-        a.mF[3 * l + d] = Fl;
-        mFr[3 * l + d] = R(Fl);
-        a.mFacc[3 * l + d] = a.pass == 0 ? Fl : a.mFacc[3 * l + d] + Fl;
+        const R Fl = R(2) * rl * (Ud[d] - U[d]);
+        mFr[3 * l + d] = Fl;
+        const R s = a.pass == 0 ? Fl : acc[3 * l + d] + Fl;
+        acc[3 * l + d] = s;
+        if (a.last) a.mFacc[3 * l + d] = double(s);
     }
 }
 
@@ -664,8 +671,8 @@ __global__ void __launch_bounds__(256) ibm_spread_particle_kernel(ParticleSpread
 
 template <typename R>
 static cudaError_t ibm_passes_t(Ctx &c) {
-    IbmArgs a{c.mX, c.mdV, c.mpid, c.mUs, c.mF, c.mFacc, c.mFr, c.mB, c.mE, c.aux, c.sup_ru, c.sup_F, c.sup_Fp,
-              c.X, c.U, c.W, c.nm, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, 0};
+    IbmArgs a{c.mX, c.mdV, c.mpid, c.mFacc, c.mUd, c.mFaccR, c.mFr, c.mB, c.mE, c.aux, c.sup_ru, c.sup_F, c.sup_Fp,
+              c.X, c.U, c.W, c.nm, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, 0, 0};
     long long ns = c.nsites_hint > 0 ? c.nsites_hint : c.max_sites;
     if (ns > c.max_sites) ns = c.max_sites;
     long long ub = (ns + 255) / 256;
@@ -687,6 +694,7 @@ static cudaError_t ibm_passes_t(Ctx &c) {
     }
     for (int pass = 0; pass < 3; pass++) {
         a.pass = pass;
+        a.last = pass == 2;
         if (c.nm > 0) {
             count_launch(c, G_IBM);
             ibm_interp_warp_kernel<R><<<(unsigned)((c.nm * 32 + 255) / 256), 256, 0, c.stream>>>(a);
