@@ -192,9 +192,12 @@ __global__ void near_key_kernel(unsigned long long *key, const uint8_t *flags, c
     const int r = (int)ceil(3.0 * Rp) + 2;
     const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
-    for (long long t = threadIdx.x; t < (long long)w * w * w; t += blockDim.x) {
-        const int x = dwrap(bx + (int)(t % w), nx), y = dwrap(by + (int)((t / w) % w), ny),
-                  z = dwrap(bz + (int)(t / ((long long)w * w)), nz);
+    const FastDiv fw((unsigned)w);
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = dwrap(bx + ix, nx), y = dwrap(by + iy, ny),
+                  z = dwrap(bz + iz, nz);
         const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
         if (flags[c] & FL_SOLID) continue;
         const double dx = dmimg(__dsub_rn((double)x, X[3 * p]), nx);

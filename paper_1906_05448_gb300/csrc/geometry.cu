@@ -67,6 +67,10 @@ struct SphereArgs {
 // clear pass: cells owned by p at the old position lose SOLID, gain
 // WAS_SOLID, and remember p in aux (needed by the refill).
 // mark pass: cells inside p at the new position gain SOLID, owner = lowest id.
+// The inside test is decided in FP32 away from the surface and by the exact
+// FP64 test (same operations and order as everywhere else) within a band of
+// 0.01 in d^2 around R^2, far wider than the FP32 error of d^2 here
+// (|d| < 2R + 4, coordinates below 2^16).
 template <bool CLEAR>
 __global__ void sphere_kernel(SphereArgs a) {
     const int p = blockIdx.x;
@@ -77,8 +81,13 @@ __global__ void sphere_kernel(SphereArgs a) {
     const int w = 2 * r + 2;
     const int total = w * w * w;
     const double R2 = __dmul_rn(R, R);
+    const float R2f = (float)R2, band = 0.01f;
+    const float X0 = (float)Xp[0], X1 = (float)Xp[1], X2 = (float)Xp[2];
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int x = gwrap(bx + t % w, a.nx), y = gwrap(by + (t / w) % w, a.ny), z = gwrap(bz + t / (w * w), a.nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = gwrap(bx + ix, a.nx), y = gwrap(by + iy, a.ny), z = gwrap(bz + iz, a.nz);
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
         if (CLEAR) {
             if (a.owner[c] == p) {
@@ -87,10 +96,23 @@ __global__ void sphere_kernel(SphereArgs a) {
                 a.flags[c] = (uint8_t)((a.flags[c] & ~FL_SOLID) | FL_WAS_SOLID);
             }
         } else {
-            const double dx = gmimg(__dsub_rn((double)x, Xp[0]), a.nx);
-            const double dy = gmimg(__dsub_rn((double)y, Xp[1]), a.ny);
-            const double dz = gmimg(__dsub_rn((double)z, Xp[2]), a.nz);
-            if (dist2(dx, dy, dz) <= R2) {
+            float fx = (float)x - X0, fy = (float)y - X1, fz = (float)z - X2;
+            fx = fx > 0.5f * a.nx ? fx - a.nx : (fx < -0.5f * a.nx ? fx + a.nx : fx);
+            fy = fy > 0.5f * a.ny ? fy - a.ny : (fy < -0.5f * a.ny ? fy + a.ny : fy);
+            fz = fz > 0.5f * a.nz ? fz - a.nz : (fz < -0.5f * a.nz ? fz + a.nz : fz);
+            const float d2f = fx * fx + fy * fy + fz * fz;
+            bool inside;
+            if (d2f < R2f - band) {
+                inside = true;
+            } else if (d2f > R2f + band) {
+                inside = false;
+            } else {
+                const double dx = gmimg(__dsub_rn((double)x, Xp[0]), a.nx);
+                const double dy = gmimg(__dsub_rn((double)y, Xp[1]), a.ny);
+                const double dz = gmimg(__dsub_rn((double)z, Xp[2]), a.nz);
+                inside = dist2(dx, dy, dz) <= R2;
+            }
+            if (inside) {
                 atomicMin(a.owner + c, p);
                 atomic_or_flag(a.flags, c, FL_SOLID);
             }
@@ -133,8 +155,11 @@ __global__ void refill_collect_kernel(RefillArgs a) {
     const int r = (int)ceil(a.R[p]) + 3;
     const int bx = (int)floor(Xp[0]) - r, by = (int)floor(Xp[1]) - r, bz = (int)floor(Xp[2]) - r;
     const int w = 2 * r + 2;
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
-        const int x = gwrap(bx + t % w, a.nx), y = gwrap(by + (t / w) % w, a.ny), z = gwrap(bz + t / (w * w), a.nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = gwrap(bx + ix, a.nx), y = gwrap(by + iy, a.ny), z = gwrap(bz + iz, a.nz);
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
         const uint8_t fl = a.flags[c];
         if (!(fl & FL_WAS_SOLID) || (fl & FL_SOLID) || a.aux[c] != p) continue;
@@ -257,8 +282,11 @@ __global__ void finish_kernel(uint8_t *flags, const double *X, const double *R, 
     const int r = (int)ceil(R[p]) + 3;
     const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
-        const int x = gwrap(bx + t % w, nx), y = gwrap(by + (t / w) % w, ny), z = gwrap(bz + t / (w * w), nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = gwrap(bx + ix, nx), y = gwrap(by + iy, ny), z = gwrap(bz + iz, nz);
         const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
         if (flags[c] & FL_WAS_SOLID) atomic_and_flag(flags, c, (uint8_t)~FL_WAS_SOLID);
     }
@@ -297,6 +325,7 @@ struct SiteArgs {
     double *link_q;
     long long max_sites, max_links;
     unsigned *status;
+    FastDiv dx, dxy;  // division by nx and nx * ny
 };
 
 // solid-neighbour mask of a fluid cell (bit l: x + c_l solid)
@@ -318,11 +347,66 @@ __device__ __forceinline__ void cell_info(const SiteArgs &a, long long c, bool &
     const uint8_t fl = a.flags[c];
     if (a.mode == 1) {
         if (fl & FL_SOLID) return;
-        const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
-        mask = solid_mask(a, x, y, z);
+        const unsigned zq = a.dxy.div((unsigned)c), rem = (unsigned)c - zq * (unsigned)(a.nx * a.ny);
+        const unsigned yq = a.dx.div(rem);
+        mask = solid_mask(a, (int)(rem - yq * (unsigned)a.nx), (int)yq, (int)zq);
         site = mask != 0;
     } else {
         site = (fl & FL_SUP) != 0;
+    }
+}
+
+// The CPT = 4 consecutive cells of a thread at once (mode 1, nx a multiple
+// of 4, so that the group starts a 4-byte word and stays in one row): the
+// solid bits of x0-1 .. x0+4 in each of the 9 rows y+dy, z+dz are read as
+// one word and two bytes, and the 18-neighbour masks are cut from them.
+__device__ __forceinline__ unsigned solid_bits6(const SiteArgs &a, long long rowbase, int x0) {
+    const unsigned mid = __ldg((const unsigned *)(a.flags + rowbase + x0));
+    const unsigned left = a.flags[rowbase + (x0 > 0 ? x0 - 1 : a.nx - 1)];
+    const unsigned right = a.flags[rowbase + (x0 + 4 < a.nx ? x0 + 4 : 0)];
+    const unsigned m = mid & 0x01010101u * FL_SOLID;
+    const unsigned four = ((m >> 0) & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u);
+    return ((left & FL_SOLID) ? 1u : 0u) | (four << 1) | ((right & FL_SOLID) ? 32u : 0u);
+}
+
+__device__ __forceinline__ void cell_info4(const SiteArgs &a, long long c0, bool site[CPT], unsigned mask[CPT]) {
+    const unsigned zq = a.dxy.div((unsigned)c0), rem = (unsigned)c0 - zq * (unsigned)(a.nx * a.ny);
+    const unsigned yq = a.dx.div(rem);
+    const int x0 = (int)(rem - yq * (unsigned)a.nx), y = (int)yq, z = (int)zq;
+    unsigned rows[3][3];  // [dz + 1][dy + 1]: bits of x0-1 .. x0+4
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++) {
+            if (dy != 0 && dz != 0) {
+                rows[dz + 1][dy + 1] = 0;  // no D3Q19 velocity has both
+                continue;
+            }
+            const int yy = gwrap(y + dy, a.ny), zz = gwrap(z + dz, a.nz);
+            rows[dz + 1][dy + 1] = solid_bits6(a, ((long long)zz * a.ny + yy) * a.nx, x0);
+        }
+    // the edge rows of D3Q19 (dy, dz both nonzero) take only the centre cell
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz += 2)
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy += 2) {
+            const int yy = gwrap(y + dy, a.ny), zz = gwrap(z + dz, a.nz);
+            const unsigned w = __ldg((const unsigned *)(a.flags + ((long long)zz * a.ny + yy) * a.nx + x0));
+            const unsigned m = w & 0x01010101u * FL_SOLID;
+            rows[dz + 1][dy + 1] = (((m >> 0) & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << 1;
+        }
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+        site[k] = false;
+        mask[k] = 0;
+        if (c0 + k >= a.N) continue;
+        if ((rows[1][1] >> (k + 1)) & 1u) continue;  // the cell itself is solid
+        unsigned m = 0;
+#pragma unroll
+        for (int l = 1; l < 19; l++)
+            if ((rows[cz(l) + 1][cy(l) + 1] >> (k + 1 + cx(l))) & 1u) m |= 1u << l;
+        mask[k] = m;
+        site[k] = m != 0;
     }
 }
 
@@ -358,12 +442,22 @@ __global__ void __launch_bounds__(CT) site_count_kernel(SiteArgs a) {
     __shared__ long long sh[CT / 32];
     const long long base = (long long)blockIdx.x * TILE + (long long)threadIdx.x * CPT;
     long long ns = 0, nl = 0;
-    for (int k = 0; k < CPT; k++) {
-        bool site;
-        unsigned mask;
-        cell_info(a, base + k, site, mask);
-        ns += site;
-        nl += __popc(mask);
+    if (a.mode == 1 && a.nx % 4 == 0 && base < a.N) {
+        bool site[CPT];
+        unsigned mask[CPT];
+        cell_info4(a, base, site, mask);
+        for (int k = 0; k < CPT; k++) {
+            ns += site[k];
+            nl += __popc(mask[k]);
+        }
+    } else {
+        for (int k = 0; k < CPT; k++) {
+            bool site;
+            unsigned mask;
+            cell_info(a, base + k, site, mask);
+            ns += site;
+            nl += __popc(mask);
+        }
     }
     long long ts, tl;
     block_exclusive_scan<long long>(ns, sh, ts);
@@ -374,34 +468,68 @@ __global__ void __launch_bounds__(CT) site_count_kernel(SiteArgs a) {
     }
 }
 
-// single block: exclusive scan of the per-tile counts
-__global__ void __launch_bounds__(CT) site_scan_kernel(SiteArgs a, int nblk) {
-    __shared__ long long sh[CT / 32];
-    __shared__ long long carry_s, carry_l;
-    if (threadIdx.x == 0) carry_s = carry_l = 0;
+// single block of ST threads: exclusive scan of the per-tile counts. Each
+// thread sums a run of consecutive tiles, the thread sums are scanned in the
+// block, and each run is written back from its thread's offset.
+constexpr int ST = 1024;
+__global__ void __launch_bounds__(ST) site_scan_kernel(SiteArgs a, int nblk) {
+    __shared__ long long ws[ST / 32], wl[ST / 32];
+    const int per = (nblk + ST - 1) / ST;
+    const int b0 = threadIdx.x * per, b1 = min(b0 + per, nblk);
+    long long ss = 0, sl = 0;
+    for (int b = b0; b < b1; b++) {
+        ss += a.blk_sites[b];
+        sl += a.blk_links[b];
+    }
+    // block exclusive scan of (ss, sl)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long is = ss, il = sl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long ts = __shfl_up_sync(0xffffffffu, is, o), tl = __shfl_up_sync(0xffffffffu, il, o);
+        if (lane >= o) {
+            is += ts;
+            il += tl;
+        }
+    }
+    if (lane == 31) {
+        ws[wid] = is;
+        wl[wid] = il;
+    }
     __syncthreads();
-    for (int b0 = 0; b0 < nblk; b0 += CT) {
-        const int b = b0 + threadIdx.x;
-        const long long vs = b < nblk ? a.blk_sites[b] : 0, vl = b < nblk ? a.blk_links[b] : 0;
-        long long ts, tl;
-        const long long es = block_exclusive_scan<long long>(vs, sh, ts);
-        const long long el = block_exclusive_scan<long long>(vl, sh, tl);
-        if (b < nblk) {
-            a.blk_sites[b] = carry_s + es;
-            a.blk_links[b] = carry_l + el;
+    if (wid == 0) {
+        long long vs = ws[lane], vl = wl[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long ts = __shfl_up_sync(0xffffffffu, vs, o), tl = __shfl_up_sync(0xffffffffu, vl, o);
+            if (lane >= o) {
+                vs += ts;
+                vl += tl;
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            carry_s += ts;
-            carry_l += tl;
-        }
-        __syncthreads();
+        ws[lane] = vs;
+        wl[lane] = vl;
     }
-    if (threadIdx.x == 0) {
-        a.counts[0] = carry_s;
-        a.counts[1] = carry_l;
-        if (carry_s > a.max_sites || carry_l > a.max_links) atomicOr(a.status, 2u);
+    __syncthreads();
+    long long es = (wid > 0 ? ws[wid - 1] : 0) + is - ss, el = (wid > 0 ? wl[wid - 1] : 0) + il - sl;
+    for (int b = b0; b < b1; b++) {
+        const long long vs = a.blk_sites[b], vl = a.blk_links[b];
+        a.blk_sites[b] = es;
+        a.blk_links[b] = el;
+        es += vs;
+        el += vl;
     }
+    if (threadIdx.x == ST - 1) {
+        a.counts[0] = es;
+        a.counts[1] = el;
+        if (es > a.max_sites || el > a.max_links) atomicOr(a.status, 2u);
+    }
+}
+
+// v / c2 for c2 = |c|^2 or its xy part: division by 1 or 2 is exact, so the
+// scaling returns the correctly rounded quotient; 0 gives the IEEE result
+__device__ __forceinline__ double exact_div_c2(double v, double c2) {
+    return c2 == 1.0 ? v : (c2 == 2.0 ? v * 0.5 : __ddiv_rn(v, c2));
 }
 
 __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, double &q, int &pid, int &scheme) {
@@ -422,7 +550,7 @@ __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, dou
         const double c0 = __dsub_rn(dist2(dx, dy, dz), __dmul_rn(Rp, Rp));
         double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(aa, c0));
         if (disc < 0.0) disc = 0.0;
-        t = __ddiv_rn(__dsub_rn(-b, __dsqrt_rn(disc)), aa);
+        t = exact_div_c2(__dsub_rn(-b, __dsqrt_rn(disc)), aa);
     } else {
         pid = -1;
         const double a2 = (double)(cx(l) * cx(l) + cy(l) * cy(l));
@@ -431,7 +559,7 @@ __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, dou
         const double c0 = __dsub_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(a.pR, a.pR));
         double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(a2, c0));
         if (disc < 0.0) disc = 0.0;
-        t = __ddiv_rn(__dadd_rn(-b, __dsqrt_rn(disc)), a2);
+        t = exact_div_c2(__dadd_rn(-b, __dsqrt_rn(disc)), a2);
     }
     if (t > 1.0) t = 1.0;
     if (t < 0.0) t = 0.0;
@@ -455,8 +583,12 @@ __global__ void __launch_bounds__(CT) site_emit_kernel(SiteArgs a) {
     bool site[CPT];
     unsigned mask[CPT];
     long long ns = 0, nl = 0;
+    if (a.mode == 1 && a.nx % 4 == 0 && base < a.N) {
+        cell_info4(a, base, site, mask);
+    } else {
+        for (int k = 0; k < CPT; k++) cell_info(a, base + k, site[k], mask[k]);
+    }
     for (int k = 0; k < CPT; k++) {
-        cell_info(a, base + k, site[k], mask[k]);
         ns += site[k];
         nl += __popc(mask[k]);
     }
@@ -505,9 +637,11 @@ __global__ void __launch_bounds__(256) link_geom_kernel(SiteArgs a) {
     const long long nl = a.counts[1] < a.max_links ? a.counts[1] : a.max_links;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nl;
          k += (long long)gridDim.x * blockDim.x) {
-        const long long c = a.link_cell[k];
+        const unsigned c = (unsigned)a.link_cell[k];
         const int l = a.link_dir[k];
-        const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
+        const unsigned zq = a.dxy.div(c), rem = c - zq * (unsigned)(a.nx * a.ny);
+        const unsigned yq = a.dx.div(rem);
+        const int x = (int)(rem - yq * (unsigned)a.nx), y = (int)yq, z = (int)zq;
         double q;
         int pid, sch;
         link_geometry(a, x, y, z, l, q, pid, sch);
@@ -548,10 +682,12 @@ cudaError_t build_sites(Ctx &c, int mode) {
     a.max_sites = c.max_sites;
     a.max_links = c.max_links;
     a.status = c.d_status;
+    a.dx = FastDiv((unsigned)c.nx);
+    a.dxy = FastDiv((unsigned)(c.nx * c.ny));
     const int nblk = (int)((c.N + TILE - 1) / TILE);
     count_launch(c, G_GEOM, mode == 1 ? 4 : 3);
     site_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
-    site_scan_kernel<<<1, CT, 0, c.stream>>>(a, nblk);
+    site_scan_kernel<<<1, ST, 0, c.stream>>>(a, nblk);
     site_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
     if (mode == 1) {
         long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;

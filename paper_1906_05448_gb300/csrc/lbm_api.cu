@@ -40,7 +40,7 @@ struct Plan {
     int max_np, nblk;
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
-    size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_fin, link_dP, link_dT;
+    size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_dP, link_dT;
     size_t blk_sites, blk_links, counts, status, seg, slink, refill;
     long long max_refill;
     long long max_seg;
@@ -88,7 +88,6 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.link_dir = L.take(ml);
     P.link_scheme = L.take(ml);
     P.link_q = L.take(8 * ml);
-    P.link_fin = L.take(8 * ml);
     P.link_dP = L.take(24 * ml);
     P.link_dT = L.take(24 * ml);
     P.max_xy = 64LL * (g->nx + g->ny);
@@ -508,9 +507,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.link_dir = (int8_t *)(b + P.link_dir);
     c.link_scheme = (int8_t *)(b + P.link_scheme);
     c.link_q = (double *)(b + P.link_q);
-    c.link_fin = (double *)(b + P.link_fin);
-    c.link_dP = (double *)(b + P.link_dP);
-    c.link_dT = (double *)(b + P.link_dT);
+    c.link_dP = b + P.link_dP;
+    c.link_dT = b + P.link_dT;
     c.pipe_xy_start = (int *)(b + P.xy_start);
     c.pipe_xy_j = (int *)(b + P.xy_j);
     c.pipe_xy_w = (double *)(b + P.xy_w);

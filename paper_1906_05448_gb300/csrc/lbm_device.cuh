@@ -87,8 +87,8 @@ inline size_t storage_bytes(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4
 // shifts (Granlund & Montgomery 1994), valid for every 32-bit dividend.
 struct FastDiv {
     unsigned d, m, s;
-    FastDiv() : d(1), m(0), s(0) {}
-    explicit FastDiv(unsigned dd) : d(dd) {
+    __host__ __device__ FastDiv() : d(1), m(0), s(0) {}
+    __host__ __device__ explicit FastDiv(unsigned dd) : d(dd) {
         unsigned l = 0;
         while ((1ull << l) < dd) l++;
         s = l;
@@ -103,6 +103,15 @@ struct FastDiv {
         return s == 0 ? n : (t + ((n - t) >> 1)) >> (s - 1);
     }
 };
+
+// t -> (ix, iy, iz) in a w x w x w box, x fastest (two multiply-shift
+// divisions instead of integer division)
+__device__ __forceinline__ void box_coords(int t, const FastDiv &fw, int w, int &ix, int &iy, int &iz) {
+    const unsigned q1 = fw.div((unsigned)t), q2 = fw.div(q1);
+    ix = t - (int)q1 * w;
+    iy = (int)q1 - (int)q2 * w;
+    iz = (int)q2;
+}
 
 // ------------------------------------------------------------ collision ----
 struct Rates {

@@ -39,7 +39,8 @@ struct Ctx {
     long long max_links;
     int *link_cell, *link_pid;
     int8_t *link_dir, *link_scheme;
-    double *link_q, *link_fin, *link_dP, *link_dT;
+    double *link_q;
+    void *link_dP, *link_dT;  // per-link momentum exchange and torque (arithmetic type of the storage)
     // row segments of the fluid extent (IBB walls with a solid margin)
     uint4 *seg;  // warp items of the pipe sweep (segments.h)
     long long nseg, max_seg;

@@ -45,21 +45,29 @@ struct GimemArgs {
     const uint8_t *flags;
     const int *aux, *site_first, *link_pid;
     const unsigned *site_mask;
-    const double *link_dP, *link_dT, *X, *R;
+    const void *link_dP, *link_dT;  // arithmetic type of the storage
+    const double *X, *R;
     double *Fh, *Th;
     int nx, ny, nz;
     long long max_sites;
 };
 
+template <typename Rl>
 __global__ void __launch_bounds__(PB) gimem_reduce_kernel(GimemArgs a) {
+    const Rl *dP = (const Rl *)a.link_dP, *dT = (const Rl *)a.link_dT;
     __shared__ double sh[6 * PB];
     const int p = blockIdx.x;
     const int r = (int)ceil(a.R[p]) + 2;
     const int bx = (int)floor(a.X[3 * p]) - r, by = (int)floor(a.X[3 * p + 1]) - r, bz = (int)floor(a.X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    // per-thread partial sums in the storage's arithmetic type (a few links
+    // each), then the fixed-order FP64 block sum
+    Rl v[6] = {0, 0, 0, 0, 0, 0};
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += PB) {
-        const int x = pwrap(bx + t % w, a.nx), y = pwrap(by + (t / w) % w, a.ny), z = pwrap(bz + t / (w * w), a.nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = pwrap(bx + ix, a.nx), y = pwrap(by + iy, a.ny), z = pwrap(bz + iz, a.nz);
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
         if (!(a.flags[c] & FL_BND)) continue;
         const int s = a.aux[c];
@@ -69,16 +77,18 @@ __global__ void __launch_bounds__(PB) gimem_reduce_kernel(GimemArgs a) {
         for (int k = first; k < first + n; k++) {
             if (a.link_pid[k] != p) continue;
             for (int d = 0; d < 3; d++) {
-                v[d] += a.link_dP[3 * k + d];
-                v[3 + d] += a.link_dT[3 * k + d];
+                v[d] += dP[3 * k + d];
+                v[3 + d] += dT[3 * k + d];
             }
         }
     }
-    block_sum<6>(v, sh);
+    double vd[6];
+    for (int d = 0; d < 6; d++) vd[d] = double(v[d]);
+    block_sum<6>(vd, sh);
     if (threadIdx.x == 0)
         for (int d = 0; d < 3; d++) {
-            a.Fh[3 * p + d] = v[d];
-            a.Th[3 * p + d] = v[3 + d];
+            a.Fh[3 * p + d] = vd[d];
+            a.Th[3 * p + d] = vd[3 + d];
         }
 }
 
@@ -87,7 +97,10 @@ cudaError_t launch_gimem(Ctx &c) {
     GimemArgs a{c.flags, c.aux, c.site_first, c.link_pid, c.site_mask, c.link_dP, c.link_dT,
                 c.X, c.R, c.Fh, c.Th, c.nx, c.ny, c.nz, c.max_sites};
     count_launch(c, G_PART);
-    gimem_reduce_kernel<<<c.np, PB, 0, c.stream>>>(a);
+    if (c.storage == LBM_F64)
+        gimem_reduce_kernel<double><<<c.np, PB, 0, c.stream>>>(a);
+    else
+        gimem_reduce_kernel<float><<<c.np, PB, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -160,8 +173,10 @@ __global__ void __launch_bounds__(PB) volume_kernel(VolArgs a) {
     const double fx = Xp[0] - floor(Xp[0]), fy = Xp[1] - floor(Xp[1]), fz = Xp[2] - floor(Xp[2]);
     Rt v[7] = {0, 0, 0, 0, 0, 0, 0};
     const Rt *su = (const Rt *)a.sup_ru;
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += PB) {
-        const int ix = t % w, iy = (t / w) % w, iz = t / (w * w);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
         const int x = pwrap(bx + ix, a.nx), y = pwrap(by + iy, a.ny), z = pwrap(bz + iz, a.nz);
         const Rt rx = Rt(ix - r) - Rt(fx), ry = Rt(iy - r) - Rt(fy), rz = Rt(iz - r) - Rt(fz);
         const Rt al = solid_fraction<Rt>(rx, ry, rz, Rt(Rp));
@@ -415,8 +430,11 @@ __global__ void mark_interior_kernel(uint8_t *flags, const double *X, const doub
     const int r = (int)ceil(Rp) + 1;
     const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
-        const int x = pwrap(bx + t % w, nx), y = pwrap(by + (t / w) % w, ny), z = pwrap(bz + t / (w * w), nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = pwrap(bx + ix, nx), y = pwrap(by + iy, ny), z = pwrap(bz + iz, nz);
         const double rx = pmimg(x - X[3 * p], nx), ry = pmimg(y - X[3 * p + 1], ny), rz = pmimg(z - X[3 * p + 2], nz);
         if (rx * rx + ry * ry + rz * rz < (Rp + 1.0) * (Rp + 1.0))
             flag_or(flags, (long long)x + (long long)nx * (y + (long long)ny * z), FL_SUP);
@@ -788,8 +806,11 @@ __global__ void rigid_overwrite_kernel(void *A, const uint8_t *flags, const int 
     const int r = (int)ceil(R[p]) + 1;
     const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
+    const FastDiv fw((unsigned)w);
     for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
-        const int x = pwrap(bx + t % w, nx), y = pwrap(by + (t / w) % w, ny), z = pwrap(bz + t / (w * w), nz);
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const int x = pwrap(bx + ix, nx), y = pwrap(by + iy, ny), z = pwrap(bz + iz, nz);
         const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
         if (!(flags[c] & FL_SOLID) || owner[c] != p) continue;
         double rho, u[3];

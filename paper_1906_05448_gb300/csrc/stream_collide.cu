@@ -66,7 +66,7 @@ struct LinkArgs {
     const int *link_cell, *link_pid;
     const int8_t *link_dir, *link_scheme;
     const double *link_q;
-    double *link_fin, *link_dP, *link_dT;
+    void *link_dP, *link_dT;  // per-link momentum exchange and torque (arithmetic type of the storage)
     const double *X, *U, *W;
     const long long *counts;  // [1]: number of links (device)
     long long max_links;
@@ -105,37 +105,76 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         const int i = opp(l);
         const R fl0 = Store<S>::ld(A + (size_t)l * N + c);  // f*_l(x_f), toward the wall
         const R fi0 = Store<S>::ld(A + (size_t)i * N + c);  // f*_ibar(x_f)
-        double uw[3] = {0.0, 0.0, 0.0};
-        if (PART && pid >= 0) {
-            const double r0 = mimg(x + q * lx - a.X[3 * pid + 0], nx);
-            const double r1 = mimg(y + q * ly - a.X[3 * pid + 1], ny);
-            const double r2 = mimg(z + q * lz - a.X[3 * pid + 2], nz);
-            const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
-            uw[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
-            uw[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
-            uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
-        }
-        // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
-        // (zero at a fixed wall: skip its FP64 arithmetic)
-        const R D = (PART && pid >= 0) ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
-        const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, D, fl0, fi0);
-        Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
-        if (PART && pid >= 0) {
-            a.link_fin[k] = double(v);
-            // momentum exchange with unshifted f = g + w (w_l = w_ibar)
-            const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
-            const double dP0 = (lx - uw[0]) * fo - (-lx - uw[0]) * fi;
-            const double dP1 = (ly - uw[1]) * fo - (-ly - uw[1]) * fi;
-            const double dP2 = (lz - uw[2]) * fo - (-lz - uw[2]) * fi;
-            const double m0 = mimg(x + 0.5 * lx - a.X[3 * pid + 0], nx);
-            const double m1 = mimg(y + 0.5 * ly - a.X[3 * pid + 1], ny);
-            const double m2 = mimg(z + 0.5 * lz - a.X[3 * pid + 2], nz);
-            a.link_dP[3 * k + 0] = dP0;
-            a.link_dP[3 * k + 1] = dP1;
-            a.link_dP[3 * k + 2] = dP2;
-            a.link_dT[3 * k + 0] = m1 * dP2 - m2 * dP1;
-            a.link_dT[3 * k + 1] = m2 * dP0 - m0 * dP2;
-            a.link_dT[3 * k + 2] = m0 * dP1 - m1 * dP0;
+        if constexpr (!PART) {
+            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, R(0), fl0, fi0);
+            Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
+        } else if constexpr (sizeof(R) == 8) {
+            // FP64 storage: wall velocity and momentum exchange in FP64
+            double uw[3] = {0.0, 0.0, 0.0};
+            if (pid >= 0) {
+                const double r0 = mimg(x + q * lx - a.X[3 * pid + 0], nx);
+                const double r1 = mimg(y + q * ly - a.X[3 * pid + 1], ny);
+                const double r2 = mimg(z + q * lz - a.X[3 * pid + 2], nz);
+                const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
+                uw[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
+                uw[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
+                uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
+            }
+            // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
+            const R Dw = pid >= 0 ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
+            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, Dw, fl0, fi0);
+            Store<S>::st(A + (size_t)i * N + cb, v);
+            if (pid >= 0) {
+                // momentum exchange with unshifted f = g + w (w_l = w_ibar)
+                const double fo = double(fl0) + wgt(l), fi = double(v) + wgt(i);
+                const double dP0 = (lx - uw[0]) * fo - (-lx - uw[0]) * fi;
+                const double dP1 = (ly - uw[1]) * fo - (-ly - uw[1]) * fi;
+                const double dP2 = (lz - uw[2]) * fo - (-lz - uw[2]) * fi;
+                const double m0 = mimg(x + 0.5 * lx - a.X[3 * pid + 0], nx);
+                const double m1 = mimg(y + 0.5 * ly - a.X[3 * pid + 1], ny);
+                const double m2 = mimg(z + 0.5 * lz - a.X[3 * pid + 2], nz);
+                double *dP = (double *)a.link_dP + 3 * k, *dT = (double *)a.link_dT + 3 * k;
+                dP[0] = dP0;
+                dP[1] = dP1;
+                dP[2] = dP2;
+                dT[0] = m1 * dP2 - m2 * dP1;
+                dT[1] = m2 * dP0 - m0 * dP2;
+                dT[2] = m0 * dP1 - m1 * dP0;
+            }
+        } else {
+            // 32- and 16-bit storage: the same in FP32 after one FP64
+            // difference x_f - X_p per component (FP64 stays in the sums)
+            float d[3] = {0.0f, 0.0f, 0.0f}, uw[3] = {0.0f, 0.0f, 0.0f};
+            const float qf = float(q);
+            if (pid >= 0) {
+                d[0] = float(mimg(double(x) - a.X[3 * pid + 0], nx));
+                d[1] = float(mimg(double(y) - a.X[3 * pid + 1], ny));
+                d[2] = float(mimg(double(z) - a.X[3 * pid + 2], nz));
+                const float r0 = d[0] + qf * lx, r1 = d[1] + qf * ly, r2 = d[2] + qf * lz;
+                const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
+                const float W0 = float(Wp[0]), W1 = float(Wp[1]), W2 = float(Wp[2]);
+                uw[0] = float(Up[0]) + (W1 * r2 - W2 * r1);
+                uw[1] = float(Up[1]) + (W2 * r0 - W0 * r2);
+                uw[2] = float(Up[2]) + (W0 * r1 - W1 * r0);
+            }
+            const float w_l = float(wgt(l));
+            const float Dw = pid >= 0 ? -6.0f * w_l * (lx * uw[0] + ly * uw[1] + lz * uw[2]) : 0.0f;
+            const float v = ibb_value<S>(A, N, l, i, sch, qf, c1, c2, Dw, fl0, fi0);
+            Store<S>::st(A + (size_t)i * N + cb, v);
+            if (pid >= 0) {
+                const float fo = fl0 + w_l, fi = v + w_l;
+                const float dP0 = (lx - uw[0]) * fo - (-lx - uw[0]) * fi;
+                const float dP1 = (ly - uw[1]) * fo - (-ly - uw[1]) * fi;
+                const float dP2 = (lz - uw[2]) * fo - (-lz - uw[2]) * fi;
+                const float m0 = d[0] + 0.5f * lx, m1 = d[1] + 0.5f * ly, m2 = d[2] + 0.5f * lz;
+                float *dP = (float *)a.link_dP + 3 * k, *dT = (float *)a.link_dT + 3 * k;
+                dP[0] = dP0;
+                dP[1] = dP1;
+                dP[2] = dP2;
+                dT[0] = m1 * dP2 - m2 * dP1;
+                dT[1] = m2 * dP0 - m0 * dP2;
+                dT[2] = m0 * dP1 - m1 * dP0;
+            }
         }
     }
 }
@@ -264,7 +303,7 @@ static cudaError_t launch_links_s(Ctx &c) {
         ibb_links_static<S><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
         return cudaGetLastError();
     }
-    LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_fin, c.link_dP, c.link_dT,
+    LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_dP, c.link_dT,
                c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N,
                FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny))};
     long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;

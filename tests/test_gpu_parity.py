@@ -253,3 +253,27 @@ def test_16bit_storage_error_bounded(lbm, storage, tol):
     o.step(100)
     ug, uo = g.macro()[1], o.macro()[1]
     assert rel(ug, uo) < tol
+
+
+@pytest.mark.parametrize("storage,tol", [("f16s", 2e-3), ("bf16s", 3e-2)])
+def test_16bit_storage_ragged_rows_and_pipe(lbm, storage, tol):
+    """16-bit storage on a 70-wide periodic box (rows of two and a ragged
+    piece, periodic x ends) and on a pipe swept by fluid-run segments."""
+    nx, ny, nz = 70, 18, 10
+    u = workloads.noise_velocity((nz, ny, nx), 0.02, seed=5)
+    g, o = pair(lbm, (nz, ny, nx), 0.6, force=(1e-5, 0, 0), storage=lbm.STORAGE[storage])
+    g.init_velocity(u)
+    o.init_velocity(u)
+    g.step(100)
+    o.step(100)
+    assert rel(g.macro()[1], o.macro()[1]) < tol
+    nx, ny, nz, R = 46, 46, 8, 21.5
+    g, o = pair(lbm, (nz, ny, nx), 0.6, force=(0, 0, 2e-6), storage=lbm.STORAGE[storage])
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.02, perturbation=0.1, seed=4)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.set_pipe(R)
+    g.step(100, lbm.BC_IBB)
+    o.step(100, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0
+    assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol

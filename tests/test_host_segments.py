@@ -129,3 +129,4 @@ def test_segments_cover_fluid_once(harness, name, make, sec):
         if len(seg) == sec:
             assert written[seg].all(), (name, s0)
 
+
