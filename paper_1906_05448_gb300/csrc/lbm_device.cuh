@@ -73,6 +73,10 @@ template <> struct Store<LBM_F16S> {
         return __half2float(__ldg(p)) * (1.0f / F16_SCALE);
     }
     static __device__ __forceinline__ void st(T *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
+    // the stored number itself (g * 2^10); the scale is a power of two, so
+    // arithmetic on scaled numbers rounds exactly as on unscaled ones
+    static __device__ __forceinline__ float ld_scaled(const T *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st_scaled(T *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Store<LBM_BF16S> {
     typedef __nv_bfloat16 T;
@@ -159,17 +163,27 @@ inline SrtK make_srt_k(double omega, const double F[3]) {
     return k;
 }
 
-template <bool FORCE>
+// SC: populations come in and go out multiplied by 2^SC (FP16 storage keeps
+// g * 2^10); every product with 2^SC or 2^-SC is exact, so the results are
+// those of the unscaled step, scaled.
+template <bool FORCE, int SC = 0>
 __device__ __forceinline__ void collide_srt_k(float g[19], const SrtK &k, float &rho_o, float &ux_o, float &uy_o,
                                               float &uz_o) {
+    constexpr float up = float(1u << SC), down = 1.0f / float(1u << SC);
     float drho = g[0];
 #pragma unroll
     for (int i = 1; i < 19; i++) drho += g[i];
     float jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
     float jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
     float jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
+    if (SC != 0) {
+        drho *= down;
+        jx *= down;
+        jy *= down;
+        jz *= down;
+    }
     const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
+    const float irho = __frcp_rn(rho);
     if (FORCE) {
         jx += k.hF[0];
         jy += k.hF[1];
@@ -188,8 +202,8 @@ __device__ __forceinline__ void collide_srt_k(float g[19], const SrtK &k, float 
     for (int i = 0; i < 19; i++) {
         const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
         const float P = fmaf(cu, fmaf(r45, cu, r3), base);
-        float v = fmaf(k.om, fmaf(float(wgt(i)), P, -g[i]), g[i]);
-        if (FORCE) v = fmaf(k.L[i], cu, v) + fmaf(-k.cw[i], uF3, k.K[i]);
+        float v = fmaf(k.om, fmaf(float(wgt(i)) * up, P, -g[i]), g[i]);
+        if (FORCE) v = fmaf(k.L[i] * up, cu, v) + fmaf(-k.cw[i] * up, uF3, k.K[i] * up);
         g[i] = v;
     }
 }

@@ -8,6 +8,8 @@
 // forcing, Sec. 2.1) and are collided later by ibm_collide.
 #include "lbm_internal.cuh"
 
+#include <type_traits>
+
 namespace lbmgb {
 
 struct SweepArgs {
@@ -49,6 +51,9 @@ constexpr int bulk_min_blocks(int S, bool SRT, int BC) {
 #ifndef LBM_SRT_FOLDED
 #define LBM_SRT_FOLDED 1
 #endif
+#ifndef LBM_IDX32
+#define LBM_IDX32 1  // 32-bit element indices where they fit
+#endif
 
 // Work items: without a segment list, one item = one row piece of
 // blockDim.x cells. With a segment list (IBB walls whose rows have a solid
@@ -56,7 +61,7 @@ constexpr int bulk_min_blocks(int S, bool SRT, int BC) {
 // cells inside the fluid extent of a row, so no lanes idle on the margin.
 // The block walks its items with a grid stride and loads the flag byte of
 // its next item before pulling the current one.
-template <int S, bool SRT, int BC, bool FORCE>
+template <int S, bool SRT, int BC, bool FORCE, bool IDX32>
 __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_collide_bulk(SweepArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
@@ -68,7 +73,17 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
     const long long stride = segs ? (long long)gridDim.x * (blockDim.x * blockDim.y / 32) : (long long)gridDim.x * blockDim.y;
     const T *__restrict__ A = (const T *)a.A;
     T *__restrict__ B = (T *)a.B;
-    const size_t N = (size_t)a.N;
+    // element index type: 32-bit when every index fits (19 N < 2^32), so an
+    // address is one 32-bit add and one scaled add to the plane base
+    typedef typename std::conditional<IDX32, unsigned, size_t>::type IX;
+    const IX N = (IX)a.N;
+    // FP16 with the folded BGK works on the stored (scaled) numbers
+    static_assert(F16_SCALE == 1024.0f, "the scaled FP16 path assumes g * 2^10");
+    constexpr bool scaled = S == LBM_F16S && SRT && BC != 2 && LBM_SRT_FOLDED;
+    auto ld = [](const T *p) -> R {
+        if constexpr (scaled) return Store<LBM_F16S>::ld_scaled(p);
+        else return Store<S>::ld(p);
+    };
     long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
                        : (long long)blockIdx.x * blockDim.y + threadIdx.y;
     // warp item: up to two pieces of fluid runs (row, word), see segments.h;
@@ -117,7 +132,7 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         if (zero) {
             const long long cz = (long long)row * nx + x;
 #pragma unroll
-            for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + cz, R(0));
+            for (int i = 0; i < 19; i++) Store<S>::st(B + (IX(i) * N + IX(cz)), R(0));
             continue;
         }
         if (x >= nx) continue;
@@ -135,25 +150,25 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         R g[19];
         // pull: f_i(x) = f*_i(x - c_i)
-        g[0] = Store<S>::ld(A + c);
-        g[1] = Store<S>::ld(A + 1 * N + r00 + xm);
-        g[2] = Store<S>::ld(A + 2 * N + r00 + xp);
-        g[3] = Store<S>::ld(A + 3 * N + rM0 + x);
-        g[4] = Store<S>::ld(A + 4 * N + rP0 + x);
-        g[5] = Store<S>::ld(A + 5 * N + r0M + x);
-        g[6] = Store<S>::ld(A + 6 * N + r0P + x);
-        g[7] = Store<S>::ld(A + 7 * N + rM0 + xm);
-        g[8] = Store<S>::ld(A + 8 * N + rP0 + xp);
-        g[9] = Store<S>::ld(A + 9 * N + rP0 + xm);
-        g[10] = Store<S>::ld(A + 10 * N + rM0 + xp);
-        g[11] = Store<S>::ld(A + 11 * N + r0M + xm);
-        g[12] = Store<S>::ld(A + 12 * N + r0P + xp);
-        g[13] = Store<S>::ld(A + 13 * N + r0P + xm);
-        g[14] = Store<S>::ld(A + 14 * N + r0M + xp);
-        g[15] = Store<S>::ld(A + 15 * N + rMM + x);
-        g[16] = Store<S>::ld(A + 16 * N + rPP + x);
-        g[17] = Store<S>::ld(A + 17 * N + rMP + x);
-        g[18] = Store<S>::ld(A + 18 * N + rPM + x);
+        g[0] = ld(A + IX(c));
+        g[1] = ld(A + (IX(1) * N + IX(r00 + xm)));
+        g[2] = ld(A + (IX(2) * N + IX(r00 + xp)));
+        g[3] = ld(A + (IX(3) * N + IX(rM0 + x)));
+        g[4] = ld(A + (IX(4) * N + IX(rP0 + x)));
+        g[5] = ld(A + (IX(5) * N + IX(r0M + x)));
+        g[6] = ld(A + (IX(6) * N + IX(r0P + x)));
+        g[7] = ld(A + (IX(7) * N + IX(rM0 + xm)));
+        g[8] = ld(A + (IX(8) * N + IX(rP0 + xp)));
+        g[9] = ld(A + (IX(9) * N + IX(rP0 + xm)));
+        g[10] = ld(A + (IX(10) * N + IX(rM0 + xp)));
+        g[11] = ld(A + (IX(11) * N + IX(r0M + xm)));
+        g[12] = ld(A + (IX(12) * N + IX(r0P + xp)));
+        g[13] = ld(A + (IX(13) * N + IX(r0P + xm)));
+        g[14] = ld(A + (IX(14) * N + IX(r0M + xp)));
+        g[15] = ld(A + (IX(15) * N + IX(rMM + x)));
+        g[16] = ld(A + (IX(16) * N + IX(rPP + x)));
+        g[17] = ld(A + (IX(17) * N + IX(rMP + x)));
+        g[18] = ld(A + (IX(18) * N + IX(rPM + x)));
         if (LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
         const bool fluid = !(fl & FL_SOLID);
         if (BC == 2 && (fl & FL_SUP)) {
@@ -183,13 +198,16 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         R rho, ux, uy, uz;
         const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
         if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
-            collide_srt_k<FORCE>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
+            collide_srt_k<FORCE, scaled ? 10 : 0>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
         else
             collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt,
                                    rho, ux, uy, uz);
         watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
-        for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
+        for (int i = 0; i < 19; i++) {
+            if constexpr (scaled) Store<LBM_F16S>::st_scaled(B + (IX(i) * N + IX(c)), g[i]);
+            else Store<S>::st(B + (IX(i) * N + IX(c)), g[i]);
+        }
     }
 }
 
@@ -237,19 +255,24 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (force)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true>, bx * by, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true, true>, bx * by, 0);
             else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false>, bx * by, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false, true>, bx * by, 0);
             res = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         }
         if (nb > res) nb = res;
     }
     dim3 block(bx, by), grid((unsigned)nb);
     count_launch(c, G_BULK);
-    if (force)
-        stream_collide_bulk<S, SRT, BC, true><<<grid, block, 0, c.stream>>>(a);
+    const bool i32 = LBM_IDX32 && 19 * (unsigned long long)c.N + 64 < (1ULL << 32);
+    if (force && i32)
+        stream_collide_bulk<S, SRT, BC, true, true><<<grid, block, 0, c.stream>>>(a);
+    else if (force)
+        stream_collide_bulk<S, SRT, BC, true, false><<<grid, block, 0, c.stream>>>(a);
+    else if (i32)
+        stream_collide_bulk<S, SRT, BC, false, true><<<grid, block, 0, c.stream>>>(a);
     else
-        stream_collide_bulk<S, SRT, BC, false><<<grid, block, 0, c.stream>>>(a);
+        stream_collide_bulk<S, SRT, BC, false, false><<<grid, block, 0, c.stream>>>(a);
     return cudaGetLastError();
 }
 
