@@ -44,7 +44,8 @@ struct Plan {
     size_t blk_sites, blk_links, counts, status, seg, slink, refill;
     long long max_refill;
     long long max_seg;
-    size_t xy_start, xy_j, xy_w;
+    size_t xy_start, xy_j, xy_w, it_k, it_w;
+    int max_ring;
     long long max_xy;
     size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
     size_t mX, mUnit, mdV, mUd, mFaccR, mFacc, mFr, mB, mE, mpid, mfirst;
@@ -94,6 +95,9 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.xy_start = L.take(4 * ((size_t)g->nx * g->ny + 1));
     P.xy_j = L.take(4 * (size_t)P.max_xy);
     P.xy_w = L.take(8 * (size_t)P.max_xy);
+    P.max_ring = 4 * (g->nx + g->ny);
+    P.it_k = L.take(4 * 16 * (size_t)P.max_ring);
+    P.it_w = L.take(8 * 16 * (size_t)P.max_ring);
     P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32 + 1);
     P.seg = L.take(16 * (size_t)P.max_seg);
     P.slink = L.take(8 * ml);
@@ -325,6 +329,15 @@ void pspan(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b) {
 int marker_count(double RL) { return (int)std::floor(M_PI / 3.0 * (12.0 * RL * RL + 1.0) + 0.5); }
 
 // Peskin (2002) 4-point kernel, host copy for the static pipe weights
+// weight tables are read in the storage's arithmetic type (FP32 unless the
+// populations are FP64): converted once here, not per use on the device
+cudaError_t upload_weights(const Ctx &c, void *dst, const std::vector<double> &w) {
+    if (w.empty()) return cudaSuccess;
+    if (c.storage == LBM_F64) return cudaMemcpy(dst, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice);
+    std::vector<float> f(w.begin(), w.end());
+    return cudaMemcpy(dst, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice);
+}
+
 double peskin_host(double r) {
     const double a = std::fabs(r);
     if (a <= 1.0) return (3.0 - 2.0 * a + std::sqrt(1.0 + 4.0 * a - 4.0 * a * a)) * 0.125;
@@ -384,7 +397,7 @@ lbm_status build_markers(Ctx &c) {
         CK(cudaMemcpy(c.pipe_xy_start, st.data(), sizeof(int) * st.size(), cudaMemcpyHostToDevice));
         if (!jj.empty()) {
             CK(cudaMemcpy(c.pipe_xy_j, jj.data(), sizeof(int) * jj.size(), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(c.pipe_xy_w, ww.data(), sizeof(double) * ww.size(), cudaMemcpyHostToDevice));
+            CK(upload_weights(c, c.pipe_xy_w, ww));
         }
         c.pipe_nc = nc;
         c.pipe_dV = 2.0 * M_PI * RL / nc;
@@ -426,6 +439,45 @@ lbm_status build_markers(Ctx &c) {
     return LBM_OK;
 }
 
+// The pipe's support set is the same in every z plane and the sites are
+// listed in cell order, so site (x, y, z) = z * S_p + k(x, y). For each ring
+// marker, its 4 x 4 column box gives up to 16 (k, x-y weight) entries; the
+// interpolation then needs no per-node lookup. Left unbuilt (pipe_sp = 0)
+// when the site list is not of that form.
+lbm_status build_pipe_interp(Ctx &c) {
+    c.pipe_sp = 0;
+    const long long ns = c.nsites;
+    if (ns <= 0 || ns % c.nz != 0 || c.pipe_nc <= 0 || c.pipe_nc > c.pipe_max_ring || ns > c.max_sites) return LBM_OK;
+    const long long sp = ns / c.nz, nxy = (long long)c.nx * c.ny;
+    std::vector<int> cell((size_t)ns);
+    CK(cudaMemcpy(cell.data(), c.site_cell, sizeof(int) * ns, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < ns; i++)
+        if ((long long)cell[i] - (i / sp) * nxy != (long long)cell[i % sp]) return LBM_OK;  // not plane-invariant
+    std::vector<int> local((size_t)nxy, -1);
+    for (long long k = 0; k < sp; k++) local[cell[k]] = (int)k;
+    const double RL = c.pipe_R + c.rd;
+    const int nc = c.pipe_nc;
+    std::vector<int> tk(16 * (size_t)nc, 0);
+    std::vector<double> tw(16 * (size_t)nc, 0.0);
+    for (int j = 0; j < nc; j++) {
+        const double th = 2.0 * M_PI * j / nc;
+        const double rx = c.pipe_cx + RL * std::cos(th), ry = c.pipe_cy + RL * std::sin(th);
+        const int bx = (int)std::floor(rx) - 1, by = (int)std::floor(ry) - 1;
+        for (int ky = 0; ky < 4; ky++)
+            for (int kx = 0; kx < 4; kx++) {
+                const int xw = ((bx + kx) % c.nx + c.nx) % c.nx, yw = ((by + ky) % c.ny + c.ny) % c.ny;
+                const int k = local[(size_t)xw + (size_t)c.nx * yw];
+                const double w = peskin_host((double)(bx + kx) - rx) * peskin_host((double)(by + ky) - ry);
+                tk[16 * (size_t)j + 4 * ky + kx] = k < 0 ? 0 : k;
+                tw[16 * (size_t)j + 4 * ky + kx] = k < 0 ? 0.0 : w;  // no site: no contribution
+            }
+    }
+    CK(cudaMemcpy(c.pipe_it_k, tk.data(), sizeof(int) * tk.size(), cudaMemcpyHostToDevice));
+    CK(upload_weights(c, c.pipe_it_w, tw));
+    c.pipe_sp = (int)sp;
+    return LBM_OK;
+}
+
 lbm_status arm(Ctx &c, int bc) {
     c.armed_bc = bc;
     if (bc == LBM_BC_IBM_U || bc == LBM_BC_IBM_B) {
@@ -446,6 +498,10 @@ lbm_status arm(Ctx &c, int bc) {
         lbm_status s = sync_all(c);
         if (s != LBM_OK) return s;
         c.nsites_hint = c.nsites;
+        if (c.has_pipe && c.np == 0) {
+            s = build_pipe_interp(c);
+            if (s != LBM_OK) return s;
+        }
     }
     return LBM_OK;
 }
@@ -511,7 +567,11 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.link_dT = b + P.link_dT;
     c.pipe_xy_start = (int *)(b + P.xy_start);
     c.pipe_xy_j = (int *)(b + P.xy_j);
-    c.pipe_xy_w = (double *)(b + P.xy_w);
+    c.pipe_xy_w = b + P.xy_w;
+    c.pipe_it_k = (int *)(b + P.it_k);
+    c.pipe_it_w = b + P.it_w;
+    c.pipe_max_ring = P.max_ring;
+    c.pipe_sp = 0;
     c.pipe_max_xy = P.max_xy;
     c.seg = (uint4 *)(b + P.seg);
     c.slink = (uint2 *)(b + P.slink);

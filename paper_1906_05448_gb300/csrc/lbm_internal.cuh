@@ -78,8 +78,13 @@ struct Ctx {
     int pipe_nc;
     double pipe_dV;
     int *pipe_xy_start, *pipe_xy_j;
-    double *pipe_xy_w;
+    void *pipe_xy_w;  // x-y weights in the storage's arithmetic type
     long long pipe_max_xy;
+    // pipe interpolation: per ring marker, 16 (support site in a plane, x-y
+    // weight) entries; pipe_sp = support sites per z plane (0: not built)
+    int *pipe_it_k;
+    void *pipe_it_w;  // arithmetic type of the storage
+    int pipe_sp, pipe_max_ring;
     // statistics scratch
     double *rho_f, *u_f, *partials;
     unsigned long long *near_key;

@@ -533,6 +533,73 @@ __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
     }
 }
 
+// Pipe ring markers (plane z = l / nc, ring index j), one thread per marker:
+// U*_l = sum over the 16 column entries of j and dz = -1, 0, 1 of
+// w_xy w_z u*(site), with the Peskin z weights 1/4, 1/2, 1/4 of markers on
+// integer planes (the fourth is zero); then the same force as
+// ibm_interp_warp_kernel (U_d = 0 on the fixed wall).
+// (rho, u*) of one support site: one 16-byte load in FP32
+__device__ __forceinline__ void ld_site4(const float *p, float q[4]) {
+    const float4 v = __ldg((const float4 *)p);
+    q[0] = v.x;
+    q[1] = v.y;
+    q[2] = v.z;
+    q[3] = v.w;
+}
+__device__ __forceinline__ void ld_site4(const double *p, double q[4]) {
+    const double2 v0 = __ldg((const double2 *)p), v1 = __ldg((const double2 *)p + 1);
+    q[0] = v0.x;
+    q[1] = v0.y;
+    q[2] = v1.x;
+    q[3] = v1.y;
+}
+
+struct PipeInterpArgs {
+    const int *it_k;
+    const void *it_w;  // R
+    const void *sup_ru;
+    double *mFacc;
+    void *mFaccR, *mFr;
+    long long nm;
+    int nc, nz, sp, pass, last;
+    FastDiv fnc;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) ibm_interp_pipe_kernel(PipeInterpArgs a) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.nm) return;
+    const int z = (int)a.fnc.div((unsigned)l), j = (int)l - z * a.nc;
+    const R *ru = (const R *)a.sup_ru;
+    const long long zm = (long long)(z == 0 ? a.nz - 1 : z - 1) * a.sp, z0 = (long long)z * a.sp,
+                    zp = (long long)(z == a.nz - 1 ? 0 : z + 1) * a.sp;
+    R rl = 0, U0 = 0, U1 = 0, U2 = 0;
+#pragma unroll 4
+    for (int e = 0; e < 16; e++) {
+        const R w = ((const R *)a.it_w)[16 * j + e];
+        if (w == R(0)) continue;
+        const int k = a.it_k[16 * j + e];
+        R qm[4], q0[4], qp[4];
+        ld_site4(ru + 4 * (zm + k), qm);
+        ld_site4(ru + 4 * (z0 + k), q0);
+        ld_site4(ru + 4 * (zp + k), qp);
+        const R wq = R(0.25) * w, wh = R(0.5) * w;
+        rl += wq * qm[0] + wh * q0[0] + wq * qp[0];
+        U0 += wq * qm[1] + wh * q0[1] + wq * qp[1];
+        U1 += wq * qm[2] + wh * q0[2] + wq * qp[2];
+        U2 += wq * qm[3] + wh * q0[3] + wq * qp[3];
+    }
+    const R U[3] = {U0, U1, U2};
+    R *mFr = (R *)a.mFr, *acc = (R *)a.mFaccR;
+    for (int d = 0; d < 3; d++) {
+        const R Fl = R(2) * rl * (R(0) - U[d]);
+        mFr[3 * l + d] = Fl;
+        const R s = a.pass == 0 ? Fl : acc[3 * l + d] + Fl;
+        acc[3 * l + d] = s;
+        if (a.last) a.mFacc[3 * l + d] = double(s);
+    }
+}
+
 // generic spreading with global atomics (large particles only)
 template <typename R>
 __global__ void ibm_spread_kernel(IbmArgs a) {
@@ -579,7 +646,7 @@ __global__ void ibm_update_kernel(IbmArgs a) {
 struct PipeSpreadArgs {
     const int *site_cell;
     const int *xy_start, *xy_j;
-    const double *xy_w;
+    const void *xy_w;  // R
     const void *mFr;
     void *sup_ru, *sup_F;
     const long long *counts;
@@ -606,7 +673,7 @@ __global__ void __launch_bounds__(256) ibm_spread_pipe_kernel(PipeSpreadArgs a) 
             const R wz = R(dz == 0 ? 0.5 : 0.25) * R(a.dV);
             const R *Fp = mFr + 3 * (long long)zm * a.nc;
             for (int k = j0; k < j1; k++) {
-                const R w = R(a.xy_w[k]) * wz;
+                const R w = ((const R *)a.xy_w)[k] * wz;
                 const int j = a.xy_j[k];
                 F0 += Fp[3 * j] * w;
                 F1 += Fp[3 * j + 1] * w;
@@ -713,7 +780,12 @@ static cudaError_t ibm_passes_t(Ctx &c) {
     for (int pass = 0; pass < 3; pass++) {
         a.pass = pass;
         a.last = pass == 2;
-        if (c.nm > 0) {
+        if (c.nm > 0 && pipe_gather && c.pipe_sp > 0 && c.nm == (long long)c.nz * c.pipe_nc) {
+            PipeInterpArgs pi{c.pipe_it_k, c.pipe_it_w, c.sup_ru, c.mFacc, c.mFaccR, c.mFr, c.nm,
+                              c.pipe_nc, c.nz, c.pipe_sp, pass, pass == 2, FastDiv((unsigned)c.pipe_nc)};
+            count_launch(c, G_IBM);
+            ibm_interp_pipe_kernel<R><<<(unsigned)((c.nm + 255) / 256), 256, 0, c.stream>>>(pi);
+        } else if (c.nm > 0) {
             count_launch(c, G_IBM);
             ibm_interp_warp_kernel<R><<<(unsigned)((c.nm * 32 + 255) / 256), 256, 0, c.stream>>>(a);
         }
