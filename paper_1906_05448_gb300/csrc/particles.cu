@@ -470,7 +470,7 @@ struct IbmArgs {
     const int *mpid;
     double *mFacc;        // per-step marker force (sum of the passes), FP64
     const void *mUd;      // desired velocity U_d at the marker (R)
-    void *mFaccR, *mFr;   // running sum of the passes' forces, force of this pass (R)
+    void *mFaccR, *mFr;   // running sum of the passes' forces; F_l dV_l of this pass for the spreading (R)
     const int *mB;
     const void *mE;
     const int *aux;
@@ -524,9 +524,10 @@ __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
     const R *Ud = (const R *)a.mUd + 3 * l;
     const R U[3] = {U0, U1, U2};
     R *mFr = (R *)a.mFr, *acc = (R *)a.mFaccR;
+    const R dVl = R(a.mdV[l]);
     for (int d = 0; d < 3; d++) {
         const R Fl = R(2) * rl * (Ud[d] - U[d]);
-        mFr[3 * l + d] = Fl;
+        mFr[3 * l + d] = Fl * dVl;  // spread weight F_l dV_l
         const R s = a.pass == 0 ? Fl : acc[3 * l + d] + Fl;
         acc[3 * l + d] = s;
         if (a.last) a.mFacc[3 * l + d] = double(s);
@@ -563,6 +564,7 @@ struct PipeInterpArgs {
     long long nm;
     int nc, nz, sp, pass, last;
     FastDiv fnc;
+    double dV;  // ring marker volume
 };
 
 template <typename R>
@@ -591,9 +593,10 @@ __global__ void __launch_bounds__(256) ibm_interp_pipe_kernel(PipeInterpArgs a) 
     }
     const R U[3] = {U0, U1, U2};
     R *mFr = (R *)a.mFr, *acc = (R *)a.mFaccR;
+    const R dVl = R(a.dV);
     for (int d = 0; d < 3; d++) {
         const R Fl = R(2) * rl * (R(0) - U[d]);
-        mFr[3 * l + d] = Fl;
+        mFr[3 * l + d] = Fl * dVl;  // spread weight F_l dV_l
         const R s = a.pass == 0 ? Fl : acc[3 * l + d] + Fl;
         acc[3 * l + d] = s;
         if (a.last) a.mFacc[3 * l + d] = double(s);
@@ -609,8 +612,7 @@ __global__ void ibm_spread_kernel(IbmArgs a) {
     const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
     const R *E = (const R *)a.mE + 3 * l;
     const int b0 = a.mB[3 * l], b1 = a.mB[3 * l + 1], b2 = a.mB[3 * l + 2];
-    const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) * peskin_r<R>(R(kz - 1) - E[2]) *
-                R(a.mdV[l]);
+    const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) * peskin_r<R>(R(kz - 1) - E[2]);
     const long long c = (long long)pwrap(b0 + kx, a.nx) +
                         (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
     const int s = a.aux[c];
@@ -652,7 +654,6 @@ struct PipeSpreadArgs {
     const long long *counts;
     long long max_sites;
     int nx, ny, nz, nc;
-    double dV;
     int pass;
 };
 
@@ -670,7 +671,7 @@ __global__ void __launch_bounds__(256) ibm_spread_pipe_kernel(PipeSpreadArgs a) 
         for (int dz = -1; dz <= 1; dz++) {
             int zm = z - dz;
             zm = zm < 0 ? zm + a.nz : (zm >= a.nz ? zm - a.nz : zm);
-            const R wz = R(dz == 0 ? 0.5 : 0.25) * R(a.dV);
+            const R wz = R(dz == 0 ? 0.5 : 0.25);
             const R *Fp = mFr + 3 * (long long)zm * a.nc;
             for (int k = j0; k < j1; k++) {
                 const R w = ((const R *)a.xy_w)[k] * wz;
@@ -725,8 +726,7 @@ __global__ void __launch_bounds__(256) ibm_spread_particle_kernel(ParticleSpread
         const int l = l0 + (int)(t >> 6), k = (int)(t & 63);
         const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
         const R *E = (const R *)a.mE + 3 * l;
-        const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) *
-                    peskin_r<R>(R(kz - 1) - E[2]) * R(a.mdV[l]);
+        const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) * peskin_r<R>(R(kz - 1) - E[2]);
         // box-local node index; the marker base is wrapped, so unwrap the difference
         int i0 = a.mB[3 * l] + kx - o0, i1 = a.mB[3 * l + 1] + ky - o1, i2 = a.mB[3 * l + 2] + kz - o2;
         i0 = i0 < -a.nx / 2 ? i0 + a.nx : (i0 >= a.nx / 2 ? i0 - a.nx : i0);
@@ -782,7 +782,7 @@ static cudaError_t ibm_passes_t(Ctx &c) {
         a.last = pass == 2;
         if (c.nm > 0 && pipe_gather && c.pipe_sp > 0 && c.nm == (long long)c.nz * c.pipe_nc) {
             PipeInterpArgs pi{c.pipe_it_k, c.pipe_it_w, c.sup_ru, c.mFacc, c.mFaccR, c.mFr, c.nm,
-                              c.pipe_nc, c.nz, c.pipe_sp, pass, pass == 2, FastDiv((unsigned)c.pipe_nc)};
+                              c.pipe_nc, c.nz, c.pipe_sp, pass, pass == 2, FastDiv((unsigned)c.pipe_nc), c.pipe_dV};
             count_launch(c, G_IBM);
             ibm_interp_pipe_kernel<R><<<(unsigned)((c.nm + 255) / 256), 256, 0, c.stream>>>(pi);
         } else if (c.nm > 0) {
@@ -791,7 +791,7 @@ static cudaError_t ibm_passes_t(Ctx &c) {
         }
         if (pipe_gather) {
             PipeSpreadArgs ps{c.site_cell, c.pipe_xy_start, c.pipe_xy_j, c.pipe_xy_w, c.mFr, c.sup_ru,
-                              c.sup_F, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, c.pipe_nc, c.pipe_dV, pass};
+                              c.sup_F, c.d_counts, c.max_sites, c.nx, c.ny, c.nz, c.pipe_nc, pass};
             count_launch(c, G_IBM);
             ibm_spread_pipe_kernel<R><<<(unsigned)ub, 256, 0, c.stream>>>(ps);
             continue;
