@@ -111,6 +111,7 @@ def lib():
                 "orc_get_markers": (None, [_P, _D, _D, _D, _I]),
                 "orc_get_ibm_force": (None, [_P, _D]),
                 "orc_stats": (None, [_P, ctypes.c_int, ctypes.POINTER(Stats)]),
+                "orc_masked_velocity": (None, [_P, ctypes.c_int, _D]),
                 "orc_marker_residual": (ctypes.c_double, [_P, ctypes.c_int]),
                 "orc_particles_advance": (None, [_P, ctypes.c_int]),
             }
@@ -301,6 +302,12 @@ class Sim:
 
     def marker_residual(self, p: int) -> float:
         return self.L.orc_marker_residual(self.h, int(p))
+
+    def masked_velocity(self, flags=0):
+        """Velocity field of the statistics, shape (3, N)."""
+        u = np.zeros((3, self.N))
+        self.L.orc_masked_velocity(self.h, int(flags), _dp(u))
+        return u
 
     def stats(self, flags=0) -> dict:
         s = Stats()

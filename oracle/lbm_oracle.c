@@ -1178,13 +1178,16 @@ double orc_marker_residual(const orc_sim *S, int pass) { return (pass >= 0 && pa
  * the zero-mean assumption of Sec. 3.2. Radial bins: fluid cells binned by
  * r / r_p of the nearest particle surface, r/r_p in [1, 3) by 0.05, each bin
  * mean normalised by the mean over all fluid cells. */
-void orc_stats(const orc_sim *S, int flags, orc_stats_t *o)
+/* Velocity field of the statistics (Sec. 3.2): u of the post-collision
+   state, with solid cells replaced by the rigid-body velocity of their
+   particle (zero outside the pipe) unless IBM statistics are asked for
+   unmasked. u: 3 N values, component-major. */
+void orc_masked_velocity(const orc_sim *S, int flags, double *u)
 {
     long long N = S->N;
-    memset(o, 0, sizeof(*o));
     double *rho = (double *)malloc(sizeof(double) * (size_t)N);
-    double *u = (double *)malloc(sizeof(double) * (size_t)(3 * N));
     orc_macro(S, rho, u);
+    free(rho);
     int ibm = (S->armed_bc == ORC_BC_IBM_U || S->armed_bc == ORC_BC_IBM_B);
     int mask = !(ibm && (flags & ORC_STATS_UNMASK));
     for (long long c = 0; c < N; c++) {
@@ -1195,6 +1198,16 @@ void orc_stats(const orc_sim *S, int flags, orc_stats_t *o)
         wall_velocity(S, S->owner[c], xr, uw);
         for (int d = 0; d < 3; d++) u[d * N + c] = uw[d];
     }
+}
+
+void orc_stats(const orc_sim *S, int flags, orc_stats_t *o)
+{
+    long long N = S->N;
+    memset(o, 0, sizeof(*o));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)N);
+    double *u = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    orc_macro(S, rho, u);
+    orc_masked_velocity(S, flags, u);
     double nu = (S->tau - 0.5) / 3.0;
     double ke = 0.0, eps = 0.0, kef = 0.0, epsf = 0.0, ub = 0.0;
     long long nf = 0, nin = 0;

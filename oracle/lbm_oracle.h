@@ -75,6 +75,7 @@ long long orc_num_markers(const orc_sim *S);
 void  orc_get_markers(const orc_sim *S, double *X, double *F, double *dV, int *pid);
 void  orc_get_ibm_force(const orc_sim *S, double *F);
 void  orc_stats(const orc_sim *S, int flags, orc_stats_t *out);
+void  orc_masked_velocity(const orc_sim *S, int flags, double *u);
 double orc_marker_residual(const orc_sim *S, int pass);
 void  orc_particles_advance(orc_sim *S, int nsteps);
 
