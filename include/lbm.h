@@ -143,6 +143,25 @@ typedef struct {
  * differences, dissipation 2 nu s_ij s_ij; Sec. 2.2 bulk velocity). Syncs. */
 lbm_status lbm_stats(lbm_ctx *ctx, int flags, lbm_stats_t *out);
 
+/* Three-dimensional spectra of kinetic energy and dissipation of the
+ * current state (Sec. 3.2), on a periodic cube of side n = nx = ny = nz, n a
+ * power of two in [8, 1024]:
+ *   u_hat(k) = (1/N) sum_x u(x) exp(-2 pi i k.x / n), N = n^3, with the
+ *   velocity of lbm_stats (solid cells masked with the rigid-body velocity
+ *   unless IBM statistics are asked for with LBM_STATS_UNMASK in flags);
+ *   E[K] = sum over wave vectors with round(|k|) = K of (1/2)|u_hat(k)|^2,
+ *   summed over the three components (sum of E = mean kinetic energy);
+ *   D[K] = the same sum of 2 nu (2 pi |k| / n)^2 (1/2)|u_hat(k)|^2, nu =
+ *   (tau - 1/2)/3 (sum of D = spectral dissipation).
+ * E and D: host arrays of nbins doubles (1 <= nbins <= LBM_SPECTRUM_MAX_BINS);
+ * shells K >= nbins are left out. The transform runs in FP32 on the device
+ * and the shell sums in FP64. Scratch: the population buffer that the next
+ * step overwrites, so the call allocates nothing and must not overlap a
+ * step on another stream. Syncs. Errors: LBM_EINVAL (arguments),
+ * LBM_EUNSUPPORTED (not such a cube), LBM_ENOMEM (scratch too small). */
+#define LBM_SPECTRUM_MAX_BINS 2048
+lbm_status lbm_spectrum(lbm_ctx *ctx, int flags, int nbins, double *E, double *D);
+
 #define LBM_FIELD_RHO 0      /* N doubles */
 #define LBM_FIELD_U 1        /* 3N doubles */
 #define LBM_FIELD_POPS 2     /* 19N doubles, unshifted f_i (post-collision state) */

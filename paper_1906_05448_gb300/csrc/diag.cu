@@ -379,6 +379,13 @@ cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scal
     return cudaGetLastError();
 }
 
+cudaError_t launch_mask(Ctx &c) {
+    count_launch(c, G_STATS);
+    mask_kernel<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx,
+                                                                     c.ny, c.nz, c.N);
+    return cudaGetLastError();
+}
+
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     cudaError_t e;
     memset(o, 0, sizeof(*o));

@@ -874,6 +874,21 @@ lbm_status lbm_stats(lbm_ctx *h, int flags, lbm_stats_t *out) {
     return s;
 }
 
+lbm_status lbm_spectrum(lbm_ctx *h, int flags, int nbins, double *E, double *D) {
+    CTX_CHECK(h);
+    if (!E || !D || nbins < 1 || nbins > LBM_SPECTRUM_MAX_BINS) return fail(c, LBM_EINVAL, "bad spectrum arguments");
+    const int n = c.nx;
+    if (c.ny != n || c.nz != n || n < 8 || n > 1024 || (n & (n - 1)) != 0)
+        return fail(c, LBM_EUNSUPPORTED, "spectra need a cube of side 2^k, 8 <= side <= 1024 (grid %dx%dx%d)", c.nx,
+                    c.ny, c.nz);
+    if (spectrum_scratch_bytes(c.N, nbins) > 19 * (size_t)c.N * storage_bytes(c.storage))
+        return fail(c, LBM_ENOMEM, "spectrum scratch does not fit the idle population buffer");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    CK(run_spectrum(c, flags, nbins, E, D));
+    return s;
+}
+
 lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
     CTX_CHECK(h);
     if (!dst) return fail(c, LBM_EINVAL, "null destination");

@@ -152,6 +152,9 @@ cudaError_t launch_ibm_passes(Ctx &c);
 cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only);
 cudaError_t launch_ibm_rigid_overwrite(Ctx &c);
 cudaError_t launch_macro(Ctx &c, int mask_mode);
+cudaError_t launch_mask(Ctx &c);  // statistics velocity: solid cells take the rigid-body velocity
+cudaError_t run_spectrum(Ctx &c, int flags, int nbins, double *E, double *D);
+size_t spectrum_scratch_bytes(long long N, int nbins);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);
 cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out);
 cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scale, float *T);
