@@ -223,6 +223,25 @@ def precision_report(lbm, torch, n=64, n_particles=31, steps=200):
     return res
 
 
+def spectrum_report(lbm, torch, n=256, nbins=222, reps=3):
+    """Time of the 3D energy and dissipation spectra (masked statistics
+    velocity, three FP32 FFTs of 256^3 and shell sums) on the HIT field."""
+    u = workloads.hit_velocity(n, seed=0, k_peak=8.0, u_rms=0.03, dtype=np.float64)
+    L = lbm.Lattice(n, n, n, 0.51, storage=lbm.F32, rates=lbm.RATES_DHUMIERES)
+    L.init_velocity(u)
+    L.step(5)
+    L.spectrum(nbins)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        E, D = L.spectrum(nbins)
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    L.close()
+    k_peak = int(np.argmax(E[1:]) + 1)
+    return {"grid": f"{n}^3", "ms_per_spectrum": round(ms, 3), "nbins": nbins, "energy_peak_shell": k_peak,
+            "kinetic_energy": float(E.sum()), "spectral_dissipation": float(D.sum())}
+
+
 def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
     """Learned closure on the particle-laden 256^3 box (IBM-B): paired
     IBB/IBM-B runs of seeds 0-7 give up to 1e6 training samples, seeds 8-9
@@ -445,9 +464,11 @@ def main():
 
     precision = None
     closure_res = None
+    spectrum_res = None
     if not args.no_variants and rank == 0:
         precision = precision_report(lbm, torch)
         closure_res = closure_report(lbm, torch)
+        spectrum_res = spectrum_report(lbm, torch)
 
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -491,6 +512,7 @@ def main():
             "variants": variants,
             "precision_vs_f64": precision,
             "closure": closure_res,
+            "spectrum": spectrum_res,
         }
         print(json.dumps(line))
     if dist:
