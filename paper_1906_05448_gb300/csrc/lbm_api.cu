@@ -12,6 +12,9 @@
 #include <utility>
 #include <vector>
 
+#ifndef LBM_WALL_VALUES
+#define LBM_WALL_VALUES 1  // the sweep keeps the wall cells' values for the next ghost pass
+#endif
 #ifndef LBM_STATIC_LINKS
 #define LBM_STATIC_LINKS 1  // 1: static-wall links regrouped by direction for the ghost pass
 #endif
@@ -41,7 +44,7 @@ struct Plan {
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status, seg, slink, refill;
+    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, seg_bnd, bvals, wrec, gidx, gvals, refill;
     long long max_refill;
     long long max_seg;
     size_t xy_start, xy_j, xy_w, it_k, it_w;
@@ -101,6 +104,12 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.max_seg = (long long)g->ny * g->nz * ((g->nx + 31) / 32 + 1);
     P.seg = L.take(16 * (size_t)P.max_seg);
     P.slink = L.take(8 * ml);
+    P.slink_rank = L.take(4 * ml);
+    P.seg_bnd = L.take(8 * (size_t)P.max_seg);
+    P.bvals = L.take(19 * sb * ms);
+    P.wrec = L.take(8 * ms);
+    P.gidx = L.take(4 * ml);
+    P.gvals = L.take(sb * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
     P.counts = L.take(32);
@@ -576,6 +585,15 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.seg = (uint4 *)(b + P.seg);
     c.slink = (uint2 *)(b + P.slink);
     c.static_links = 0;
+    c.slink_rank = (int *)(b + P.slink_rank);
+    c.seg_bnd = (uint2 *)(b + P.seg_bnd);
+    c.bvals = b + P.bvals;
+    c.wrec = (uint2 *)(b + P.wrec);
+    c.gidx = (int *)(b + P.gidx);
+    c.gvals = b + P.gvals;
+    c.max_bvals = P.max_sites;
+    c.bvals_ready = 0;
+    c.bvals_valid = 0;
     c.max_seg = P.max_seg;
     c.nseg = 0;
     c.nblk = P.nblk;
@@ -665,6 +683,7 @@ lbm_status lbm_init_velocity(lbm_ctx *h, const double *u_host, double rho0) {
     CTX_CHECK(h);
     if (!u_host || !(rho0 > 0)) return fail(c, LBM_EINVAL, "bad velocity field or rho0");
     if (c.broken || c.armed_bc >= 0) return fail(c, LBM_ESTATE, "init_velocity only before the first step");
+    c.bvals_valid = 0;
     CK(cudaMemcpyAsync(c.u_f, u_host, sizeof(double) * 3 * c.N, cudaMemcpyHostToDevice, c.stream));
     CK(launch_init_equilibrium(c, c.u_f, rho0));
     CK(cudaStreamSynchronize(c.stream));
@@ -675,6 +694,7 @@ lbm_status lbm_set_populations(lbm_ctx *h, const double *f_host) {
     CTX_CHECK(h);
     if (!f_host) return fail(c, LBM_EINVAL, "null populations");
     if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
+    c.bvals_valid = 0;
     for (int i = 0; i < 19; i++) {
         CK(cudaMemcpyAsync(c.rho_f, f_host + (size_t)i * c.N, sizeof(double) * c.N, cudaMemcpyHostToDevice, c.stream));
         CK(plane_copy(c, i, false));
@@ -733,15 +753,81 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
             for (int l = 0; l < 19; l++) c.slink_off[l + 1] = c.slink_off[l] + cnt[l];
             int pos[19];
             for (int l = 0; l < 19; l++) pos[l] = c.slink_off[l];
+            // wall cells (cells with links; the list is in cell order) and their ranks
+            std::vector<int> bcells;
+            bool sorted = true;
+            for (size_t k = 0; k < nl; k++) {
+                if (k > 0 && lcell[k] < lcell[k - 1]) sorted = false;
+                if (k == 0 || lcell[k] != lcell[k - 1]) bcells.push_back(lcell[k]);
+            }
+            auto rank_of = [&](long long cell) -> long long {
+                auto it = std::lower_bound(bcells.begin(), bcells.end(), (int)cell);
+                return (it != bcells.end() && *it == (int)cell) ? (long long)(it - bcells.begin()) : -1;
+            };
             std::vector<uint2> pk(nl);
+            std::vector<int> rk(nl);
             for (size_t k = 0; k < nl; k++) {
                 const float qf = (float)lq[k];
                 unsigned qb;
                 std::memcpy(&qb, &qf, 4);
-                pk[pos[ldir[k]]++] = make_uint2((unsigned)lcell[k] | ((unsigned)lsch[k] << 30), qb);
+                const int at = pos[ldir[k]]++;
+                pk[at] = make_uint2((unsigned)lcell[k] | ((unsigned)lsch[k] << 30), qb);
+                rk[at] = (int)rank_of(lcell[k]);
             }
             CK(cudaMemcpy(c.slink, pk.data(), 8 * nl, cudaMemcpyHostToDevice));
             c.static_links = 1;
+            // per sweep item: rank of its first wall cell and the lanes that hold wall cells
+            bool bok = LBM_WALL_VALUES && sorted && c.nseg > 0 && (long long)bcells.size() <= c.max_bvals;
+            std::vector<uint2> sb(bok ? items.size() : 0);
+            for (size_t it = 0; bok && it < items.size(); it++) {
+                const SweepItem &w = items[it];
+                const unsigned la = (w.word_a >> 16) & 0xff;
+                long long base = -1;
+                unsigned mask = 0;
+                for (unsigned lane = 0; lane < 32 && bok; lane++) {
+                    const bool pa = lane < la;
+                    const unsigned wd = pa ? w.word_a : w.word_b, row = pa ? w.row_a : w.row_b;
+                    const int lp = pa ? (int)lane : (int)(lane - la);
+                    const int len = (int)((wd >> 16) & 0xff), lead = (int)((wd >> 24) & 15), trail = (int)(wd >> 28);
+                    if (lp >= len || lp < lead || lp >= len - trail) continue;  // idle or zero lane
+                    const long long cell = (long long)row * c.nx + (long long)(wd & 0xffff) - lead + lp;
+                    const long long r = rank_of(cell);
+                    if (r < 0) continue;
+                    if (base < 0) base = r;
+                    if (r != base + __builtin_popcount(mask)) bok = false;  // ranks must follow the lanes
+                    mask |= 1u << lane;
+                }
+                sb[it] = make_uint2((unsigned)(base < 0 ? 0 : base), mask);
+            }
+            // compact ghosts: per wall cell the directions ibar = opp(l) of its
+            // links and the first of its values; per link the index of its value
+            std::vector<uint2> wr(bok ? bcells.size() : 0);
+            std::vector<int> gx(bok ? nl : 0);
+            if (bok) {
+                std::vector<unsigned> dm(bcells.size(), 0u);
+                for (size_t k = 0; k < nl; k++) dm[(size_t)rank_of(lcell[k])] |= 1u << (ldir[k] == 0 ? 0 : ((ldir[k] & 1) ? ldir[k] + 1 : ldir[k] - 1));
+                unsigned acc = 0;
+                for (size_t r = 0; r < bcells.size(); r++) {
+                    wr[r] = make_uint2(acc, dm[r]);
+                    acc += (unsigned)__builtin_popcount(dm[r]);
+                }
+                int pos2[19];
+                for (int l = 0; l < 19; l++) pos2[l] = c.slink_off[l];
+                for (size_t k = 0; k < nl; k++) {
+                    const int l = ldir[k], i = l == 0 ? 0 : ((l & 1) ? l + 1 : l - 1);
+                    const size_t r = (size_t)rank_of(lcell[k]);
+                    gx[pos2[l]++] = (int)(wr[r].x + (unsigned)__builtin_popcount(dm[r] & ((1u << i) - 1u)));
+                }
+                if (acc != (unsigned)nl) bok = false;  // one value per link
+            }
+            if (bok) {
+                CK(cudaMemcpy(c.wrec, wr.data(), 8 * wr.size(), cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(c.gidx, gx.data(), 4 * nl, cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(c.slink_rank, rk.data(), 4 * nl, cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(c.seg_bnd, sb.data(), 8 * sb.size(), cudaMemcpyHostToDevice));
+                c.bvals_ready = 1;
+                c.bvals_valid = 0;
+            }
         }
     }
     return LBM_OK;
@@ -817,6 +903,7 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
             t1 = pmark(c);
             pspan(c, G_BND, t0, t1);
             CK(launch_stream_collide(c, bc));
+            c.bvals_valid = c.bvals_ready;  // the sweep wrote the wall cells' values
             t0 = pmark(c);
             pspan(c, G_BULK, t1, t0);
             if (c.np > 0) CK(launch_gimem(c));

@@ -49,6 +49,20 @@ struct Ctx {
     uint2 *slink;
     int slink_off[20];  // first link of each direction, and the total
     int static_links;   // 1: the ghost pass uses slink (FP32-arithmetic storages)
+    // wall cells' post-collision populations, written by the sweep for the
+    // next ghost pass: 19 values (storage type) per wall cell in cell order
+    int *slink_rank;    // per static link: rank of its wall cell
+    uint2 *seg_bnd;     // per sweep item: rank of its first wall cell, lane mask of wall cells
+    void *bvals;
+    long long max_bvals;
+    // compact ghosts: the ghost pass stores the bounced values here (one per
+    // link, storage type) instead of in the solid nodes' slots; per wall
+    // cell (rank) a record {first value, mask of the directions it replaces}
+    uint2 *wrec;
+    int *gidx;          // per static link: index of its value
+    void *gvals;
+    int bvals_ready;    // the tables above are built
+    int bvals_valid;    // bvals holds the values of the current state
     // compaction scratch
     int nblk;
     long long *blk_sites, *blk_links;

@@ -248,6 +248,10 @@ static unsigned site_grid(const Ctx &c, int tb) {
 struct StaticLinkArgs {
     void *A;
     const uint2 *slink;  // x = cell | scheme << 30, y = FP32 bits of q
+    const int *rank;     // wall-cell rank of each link
+    const void *bvals;   // wall cells' values (19 per cell), or null: read A
+    const int *gidx;     // compact ghost value of each link
+    void *gvals;         // compact ghost values (null: store in the solid nodes' slots)
     int off[20];
     int nx, ny, nz;
     long long N;
@@ -275,9 +279,20 @@ __global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
         const int x1 = wrap(x - lx, nx), y1 = wrap(y - ly, ny), z1 = wrap(z - lz, nz);
         const int c1 = x1 + nx * (y1 + ny * z1);
         const int c2 = wrap(x1 - lx, nx) + nx * (wrap(y1 - ly, ny) + ny * wrap(z1 - lz, nz));
-        const R fl0 = Store<S>::ld(A + (size_t)l * N + c), fi0 = Store<S>::ld(A + (size_t)i * N + c);
+        R fl0, fi0;
+        if (a.bvals) {  // the same values, kept contiguous by the last sweep
+            const T *wv = (const T *)a.bvals + (size_t)19 * __ldg(a.rank + k);
+            fl0 = Store<S>::ld(wv + l);
+            fi0 = Store<S>::ld(wv + i);
+        } else {
+            fl0 = Store<S>::ld(A + (size_t)l * N + c);
+            fi0 = Store<S>::ld(A + (size_t)i * N + c);
+        }
         const R v = ibb_value<S>(A, N, l, i, sch, qq, c1, c2, R(0), fl0, fi0);
-        Store<S>::st(A + (size_t)i * N + cb, v);
+        if (a.gvals)
+            Store<S>::st((T *)a.gvals + __ldg(a.gidx + k), v);  // read by the sweep in place of the pull
+        else
+            Store<S>::st(A + (size_t)i * N + cb, v);
     }
 }
 
@@ -288,6 +303,10 @@ static cudaError_t launch_links_s(Ctx &c) {
         StaticLinkArgs a;
         a.A = c.fA;
         a.slink = c.slink;
+        a.rank = c.slink_rank;
+        a.bvals = c.bvals_valid ? c.bvals : nullptr;
+        a.gidx = c.gidx;
+        a.gvals = c.bvals_ready ? c.gvals : nullptr;
         for (int l = 0; l < 20; l++) a.off[l] = c.slink_off[l];
         a.nx = c.nx;
         a.ny = c.ny;

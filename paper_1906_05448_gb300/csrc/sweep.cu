@@ -29,18 +29,22 @@ struct SweepArgs {
     float Fs[3];  // F in single precision (a double-to-single conversion per cell is costly on GB300)
     Rates rt;
     SrtK sk;  // folded BGK factors (FP32 arithmetic, uniform force)
+    const uint2 *seg_bnd;  // per item: rank of its first wall cell, wall-cell lanes
+    void *bvals;           // wall cells' populations for the next ghost pass (storage type), or null
+    const uint2 *wrec;     // per wall cell: first compact ghost value, replaced directions
+    const void *gvals;     // compact ghost values of this step (storage type)
 };
 
 // BC: 0 periodic, 1 IBB, 2 IBM
 // Resident blocks of 256 threads per SM the register allocation aims at
-// (measured per variant: the BGK box and the 16-bit pipe sweep fit 5 blocks
-// without spilling; the FP32 pipe sweep and MRT are fastest at 4).
+// (measured per variant: the BGK box fits 5 blocks without spilling; the
+// pipe sweeps, which also handle the wall cells, and MRT are fastest at 4).
 #ifndef LBM_BULK_MINB
 #define LBM_BULK_MINB 0  // 0: per variant below
 #endif
 constexpr int bulk_min_blocks(int S, bool SRT, int BC) {
     return LBM_BULK_MINB > 0 ? LBM_BULK_MINB
-                             : (!SRT || BC == 2 || S == LBM_F64) ? 4 : (BC == 0 ? 5 : (S == LBM_F32 ? 4 : 5));
+                             : (!SRT || BC == 2 || S == LBM_F64) ? 4 : (BC == 0 ? 5 : 4);
 }
 #ifndef LBM_BULK_PERSIST
 #define LBM_BULK_PERSIST 2  // persistent grid: 0 never, 1 always, 2 for segment sweeps
@@ -89,7 +93,19 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
     // warp item: up to two pieces of fluid runs (row, word), see segments.h;
     // the next item is loaded one iteration ahead
     uint4 sg_next = make_uint4(0u, 0u, 0u, 0u);
+    uint2 bd_next = make_uint2(0u, 0u), wr_next = make_uint2(0u, 0u);
+    const bool keep_walls = BC == 1 && segs && a.bvals != nullptr;
+    // the wall record of this lane's cell in the next item (its compact
+    // ghost values replace the pulls from the solid nodes)
+    auto wall_record = [&](uint2 bdv) -> uint2 {
+        if (!((bdv.y >> lane) & 1u)) return make_uint2(0u, 0u);
+        return __ldg(a.wrec + bdv.x + __popc(bdv.y & ((1u << lane) - 1u)));
+    };
     if (segs && w < items) sg_next = __ldg(a.seg + w);
+    if (keep_walls && w < items) {
+        bd_next = __ldg(a.seg_bnd + w);
+        wr_next = wall_record(bd_next);
+    }
     auto cell_of = [&](long long item, int &x, int &row) {  // without a segment list
         row = (int)(item / ipr);
         x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
@@ -105,9 +121,16 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
     for (; w < items; w += stride) {
         int x, row;
         bool zero = false;
+        uint2 bd = make_uint2(0u, 0u), wr = make_uint2(0u, 0u);
         if (segs) {
             const uint4 sg = sg_next;
+            bd = bd_next;
+            wr = wr_next;
             if (w + stride < items) sg_next = __ldg(a.seg + w + stride);
+            if (keep_walls && w + stride < items) {
+                bd_next = __ldg(a.seg_bnd + w + stride);
+                wr_next = wall_record(bd_next);
+            }
             const int la = (int)((sg.y >> 16) & 0xff);
             const bool pa = lane < la;
             const unsigned wd = pa ? sg.y : sg.w;
@@ -149,26 +172,36 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         const int c = r00 + x;
         const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
         R g[19];
-        // pull: f_i(x) = f*_i(x - c_i)
+        // pull: f_i(x) = f*_i(x - c_i); at a wall cell of the pipe, the
+        // populations bounced at the wall are taken from the compact ghost
+        // values of this step instead (one load either way)
+        const T *gv = keep_walls ? (const T *)a.gvals + wr.x : A;
+        auto pick = [&](int i, const T *pull) -> const T * {
+            if constexpr (BC == 1)
+                return ((wr.y >> i) & 1u) ? gv + __popc(wr.y & ((1u << i) - 1u)) : pull;
+            else
+                return pull;
+        };
         g[0] = ld(A + IX(c));
-        g[1] = ld(A + (IX(1) * N + IX(r00 + xm)));
-        g[2] = ld(A + (IX(2) * N + IX(r00 + xp)));
-        g[3] = ld(A + (IX(3) * N + IX(rM0 + x)));
-        g[4] = ld(A + (IX(4) * N + IX(rP0 + x)));
-        g[5] = ld(A + (IX(5) * N + IX(r0M + x)));
-        g[6] = ld(A + (IX(6) * N + IX(r0P + x)));
-        g[7] = ld(A + (IX(7) * N + IX(rM0 + xm)));
-        g[8] = ld(A + (IX(8) * N + IX(rP0 + xp)));
-        g[9] = ld(A + (IX(9) * N + IX(rP0 + xm)));
-        g[10] = ld(A + (IX(10) * N + IX(rM0 + xp)));
-        g[11] = ld(A + (IX(11) * N + IX(r0M + xm)));
-        g[12] = ld(A + (IX(12) * N + IX(r0P + xp)));
-        g[13] = ld(A + (IX(13) * N + IX(r0P + xm)));
-        g[14] = ld(A + (IX(14) * N + IX(r0M + xp)));
-        g[15] = ld(A + (IX(15) * N + IX(rMM + x)));
-        g[16] = ld(A + (IX(16) * N + IX(rPP + x)));
-        g[17] = ld(A + (IX(17) * N + IX(rMP + x)));
-        g[18] = ld(A + (IX(18) * N + IX(rPM + x)));
+        g[1] = ld(pick(1, A + (IX(1) * N + IX(r00 + xm))));
+        g[2] = ld(pick(2, A + (IX(2) * N + IX(r00 + xp))));
+        g[3] = ld(pick(3, A + (IX(3) * N + IX(rM0 + x))));
+        g[4] = ld(pick(4, A + (IX(4) * N + IX(rP0 + x))));
+        g[5] = ld(pick(5, A + (IX(5) * N + IX(r0M + x))));
+        g[6] = ld(pick(6, A + (IX(6) * N + IX(r0P + x))));
+        g[7] = ld(pick(7, A + (IX(7) * N + IX(rM0 + xm))));
+        g[8] = ld(pick(8, A + (IX(8) * N + IX(rP0 + xp))));
+        g[9] = ld(pick(9, A + (IX(9) * N + IX(rP0 + xm))));
+        g[10] = ld(pick(10, A + (IX(10) * N + IX(rM0 + xp))));
+        g[11] = ld(pick(11, A + (IX(11) * N + IX(r0M + xm))));
+        g[12] = ld(pick(12, A + (IX(12) * N + IX(r0P + xp))));
+        g[13] = ld(pick(13, A + (IX(13) * N + IX(r0P + xm))));
+        g[14] = ld(pick(14, A + (IX(14) * N + IX(r0M + xp))));
+        g[15] = ld(pick(15, A + (IX(15) * N + IX(rMM + x))));
+        g[16] = ld(pick(16, A + (IX(16) * N + IX(rPP + x))));
+        g[17] = ld(pick(17, A + (IX(17) * N + IX(rMP + x))));
+        g[18] = ld(pick(18, A + (IX(18) * N + IX(rPM + x))));
+
         if (LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
         const bool fluid = !(fl & FL_SOLID);
         if (BC == 2 && (fl & FL_SUP)) {
@@ -208,6 +241,15 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
             if constexpr (scaled) Store<LBM_F16S>::st_scaled(B + (IX(i) * N + IX(c)), g[i]);
             else Store<S>::st(B + (IX(i) * N + IX(c)), g[i]);
         }
+        if (keep_walls && ((bd.y >> lane) & 1u)) {
+            // a wall cell: the same 19 stored values, contiguous, for the ghost pass
+            T *wv = (T *)a.bvals + (size_t)19 * (bd.x + __popc(bd.y & ((1u << lane) - 1u)));
+#pragma unroll
+            for (int i = 0; i < 19; i++) {
+                if constexpr (scaled) Store<LBM_F16S>::st_scaled(wv + i, g[i]);
+                else Store<S>::st(wv + i, g[i]);
+            }
+        }
     }
 }
 
@@ -233,6 +275,10 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     a.rt = c.rt;
     a.sk = make_srt_k(c.rt.d_nu, c.F);
     const bool segs = BC == 1 && c.nseg > 0;
+    a.seg_bnd = c.seg_bnd;
+    a.bvals = (segs && c.bvals_ready && c.static_links && S != LBM_F64) ? c.bvals : nullptr;
+    a.wrec = c.wrec;
+    a.gvals = c.gvals;
     a.seg = c.seg;
     a.nseg = segs ? c.nseg : 0;
     a.fd_ny = FastDiv((unsigned)c.ny);

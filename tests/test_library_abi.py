@@ -39,7 +39,11 @@ def test_workspace_bytes_host_only(lib):
     b16 = lbm.workspace_bytes(g16)
     N = 148 * 148 * 438
     assert b32 >= 2 * 19 * 4 * N
-    assert b32 - b16 == pytest.approx(2 * 19 * 2 * N, rel=0.01)
+    # storage-dependent parts: two population buffers, the wall cells'
+    # values (19 per possible site, default N/4 + 65536 sites) and the
+    # compact ghost values (one per possible link, default N/4 + 65536)
+    ms = N // 4 + 65536
+    assert b32 - b16 == pytest.approx(2 * 19 * 2 * N + 19 * 2 * ms + 2 * ms, rel=0.01)
     assert lbm.workspace_bytes(lbm.make_grid(2, 2, 2)) == 0
     assert lbm.workspace_bytes(lbm.make_grid(16, 16, 16, storage=9)) == 0
 
