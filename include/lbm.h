@@ -162,6 +162,21 @@ lbm_status lbm_stats(lbm_ctx *ctx, int flags, lbm_stats_t *out);
 #define LBM_SPECTRUM_MAX_BINS 2048
 lbm_status lbm_spectrum(lbm_ctx *ctx, int flags, int nbins, double *E, double *D);
 
+/* Radial profiles of the pipe (Sec. 2.2: statistics against the distance
+ * to the axis), for the cells inside the pipe, in nbins bins
+ * b = floor(r nbins / R), r the distance to the axis (cells at
+ * ((nx-1)/2, (ny-1)/2)). out: host array of nbins x LBM_PROF_NQ doubles,
+ * bin-major; per bin the number of cells, then the means over its cells of
+ * u_r, u_theta, u_z, u_r^2, u_theta^2, u_z^2, u_r u_z, u_r u_theta,
+ * u_theta u_z, rho and 2 nu s_ij s_ij (central differences). The velocity is
+ * that of lbm_stats (LBM_STATS_UNMASK in flags as there). One snapshot:
+ * time averages are the caller's sums over calls. Scratch: the population
+ * buffer that the next step overwrites. Syncs. Errors: LBM_EINVAL,
+ * LBM_ESTATE (no pipe), LBM_ENOMEM. */
+#define LBM_PROF_NQ 12
+#define LBM_PROF_MAX_BINS 256
+lbm_status lbm_pipe_profiles(lbm_ctx *ctx, int flags, int nbins, double *out);
+
 #define LBM_FIELD_RHO 0      /* N doubles */
 #define LBM_FIELD_U 1        /* 3N doubles */
 #define LBM_FIELD_POPS 2     /* 19N doubles, unshifted f_i (post-collision state) */

@@ -379,6 +379,72 @@ cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scal
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ pipe radial profiles ----
+// Per radial bin b = floor(r nbins / R) of the cells inside the pipe, the
+// sums of 1, u_r, u_theta, u_z, their products, rho and 2 nu s_ij s_ij
+// (statistics velocity, central differences); FP64 shared sums per block,
+// the blocks added on the host in a fixed order. r and the bin use
+// explicitly rounded operations so that a cell on a bin edge falls in the
+// same bin everywhere.
+constexpr int PROF_NQ = LBM_PROF_NQ;
+constexpr int PROF_BLOCKS = 304;
+
+__global__ void __launch_bounds__(SB) pipe_profile_kernel(const double *u, const double *rho, const uint8_t *flags,
+                                                         int nx, int ny, int nz, long long N, double cx, double cy,
+                                                         double R, int nbins, double nu, double *part) {
+    extern __shared__ double sp[];  // nbins x PROF_NQ
+    for (int i = threadIdx.x; i < nbins * PROF_NQ; i += blockDim.x) sp[i] = 0.0;
+    __syncthreads();
+    for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)gridDim.x * SB) {
+        if (flags[c] & FL_SOLID) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double dx = __dsub_rn((double)x, cx), dy = __dsub_rn((double)y, cy);
+        const double r = sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        const int b = (int)floor(__ddiv_rn(__dmul_rn(r, (double)nbins), R));
+        if (b < 0 || b >= nbins) continue;
+        const double ux = u[c], uy = u[N + c], uz = u[2 * N + c];
+        const double ur = r > 0.0 ? (ux * dx + uy * dy) / r : ux;
+        const double ut = r > 0.0 ? (uy * dx - ux * dy) / r : uy;
+        const double q[PROF_NQ] = {1.0,     ur,      ut,      uz,      ur * ur, ut * ut,
+                                   uz * uz, ur * uz, ur * ut, ut * uz, rho[c],  cell_eps(u, x, y, z, nx, ny, nz, N, nu)};
+        double *row = sp + b * PROF_NQ;
+        for (int k = 0; k < PROF_NQ; k++) atomicAdd(row + k, q[k]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins * PROF_NQ; i += blockDim.x) part[(size_t)blockIdx.x * nbins * PROF_NQ + i] = sp[i];
+}
+
+size_t pipe_profile_scratch_bytes(int nbins) { return sizeof(double) * (size_t)PROF_BLOCKS * nbins * PROF_NQ; }
+
+// scratch: the population buffer that the next step overwrites
+cudaError_t run_pipe_profiles(Ctx &c, int flags, int nbins, double *out) {
+    cudaError_t e;
+    if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
+    const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
+    if (!(ibm && (flags & LBM_STATS_UNMASK)))
+        if ((e = launch_mask(c)) != cudaSuccess) return e;
+    double *part = (double *)c.fB;
+    const double nu = (c.tau - 0.5) / 3.0;
+    count_launch(c, G_STATS);
+    pipe_profile_kernel<<<PROF_BLOCKS, SB, sizeof(double) * nbins * PROF_NQ, c.stream>>>(
+        c.u_f, c.rho_f, c.flags, c.nx, c.ny, c.nz, c.N, c.pipe_cx, c.pipe_cy, c.pipe_R, nbins, nu, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::vector<double> hp((size_t)PROF_BLOCKS * nbins * PROF_NQ);
+    if ((e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, c.stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    for (int b = 0; b < nbins; b++) {
+        double s[PROF_NQ] = {0};
+        for (int blk = 0; blk < PROF_BLOCKS; blk++)  // fixed block order
+            for (int k = 0; k < PROF_NQ; k++) s[k] += hp[((size_t)blk * nbins + b) * PROF_NQ + k];
+        const double cnt = s[0];
+        out[(size_t)b * PROF_NQ] = cnt;
+        for (int k = 1; k < PROF_NQ; k++) out[(size_t)b * PROF_NQ + k] = cnt > 0.0 ? s[k] / cnt : 0.0;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_mask(Ctx &c) {
     count_launch(c, G_STATS);
     mask_kernel<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx,

@@ -976,6 +976,18 @@ lbm_status lbm_spectrum(lbm_ctx *h, int flags, int nbins, double *E, double *D) 
     return s;
 }
 
+lbm_status lbm_pipe_profiles(lbm_ctx *h, int flags, int nbins, double *out) {
+    CTX_CHECK(h);
+    if (!out || nbins < 1 || nbins > LBM_PROF_MAX_BINS) return fail(c, LBM_EINVAL, "bad profile arguments");
+    if (!c.has_pipe) return fail(c, LBM_ESTATE, "no pipe");
+    if (pipe_profile_scratch_bytes(nbins) > 19 * (size_t)c.N * storage_bytes(c.storage))
+        return fail(c, LBM_ENOMEM, "profile scratch does not fit the idle population buffer");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    CK(run_pipe_profiles(c, flags, nbins, out));
+    return s;
+}
+
 lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
     CTX_CHECK(h);
     if (!dst) return fail(c, LBM_EINVAL, "null destination");
