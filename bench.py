@@ -378,6 +378,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=PIPE["nz"],
                     help="pipe length in cells (default 438; shorter only for profiler captures)")
+    ap.add_argument("--wall", default="ibb", choices=["ibb", "ibm_b"],
+                    help="wall treatment of the main line (default ibb; ibm_b only for profiler captures "
+                         "of the IBM step, whose line is then not the benchmark's)")
     args = ap.parse_args()
     global NZ
     NZ = args.nz
@@ -426,8 +429,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(dev)
-    main_res = run_case(lbm, torch, "pipe_ibb_f32", PIPE["nx"], PIPE["ny"], NZ, PP["tau"], (0, 0, PP["g"]),
-                        lbm.F32, lbm.RATES_SRT, lbm.BC_IBB, args.steps, args.warmup, setup)
+    main_bc = lbm.BC_IBB if args.wall == "ibb" else lbm.BC_IBM_B
+    main_res = run_case(lbm, torch, "pipe_" + args.wall + "_f32", PIPE["nx"], PIPE["ny"], NZ, PP["tau"],
+                        (0, 0, PP["g"]), lbm.F32, lbm.RATES_SRT, main_bc, args.steps, args.warmup, setup)
     clk = clocks.stop()
     ms_total = main_res["ms"]
     if dist:
@@ -482,7 +486,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "MLUPS (pipe 148x148x438, IBB wall)",
+            "metric": "MLUPS (pipe 148x148x438, IBB wall)" if args.wall == "ibb" else "MLUPS (pipe, IBM-B wall)",
             "value": round(value, 1),
             "unit": "MLUPS",
             "n_gpus": world,
@@ -495,13 +499,13 @@ def main():
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"pipe D=146 L={NZ} in 148x148x{NZ} D3Q19, FP32 populations, SRT, nu=0.0032, "
-                                   "Re_tau=180 body force, linear IBB wall",
+                                   "Re_tau=180 body force, " + ("linear IBB wall" if args.wall == "ibb" else "IBM-B wall"),
                        "fluid_cells": main_res["fluid_cells"], "parallelism": f"replicas x{world}",
                        "l2": "no flush: populations 2x1.46 GB >> 129 MB L2"},
-            "roofline": {"bound": "hbm", "kernel": "stream_collide_bulk<f32,srt,ibb>",
+            "roofline": {"bound": "hbm", "kernel": "stream_collide_bulk<f32,srt," + args.wall[:3] + ">",
                          "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind,
-                         "traffic": traffic_for("stream_collide_bulk_pipe_f32"),
+                         "traffic": traffic_for("stream_collide_bulk_pipe_f32") if args.wall == "ibb" else None,
                          "algorithmic_bytes_per_launch": bulk_bytes,
                          "avg_launch_ms": round(bulk_ms, 5)},
             "group_ms_per_step": {k: round(v / args.steps, 4) for k, v in prof["ms"].items() if v > 0},

@@ -181,15 +181,13 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
 
 // ------------------------------------------------------------ IBM cells ----
 struct IbmCollideArgs {
-    const void *A;
-    void *B;
+    void *B;  // streamed populations of the support cells, collided in place
     const int *site_cell;
     const uint8_t *flags;
     const void *sup_F;  // arithmetic type of the storage
     unsigned *status;
     const long long *counts;
     long long max_sites;
-    int nx, ny, nz;
     long long N;
     double F[3];
     float Fs[3];
@@ -197,24 +195,19 @@ struct IbmCollideArgs {
 };
 
 template <int S, bool SRT>
-__global__ void __launch_bounds__(128) ibm_collide(IbmCollideArgs a) {
+__global__ void __launch_bounds__(256) ibm_collide(IbmCollideArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
     const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns;
          s += (long long)gridDim.x * blockDim.x) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int c = a.site_cell[s];
-    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-    const T *__restrict__ A = (const T *)a.A;
     T *__restrict__ B = (T *)a.B;
     const size_t N = (size_t)a.N;
+    // the bulk sweep left this cell's streamed populations f_i(x) = f*_i(x - c_i) in B
     R g[19];
 #pragma unroll
-    for (int i = 0; i < 19; i++) {
-        const int xs = wrap(x - cx(i), nx), ys = wrap(y - cy(i), ny), zs = wrap(z - cz(i), nz);
-        g[i] = Store<S>::ld(A + i * N + (xs + nx * (ys + ny * zs)));
-    }
+    for (int i = 0; i < 19; i++) g[i] = Store<S>::ld(B + (i * N + c));
     const bool fluid = !(a.flags[c] & FL_SOLID);
     const R *sF = (const R *)a.sup_F;
     const R fs = fluid ? R(1) : R(0);
@@ -225,7 +218,7 @@ __global__ void __launch_bounds__(128) ibm_collide(IbmCollideArgs a) {
     collide<R, true, SRT>(g, Fx, Fy, Fz, a.rt, rho, ux, uy, uz);
     watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
-    for (int i = 0; i < 19; i++) Store<S>::st(B + i * N + c, g[i]);
+    for (int i = 0; i < 19; i++) Store<S>::st(B + (i * N + c), g[i]);
     }
 }
 
@@ -349,7 +342,6 @@ template <int S>
 static cudaError_t launch_ibm_s(Ctx &c) {
     if (c.max_sites == 0) return cudaSuccess;
     IbmCollideArgs a;
-    a.A = c.fA;
     a.B = c.fB;
     a.site_cell = c.site_cell;
     a.flags = c.flags;
@@ -357,16 +349,13 @@ static cudaError_t launch_ibm_s(Ctx &c) {
     a.status = c.d_status;
     a.counts = c.d_counts;
     a.max_sites = c.max_sites;
-    a.nx = c.nx;
-    a.ny = c.ny;
-    a.nz = c.nz;
     a.N = c.N;
     for (int d = 0; d < 3; d++) {
         a.F[d] = c.F[d];
         a.Fs[d] = (float)c.F[d];
     }
     a.rt = c.rt;
-    const int tb = 128;
+    const int tb = 256;
     const unsigned nb = site_grid(c, tb);
     count_launch(c, G_IBMCOL);
     if (c.rates == LBM_RATES_SRT) ibm_collide<S, true><<<nb, tb, 0, c.stream>>>(a);

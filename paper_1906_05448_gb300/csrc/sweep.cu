@@ -4,8 +4,9 @@
 // population plane is read and written in coalesced rows; the 19 loads of a
 // cell are independent and issued together. IBB: solid cells are never
 // swept (the pipe's fluid runs are listed as segments, see segments.h).
-// IBM: support cells only store rho and u* (first half of the direct
-// forcing, Sec. 2.1) and are collided later by ibm_collide.
+// IBM: support cells store rho and u* (first half of the direct forcing,
+// Sec. 2.1) and their streamed populations, which ibm_collide later
+// collides in place with the IBM force.
 #include "lbm_internal.cuh"
 
 #include <type_traits>
@@ -18,6 +19,8 @@ struct SweepArgs {
     const uint4 *seg;  // optional warp items of fluid-run pieces (segments.h)
     long long nseg;
     FastDiv fd_ny;  // row -> (y, z)
+    FastDiv fd_nx;     // cell -> (row, x) without a segment list
+    long long nflat;   // without a segment list: items of blockDim.x consecutive cells
     const uint8_t *flags;
     const int *aux;
     void *sup_ru;  // (rho, u*) per support site, arithmetic type of the storage
@@ -59,8 +62,9 @@ constexpr int bulk_min_blocks(int S, bool SRT, int BC) {
 #define LBM_IDX32 1  // 32-bit element indices where they fit
 #endif
 
-// Work items: without a segment list, one item = one row piece of
-// blockDim.x cells. With a segment list (IBB walls whose rows have a solid
+// Work items: without a segment list, one item = blockDim.x consecutive
+// cells in cell order, across row ends, so warps are full and start on a
+// 32-cell boundary whatever nx is. With a segment list (IBB walls whose rows have a solid
 // margin, e.g. the pipe), one warp = one segment of up to 32 consecutive
 // cells inside the fluid extent of a row, so no lanes idle on the margin.
 // The block walks its items with a grid stride and loads the flag byte of
@@ -71,10 +75,9 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
     typedef typename Store<S>::R R;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool segs = a.nseg > 0;  // one warp per item
-    const int ipr = (nx + blockDim.x - 1) / blockDim.x;  // items per row (no segment list)
     const int lane = threadIdx.x & 31;
-    const long long items = segs ? a.nseg : (long long)ny * nz * ipr;
-    const long long stride = segs ? (long long)gridDim.x * (blockDim.x * blockDim.y / 32) : (long long)gridDim.x * blockDim.y;
+    const long long items = segs ? a.nseg : a.nflat;
+    const long long stride = segs ? (long long)gridDim.x * (blockDim.x / 32) : (long long)gridDim.x;
     const T *__restrict__ A = (const T *)a.A;
     T *__restrict__ B = (T *)a.B;
     // element index type: 32-bit when every index fits (19 N < 2^32), so an
@@ -88,8 +91,7 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         if constexpr (scaled) return Store<LBM_F16S>::ld_scaled(p);
         else return Store<S>::ld(p);
     };
-    long long w = segs ? (long long)blockIdx.x * (blockDim.x * blockDim.y / 32) + (threadIdx.y * blockDim.x + threadIdx.x) / 32
-                       : (long long)blockIdx.x * blockDim.y + threadIdx.y;
+    long long w = segs ? (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : (long long)blockIdx.x;
     // warp item: up to two pieces of fluid runs (row, word), see segments.h;
     // the next item is loaded one iteration ahead
     uint4 sg_next = make_uint4(0u, 0u, 0u, 0u);
@@ -107,8 +109,11 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         wr_next = wall_record(bd_next);
     }
     auto cell_of = [&](long long item, int &x, int &row) {  // without a segment list
-        row = (int)(item / ipr);
-        x = (int)(item - (long long)row * ipr) * blockDim.x + threadIdx.x;
+        // consecutive cells across row ends (N < 2^31): full warps for any nx
+        const unsigned cc = (unsigned)item * blockDim.x + threadIdx.x;
+        row = (int)a.fd_nx.div(cc);
+        x = (int)(cc - (unsigned)row * (unsigned)nx);
+        if (row >= ny * nz) x = nx;  // past the last cell
     };
     // segments cover fluid cells only: no flag byte is needed (IBB)
     const bool read_flags = BC != 0 && !(BC == 1 && segs);
@@ -219,23 +224,26 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
             }
             const R rho = R(1) + drho;
             const int s = a.aux[c];
-            if (s < 0 || s >= a.max_sites) continue;
-            R *ru = (R *)a.sup_ru + 4 * (size_t)s;
-            const R ir = R(1) / rho;
-            ru[0] = rho;
-            ru[1] = jx * ir;
-            ru[2] = jy * ir;
-            ru[3] = jz * ir;
-            continue;
+            if (s >= 0 && s < a.max_sites) {
+                R *ru = (R *)a.sup_ru + 4 * (size_t)s;
+                const R ir = R(1) / rho;
+                ru[0] = rho;
+                ru[1] = jx * ir;
+                ru[2] = jy * ir;
+                ru[3] = jz * ir;
+            }
+            // the streamed populations wait in B for the forced collision
+            // (ibm_collide, in place), so every row of B is written whole
+        } else {
+            R rho, ux, uy, uz;
+            const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
+            if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
+                collide_srt_k<FORCE, scaled ? 10 : 0>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
+            else
+                collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2),
+                                       a.rt, rho, ux, uy, uz);
+            watchdog(rho, ux, uy, uz, a.status);
         }
-        R rho, ux, uy, uz;
-        const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
-        if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
-            collide_srt_k<FORCE, scaled ? 10 : 0>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
-        else
-            collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2), a.rt,
-                                   rho, ux, uy, uz);
-        watchdog(rho, ux, uy, uz, a.status);
 #pragma unroll
         for (int i = 0; i < 19; i++) {
             if constexpr (scaled) Store<LBM_F16S>::st_scaled(B + (IX(i) * N + IX(c)), g[i]);
@@ -282,16 +290,10 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     a.seg = c.seg;
     a.nseg = segs ? c.nseg : 0;
     a.fd_ny = FastDiv((unsigned)c.ny);
-    int bx = ((c.nx + 31) / 32) * 32;
-    if (bx > 256) bx = 256;
-    int by = 256 / bx;
-    if (by < 1) by = 1;
-    if (segs) {
-        bx = 256;  // 8 warps, one segment each
-        by = 1;
-    }
-    const long long items = segs ? c.nseg : (long long)c.ny * c.nz * ((c.nx + bx - 1) / bx);
-    long long nb = segs ? (items + 7) / 8 : (items + by - 1) / by;
+    a.fd_nx = FastDiv((unsigned)c.nx);
+    const int bx = 256;  // 8 warps: one segment each, or 256 consecutive cells
+    a.nflat = (c.N + bx - 1) / bx;
+    long long nb = segs ? (c.nseg + 7) / 8 : a.nflat;
     if (LBM_BULK_PERSIST == 1 || (LBM_BULK_PERSIST == 2 && segs)) {
         // persistent grid: as many blocks as fit on the device at once
         static int resident[4][2][3][2];
@@ -301,14 +303,14 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (force)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true, true>, bx * by, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, true, true>, bx, 0);
             else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false, true>, bx * by, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stream_collide_bulk<S, SRT, BC, false, true>, bx, 0);
             res = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         }
         if (nb > res) nb = res;
     }
-    dim3 block(bx, by), grid((unsigned)nb);
+    dim3 block(bx), grid((unsigned)nb);
     count_launch(c, G_BULK);
     const bool i32 = LBM_IDX32 && 19 * (unsigned long long)c.N + 64 < (1ULL << 32);
     if (force && i32)
