@@ -326,7 +326,16 @@ struct SiteArgs {
     long long max_sites, max_links;
     unsigned *status;
     FastDiv dx, dxy;  // division by nx and nx * ny
+    double dn[3], hn[3];  // nx, ny, nz and their halves as doubles
 };
+
+// minimum image with the box size and its half given as doubles (no
+// int-to-double conversion per call; the same values as gmimg)
+__device__ __forceinline__ double gmimg_d(double d, double n, double h) {
+    if (d > h) d = __dsub_rn(d, n);
+    else if (d < -h) d = __dadd_rn(d, n);
+    return d;
+}
 
 // solid-neighbour mask of a fluid cell (bit l: x + c_l solid)
 __device__ __forceinline__ unsigned solid_mask(const SiteArgs &a, int x, int y, int z) {
@@ -536,21 +545,36 @@ __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, dou
     const int xb = gwrap(x + cx(l), a.nx), yb = gwrap(y + cy(l), a.ny), zb = gwrap(z + cz(l), a.nz);
     const long long cb = (long long)xb + (long long)a.nx * (yb + (long long)a.ny * zb);
     const int own = a.owner[cb];
-    const double cl0 = (double)cx(l), cl1 = (double)cy(l), cl2 = (double)cz(l);
-    const double aa = (double)(cx(l) * cx(l) + cy(l) * cy(l) + cz(l) * cz(l));
+    // FP64 issue is what this kernel costs on GB300, so c_l and |c_l|^2 come
+    // from selects on constants rather than int-to-double conversions (the
+    // values are the same)
+    const int i0 = cx(l), i1 = cy(l), i2 = cz(l);
+    const double cl0 = i0 > 0 ? 1.0 : (i0 < 0 ? -1.0 : 0.0);
+    const double cl1 = i1 > 0 ? 1.0 : (i1 < 0 ? -1.0 : 0.0);
+    const double cl2 = i2 > 0 ? 1.0 : (i2 < 0 ? -1.0 : 0.0);
+    const bool diag = (i0 != 0) + (i1 != 0) + (i2 != 0) == 2;  // |c_l|^2 = 2
+    const double aa = diag ? 2.0 : 1.0;
     double t;
     if (own != NO_OWNER) {
         pid = own;
         const double *Xp = a.X + 3 * own;
         const double Rp = a.R[own];
-        const double dx = gmimg(__dsub_rn((double)x, Xp[0]), a.nx);
-        const double dy = gmimg(__dsub_rn((double)y, Xp[1]), a.ny);
-        const double dz = gmimg(__dsub_rn((double)z, Xp[2]), a.nz);
-        const double b = __dadd_rn(__dadd_rn(__dmul_rn(cl0, dx), __dmul_rn(cl1, dy)), __dmul_rn(cl2, dz));
+        const double dx = gmimg_d(__dsub_rn((double)x, Xp[0]), a.dn[0], a.hn[0]);
+        const double dy = gmimg_d(__dsub_rn((double)y, Xp[1]), a.dn[1], a.hn[1]);
+        const double dz = gmimg_d(__dsub_rn((double)z, Xp[2]), a.dn[2], a.hn[2]);
+        // b = c_l . d as ((c0 dx + c1 dy) + c2 dz): with components in
+        // {-1, 0, 1} this is the sum of the one or two nonzero terms, which
+        // gives the same bits whenever that sum is not zero; a zero sum takes
+        // the full form for the sign of zero
+        const double u = i0 ? (i0 > 0 ? dx : -dx) : (i1 ? (i1 > 0 ? dy : -dy) : (i2 > 0 ? dz : -dz));
+        const double v = !diag ? 0.0 : (i2 ? (i2 > 0 ? dz : -dz) : (i1 > 0 ? dy : -dy));
+        double b = __dadd_rn(u, v);
+        if (b == 0.0) b = __dadd_rn(__dadd_rn(__dmul_rn(cl0, dx), __dmul_rn(cl1, dy)), __dmul_rn(cl2, dz));
         const double c0 = __dsub_rn(dist2(dx, dy, dz), __dmul_rn(Rp, Rp));
         double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(aa, c0));
         if (disc < 0.0) disc = 0.0;
-        t = exact_div_c2(__dsub_rn(-b, __dsqrt_rn(disc)), aa);
+        const double num = __dsub_rn(-b, __dsqrt_rn(disc));
+        t = diag ? num * 0.5 : num;  // division by |c_l|^2 = 1 or 2, exact
     } else {
         pid = -1;
         const double a2 = (double)(cx(l) * cx(l) + cy(l) * cy(l));
@@ -684,6 +708,11 @@ cudaError_t build_sites(Ctx &c, int mode) {
     a.status = c.d_status;
     a.dx = FastDiv((unsigned)c.nx);
     a.dxy = FastDiv((unsigned)(c.nx * c.ny));
+    const int nd[3] = {c.nx, c.ny, c.nz};
+    for (int d = 0; d < 3; d++) {
+        a.dn[d] = (double)nd[d];
+        a.hn[d] = 0.5 * (double)nd[d];
+    }
     const int nblk = (int)((c.N + TILE - 1) / TILE);
     count_launch(c, G_GEOM, mode == 1 ? 4 : 3);
     site_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
