@@ -378,11 +378,12 @@ __device__ __forceinline__ unsigned solid_bits6(const SiteArgs &a, long long row
     return ((left & FL_SOLID) ? 1u : 0u) | (four << 1) | ((right & FL_SOLID) ? 32u : 0u);
 }
 
-__device__ __forceinline__ void cell_info4(const SiteArgs &a, long long c0, bool site[CPT], unsigned mask[CPT]) {
+// Solid bits around the 4 cells c0 .. c0+3 of one x-row word: rows[dz+1][dy+1]
+// holds the cells x0-1 .. x0+4 of the row (y+dy, z+dz) in bits 0 .. 5.
+__device__ __forceinline__ void solid_rows4(const SiteArgs &a, long long c0, unsigned rows[3][3]) {
     const unsigned zq = a.dxy.div((unsigned)c0), rem = (unsigned)c0 - zq * (unsigned)(a.nx * a.ny);
     const unsigned yq = a.dx.div(rem);
     const int x0 = (int)(rem - yq * (unsigned)a.nx), y = (int)yq, z = (int)zq;
-    unsigned rows[3][3];  // [dz + 1][dy + 1]: bits of x0-1 .. x0+4
 #pragma unroll
     for (int dz = -1; dz <= 1; dz++)
 #pragma unroll
@@ -404,18 +405,38 @@ __device__ __forceinline__ void cell_info4(const SiteArgs &a, long long c0, bool
             const unsigned m = w & 0x01010101u * FL_SOLID;
             rows[dz + 1][dy + 1] = (((m >> 0) & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << 1;
         }
+}
+
+// Direction-major neighbour bits of the 4 cells: bit k of v[l] is set when
+// cell c0 + k is a fluid cell of the grid and its neighbour x + c_l is solid.
+// Counting needs only popcounts of these 18 words; the per-cell masks are
+// formed for the few cells that have a link.
+__device__ __forceinline__ void link_bits4(const SiteArgs &a, long long c0, unsigned v[19]) {
+    unsigned rows[3][3];
+    solid_rows4(a, c0, rows);
+    const long long left = a.N - c0;
+    const unsigned valid = left >= CPT ? (1u << CPT) - 1u : (left > 0 ? (1u << left) - 1u : 0u);
+    const unsigned fluid = ~(rows[1][1] >> 1) & valid;
+    v[0] = 0;
+#pragma unroll
+    for (int l = 1; l < 19; l++) v[l] = (rows[cz(l) + 1][cy(l) + 1] >> (1 + cx(l))) & fluid;
+}
+
+__device__ __forceinline__ void cell_info4(const SiteArgs &a, long long c0, bool site[CPT], unsigned mask[CPT]) {
+    unsigned v[19];
+    link_bits4(a, c0, v);
+    unsigned any = 0;
+#pragma unroll
+    for (int l = 1; l < 19; l++) any |= v[l];
 #pragma unroll
     for (int k = 0; k < CPT; k++) {
-        site[k] = false;
-        mask[k] = 0;
-        if (c0 + k >= a.N) continue;
-        if ((rows[1][1] >> (k + 1)) & 1u) continue;  // the cell itself is solid
+        site[k] = (any >> k) & 1u;
         unsigned m = 0;
+        if (site[k]) {
 #pragma unroll
-        for (int l = 1; l < 19; l++)
-            if ((rows[cz(l) + 1][cy(l) + 1] >> (k + 1 + cx(l))) & 1u) m |= 1u << l;
+            for (int l = 1; l < 19; l++) m |= ((v[l] >> k) & 1u) << l;
+        }
         mask[k] = m;
-        site[k] = m != 0;
     }
 }
 
@@ -452,13 +473,14 @@ __global__ void __launch_bounds__(CT) site_count_kernel(SiteArgs a) {
     const long long base = (long long)blockIdx.x * TILE + (long long)threadIdx.x * CPT;
     long long ns = 0, nl = 0;
     if (a.mode == 1 && a.nx % 4 == 0 && base < a.N) {
-        bool site[CPT];
-        unsigned mask[CPT];
-        cell_info4(a, base, site, mask);
-        for (int k = 0; k < CPT; k++) {
-            ns += site[k];
-            nl += __popc(mask[k]);
+        unsigned v[19], any = 0;
+        link_bits4(a, base, v);
+#pragma unroll
+        for (int l = 1; l < 19; l++) {
+            any |= v[l];
+            nl += __popc(v[l]);
         }
+        ns = __popc(any);
     } else {
         for (int k = 0; k < CPT; k++) {
             bool site;
