@@ -483,6 +483,22 @@ struct IbmArgs {
     int pass, last;
 };
 
+// (rho, u*) of one support site: one 16-byte load in FP32
+__device__ __forceinline__ void ld_site4(const float *p, float q[4]) {
+    const float4 v = __ldg((const float4 *)p);
+    q[0] = v.x;
+    q[1] = v.y;
+    q[2] = v.z;
+    q[3] = v.w;
+}
+__device__ __forceinline__ void ld_site4(const double *p, double q[4]) {
+    const double2 v0 = __ldg((const double2 *)p), v1 = __ldg((const double2 *)p + 1);
+    q[0] = v0.x;
+    q[1] = v0.y;
+    q[2] = v1.x;
+    q[3] = v1.y;
+}
+
 // Interpolation, one warp per marker: lane k takes stencil nodes k and k+32;
 // U*_l = sum u* delta, rho_l = sum rho delta (fixed butterfly reduction);
 // F_l = 2 rho_l (U_d - U*_l).
@@ -495,17 +511,26 @@ __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
     const R *E = (const R *)a.mE + 3 * l;
     const R e0 = E[0], e1 = E[1], e2 = E[2];  // X - floor(X)
     const int b0 = a.mB[3 * l], b1 = a.mB[3 * l + 1], b2 = a.mB[3 * l + 2];  // floor(X) - 1, wrapped
+    // the 12 one-dimensional kernel values of the marker: lane 4 d + o holds
+    // phi(o - 1 - e_d); every node's weight is a product of three of them
+    R phi = R(0);
+    if (lane < 12) {
+        const int d = lane >> 2, o = lane & 3;
+        phi = peskin_r<R>(R(o - 1) - (d == 0 ? e0 : (d == 1 ? e1 : e2)));
+    }
     R U0 = 0, U1 = 0, U2 = 0, rl = 0;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int k = lane + 32 * h;
         const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
-        const R w = peskin_r<R>(R(kx - 1) - e0) * peskin_r<R>(R(ky - 1) - e1) * peskin_r<R>(R(kz - 1) - e2);
+        const R w = __shfl_sync(0xffffffffu, phi, kx) * __shfl_sync(0xffffffffu, phi, 4 + ky) *
+                    __shfl_sync(0xffffffffu, phi, 8 + kz);
         const long long c = (long long)pwrap(b0 + kx, a.nx) +
                             (long long)a.nx * (pwrap(b1 + ky, a.ny) + (long long)a.ny * pwrap(b2 + kz, a.nz));
         const int s = a.aux[c];
         if (s < 0 || s >= a.max_sites) continue;
-        const R *q = ru + 4 * (size_t)s;
+        R q[4];
+        ld_site4(ru + 4 * (size_t)s, q);
         rl += w * q[0];
         U0 += w * q[1];
         U1 += w * q[2];
@@ -532,22 +557,6 @@ __global__ void __launch_bounds__(256) ibm_interp_warp_kernel(IbmArgs a) {
         acc[3 * l + d] = s;
         if (a.last) a.mFacc[3 * l + d] = double(s);
     }
-}
-
-// (rho, u*) of one support site: one 16-byte load in FP32
-__device__ __forceinline__ void ld_site4(const float *p, float q[4]) {
-    const float4 v = __ldg((const float4 *)p);
-    q[0] = v.x;
-    q[1] = v.y;
-    q[2] = v.z;
-    q[3] = v.w;
-}
-__device__ __forceinline__ void ld_site4(const double *p, double q[4]) {
-    const double2 v0 = __ldg((const double2 *)p), v1 = __ldg((const double2 *)p + 1);
-    q[0] = v0.x;
-    q[1] = v0.y;
-    q[2] = v1.x;
-    q[3] = v1.y;
 }
 
 // Pipe wall tiles. The ring of markers is the same in every z plane and sits
