@@ -812,11 +812,18 @@ __global__ void __launch_bounds__(256) ibm_spread_particle_kernel(ParticleSpread
     const int o0 = (int)floor(Xp0) - h, o1 = (int)floor(Xp1) - h, o2 = (int)floor(Xp2) - h;
     const int l0 = a.m_first[p], l1 = a.m_first[p + 1];
     const R *mFr = (const R *)a.mFr;
+    const int lane = threadIdx.x & 31;
+    // 64 (marker, node) pairs per marker: a warp's 32 pairs share one marker
+    // and every warp runs the same number of rounds (64 n is a multiple of 32)
     for (long long t = threadIdx.x; t < 64LL * (l1 - l0); t += blockDim.x) {
         const int l = l0 + (int)(t >> 6), k = (int)(t & 63);
         const int kx = k & 3, ky = (k >> 2) & 3, kz = k >> 4;
         const R *E = (const R *)a.mE + 3 * l;
-        const R w = peskin_r<R>(R(kx - 1) - E[0]) * peskin_r<R>(R(ky - 1) - E[1]) * peskin_r<R>(R(kz - 1) - E[2]);
+        // the marker's 12 one-dimensional kernel values on lanes 0 .. 11
+        R phi = R(0);
+        if (lane < 12) phi = peskin_r<R>(R((lane & 3) - 1) - E[lane >> 2]);
+        const R w = __shfl_sync(0xffffffffu, phi, kx) * __shfl_sync(0xffffffffu, phi, 4 + ky) *
+                    __shfl_sync(0xffffffffu, phi, 8 + kz);
         // box-local node index; the marker base is wrapped, so unwrap the difference
         int i0 = a.mB[3 * l] + kx - o0, i1 = a.mB[3 * l + 1] + ky - o1, i2 = a.mB[3 * l + 2] + kz - o2;
         i0 = i0 < -a.nx / 2 ? i0 + a.nx : (i0 >= a.nx / 2 ? i0 - a.nx : i0);
