@@ -242,6 +242,27 @@ def spectrum_report(lbm, torch, n=256, nbins=222, reps=3):
             "kinetic_energy": float(E.sum()), "spectral_dissipation": float(D.sum())}
 
 
+def budget_report(lbm, torch, nbins=64, steps=20, reps=5):
+    """Time of the pipe's component-wise TKE budget (Eq. 1a-c: two binned
+    passes over the 148x148x438 pipe, FP64 sums) on the benchmark pipe,
+    FP32, IBB, after a few steps; the near-wall dissipation and production
+    show that the terms are populated."""
+    L = lbm.Lattice(PIPE["nx"], PIPE["ny"], PIPE["nz"], PP["tau"], force=(0, 0, PP["g"]), storage=lbm.F32)
+    L.init_velocity(pipe_field(PIPE["nz"]))
+    L.set_pipe(PIPE["radius"])
+    L.step(steps, lbm.BC_IBB)
+    L.tke_budget(nbins)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        B = L.tke_budget(nbins)
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    L.close()
+    return {"grid": f"{PIPE['nx']}x{PIPE['ny']}x{PIPE['nz']}", "nbins": nbins, "ms_per_budget": round(ms, 3),
+            "cells": int(B[:, 0].sum()), "min_E_Dz": float(B[:, 5].min()), "max_abs_E_Oz": float(np.abs(B[:, 1]).max()),
+            "finite": bool(np.all(np.isfinite(B)))}
+
+
 def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
     """Learned closure on the particle-laden 256^3 box (IBM-B): paired
     IBB/IBM-B runs of seeds 0-7 give up to 1e6 training samples, seeds 8-9
@@ -469,10 +490,15 @@ def main():
     precision = None
     closure_res = None
     spectrum_res = None
+    budget_res = None
     if not args.no_variants and rank == 0:
         precision = precision_report(lbm, torch)
         closure_res = closure_report(lbm, torch)
         spectrum_res = spectrum_report(lbm, torch)
+        try:
+            budget_res = budget_report(lbm, torch)
+        except Exception as ex:  # a diagnostic's failure must not lose the line
+            budget_res = {"error": str(ex)[:200]}
 
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -517,6 +543,7 @@ def main():
             "precision_vs_f64": precision,
             "closure": closure_res,
             "spectrum": spectrum_res,
+            "tke_budget": budget_res,
         }
         print(json.dumps(line))
     if dist:

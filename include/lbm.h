@@ -177,6 +177,24 @@ lbm_status lbm_spectrum(lbm_ctx *ctx, int flags, int nbins, double *E, double *D
 #define LBM_PROF_MAX_BINS 256
 lbm_status lbm_pipe_profiles(lbm_ctx *ctx, int flags, int nbins, double *out);
 
+/* Component-wise TKE budget of the pipe (Eq. 1a-c, Sec. 2.2) of the current
+ * snapshot, in the radial bins of lbm_pipe_profiles (cells with r > 0).
+ * Averages are means over a bin's cells and fluctuations are departures
+ * from them; velocity gradients are central differences of the statistics
+ * velocity (LBM_STATS_UNMASK in flags as for lbm_stats) rotated into
+ * (e_r, e_theta, e_z); p' = c_s^2 rho'; d/dr of a binned profile is a
+ * central difference over the bin centres (b + 1/2) R / nbins, one-sided at
+ * the ends. out: host array of nbins x LBM_BUDGET_NT doubles, bin-major:
+ * the cell count, then E_Oz, E_Tz, E_Pz, E_Vz, E_Dz, E_Tr, E_Pr, E_Vr, E_Dr,
+ * E_Ttheta, E_Ptheta, E_Vtheta, E_Dtheta (production, turbulent transport,
+ * pressure work, viscous diffusion, dissipation); empty bins hold zeros.
+ * One snapshot: time averages are the caller's. Scratch: the population
+ * buffer that the next step overwrites. Syncs. Errors: LBM_EINVAL (bins
+ * outside 1..LBM_PROF_MAX_BINS, null out), LBM_ESTATE (no pipe),
+ * LBM_ENOMEM (scratch larger than that buffer). */
+#define LBM_BUDGET_NT 14
+lbm_status lbm_tke_budget(lbm_ctx *ctx, int flags, int nbins, double *out);
+
 #define LBM_FIELD_RHO 0      /* N doubles */
 #define LBM_FIELD_U 1        /* 3N doubles */
 #define LBM_FIELD_POPS 2     /* 19N doubles, unshifted f_i (post-collision state) */

@@ -988,6 +988,18 @@ lbm_status lbm_pipe_profiles(lbm_ctx *h, int flags, int nbins, double *out) {
     return s;
 }
 
+lbm_status lbm_tke_budget(lbm_ctx *h, int flags, int nbins, double *out) {
+    CTX_CHECK(h);
+    if (!out || nbins < 1 || nbins > LBM_PROF_MAX_BINS) return fail(c, LBM_EINVAL, "bad budget arguments");
+    if (!c.has_pipe) return fail(c, LBM_ESTATE, "no pipe");
+    if (tke_budget_scratch_bytes(nbins) > 19 * (size_t)c.N * storage_bytes(c.storage))
+        return fail(c, LBM_ENOMEM, "budget scratch does not fit the idle population buffer");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK && s != LBM_EUNSTABLE) return s;
+    CK(run_tke_budget(c, flags, nbins, out));
+    return s;
+}
+
 lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
     CTX_CHECK(h);
     if (!dst) return fail(c, LBM_EINVAL, "null destination");

@@ -170,6 +170,8 @@ cudaError_t launch_mask(Ctx &c);  // statistics velocity: solid cells take the r
 cudaError_t run_spectrum(Ctx &c, int flags, int nbins, double *E, double *D);
 cudaError_t run_pipe_profiles(Ctx &c, int flags, int nbins, double *out);
 size_t pipe_profile_scratch_bytes(int nbins);
+cudaError_t run_tke_budget(Ctx &c, int flags, int nbins, double *out);
+size_t tke_budget_scratch_bytes(int nbins);
 size_t spectrum_scratch_bytes(long long N, int nbins);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);
 cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out);
