@@ -177,6 +177,16 @@ lbm_status lbm_spectrum(lbm_ctx *ctx, int flags, int nbins, double *E, double *D
 #define LBM_PROF_MAX_BINS 256
 lbm_status lbm_pipe_profiles(lbm_ctx *ctx, int flags, int nbins, double *out);
 
+/* Non-shear relaxation rates of the MRT collision by d'Humieres group:
+ * energy e (bulk viscosity (2/9)(1/s_e - 1/2); the BGK value 2 nu / 3 at
+ * s_e = 1/tau), energy square eps, energy flux q, pi_xx and pi_ww, and the
+ * third-order m modes. The shear rate stays 1/tau. The paper's solver has
+ * this knob for damping acoustic noise and leaves it off (Sec. 2.2). The
+ * context switches to the multiple-relaxation-time collision; the rates
+ * apply from the next step. Each rate must lie in (0, 2). Errors:
+ * LBM_EINVAL. */
+lbm_status lbm_set_mrt_rates(lbm_ctx *ctx, double s_e, double s_eps, double s_q, double s_pi, double s_m);
+
 /* Component-wise TKE budget of the pipe (Eq. 1a-c, Sec. 2.2) of the current
  * snapshot, in the radial bins of lbm_pipe_profiles (cells with r > 0).
  * Averages are means over a bin's cells and fluctuations are departures

@@ -93,6 +93,7 @@ def lib():
                 "orc_sphere_markers": (None, [ctypes.c_double, ctypes.c_int, _D]),
                 "orc_create": (_P, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, ctypes.c_int]),
                 "orc_destroy": (None, [_P]),
+                "orc_set_group_rates": (None, [_P] + [ctypes.c_double] * 5),
                 "orc_set_threads": (None, [ctypes.c_int]),
                 "orc_get_threads": (ctypes.c_int, []),
                 "orc_init_velocity": (None, [_P, _D, ctypes.c_double]),
@@ -223,6 +224,10 @@ class Sim:
     def init_velocity(self, u, rho0=1.0):
         u = _c64(u).reshape(3, self.N)
         self.L.orc_init_velocity(self.h, _dp(u), float(rho0))
+
+    def set_group_rates(self, s_e, s_eps, s_q, s_pi, s_m):
+        """Non-shear MRT rates by group (e, eps, q, pi, m); shear stays 1/tau."""
+        self.L.orc_set_group_rates(self.h, float(s_e), float(s_eps), float(s_q), float(s_pi), float(s_m))
 
     def set_populations(self, f):
         f = _c64(f).reshape(19, self.N)

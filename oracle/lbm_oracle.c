@@ -285,6 +285,16 @@ static inline double mimg(double d, int n)
  * undriven). */
 static double fext_at(const orc_sim *S, long long c, int d) { return S->solid[c] ? 0.0 : S->Fext[d]; }
 
+void orc_set_group_rates(orc_sim *S, double s_e, double s_eps, double s_q, double s_pi, double s_m)
+{
+    S->s[1] = s_e;
+    S->s[2] = s_eps;
+    S->s[4] = S->s[6] = S->s[8] = s_q;
+    S->s[10] = S->s[12] = s_pi;
+    S->s[16] = S->s[17] = S->s[18] = s_m;
+    S->rates = ORC_RATES_DHUMIERES;
+}
+
 orc_sim *orc_create(int nx, int ny, int nz, double tau, const double *F, int rates)
 {
     orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));

@@ -55,6 +55,11 @@ void   orc_sphere_markers(double RL, int n, double *unit);
 
 /* simulation */
 orc_sim *orc_create(int nx, int ny, int nz, double tau, const double *F, int rates);
+/* Non-shear relaxation rates by d'Humieres group: energy e (bulk viscosity
+ * (2/9)(1/s_e - 1/2)), energy square eps, energy flux q, pi_xx and pi_ww,
+ * and the third-order m modes; the shear rate stays 1/tau. The paper's
+ * solver has this knob for the bulk viscosity but leaves it off (Sec. 2.2). */
+void  orc_set_group_rates(orc_sim *S, double s_e, double s_eps, double s_q, double s_pi, double s_m);
 void  orc_destroy(orc_sim *S);
 void  orc_set_threads(int n);
 int   orc_get_threads(void);

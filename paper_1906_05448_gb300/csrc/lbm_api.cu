@@ -988,6 +988,27 @@ lbm_status lbm_pipe_profiles(lbm_ctx *h, int flags, int nbins, double *out) {
     return s;
 }
 
+lbm_status lbm_set_mrt_rates(lbm_ctx *h, double s_e, double s_eps, double s_q, double s_pi, double s_m) {
+    CTX_CHECK(h);
+    const double v[5] = {s_e, s_eps, s_q, s_pi, s_m};
+    for (double x : v)
+        if (!(x > 0.0 && x < 2.0)) return fail(c, LBM_EINVAL, "relaxation rates must lie in (0, 2)");
+    // kernels take the rates by value at launch: the change applies from the next step
+    c.rates = LBM_RATES_DHUMIERES;
+    Rates &r = c.rt;
+    r.d_e = s_e;
+    r.d_eps = s_eps;
+    r.d_q = s_q;
+    r.d_pi = s_pi;
+    r.d_m = s_m;
+    r.s_e = (float)s_e;
+    r.s_eps = (float)s_eps;
+    r.s_q = (float)s_q;
+    r.s_pi = (float)s_pi;
+    r.s_m = (float)s_m;
+    return LBM_OK;
+}
+
 lbm_status lbm_tke_budget(lbm_ctx *h, int flags, int nbins, double *out) {
     CTX_CHECK(h);
     if (!out || nbins < 1 || nbins > LBM_PROF_MAX_BINS) return fail(c, LBM_EINVAL, "bad budget arguments");

@@ -29,7 +29,7 @@ BC = {"none": BC_NONE, "ibb": BC_IBB, "ibm_u": BC_IBM_U, "ibm_b": BC_IBM_B}
 # every entry point declared in include/lbm.h
 EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_init_velocity", "lbm_set_populations", "lbm_set_pipe",
-    "lbm_add_spheres", "lbm_step", "lbm_stats", "lbm_spectrum", "lbm_pipe_profiles", "lbm_tke_budget", "lbm_get_field", "lbm_num_links", "lbm_get_links",
+    "lbm_add_spheres", "lbm_step", "lbm_stats", "lbm_spectrum", "lbm_pipe_profiles", "lbm_tke_budget", "lbm_set_mrt_rates", "lbm_get_field", "lbm_num_links", "lbm_get_links",
     "lbm_get_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile",
     "lbm_mlp_workspace_bytes", "lbm_mlp_num_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train",
     "lbm_closure_samples", "lbm_closure_targets", "lbm_closure_set_weights",
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = False):
         "lbm_spectrum": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D, _D]),
         "lbm_pipe_profiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
         "lbm_tke_budget": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+        "lbm_set_mrt_rates": (ctypes.c_int, [_P] + [ctypes.c_double] * 5),
         "lbm_get_field": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t]),
         "lbm_num_links": (ctypes.c_int, [_P, _L]),
         "lbm_get_links": (ctypes.c_int, [_P, ctypes.c_longlong, _L, _I, _I, _D, _I]),
@@ -248,6 +249,10 @@ class Lattice:
         out = np.zeros((int(nbins), 12))
         self._check(self.L.lbm_pipe_profiles(self.h, int(flags), int(nbins), _dp(out)))
         return out
+
+    def set_mrt_rates(self, s_e, s_eps, s_q, s_pi, s_m):
+        """Non-shear MRT rates by group (e, eps, q, pi, m); shear stays 1/tau."""
+        self._check(self.L.lbm_set_mrt_rates(self.h, float(s_e), float(s_eps), float(s_q), float(s_pi), float(s_m)))
 
     def tke_budget(self, nbins, flags=0):
         """Component-wise TKE budget of the pipe, shape (nbins, 14): count, then

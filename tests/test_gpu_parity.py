@@ -54,6 +54,41 @@ def test_periodic_random_populations_f64(lbm, rates):
     assert rel(rg, ro) < 1e-12 and rel(ug, uo) < 1e-12
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_custom_mrt_rates(lbm, storage, tol):
+    """Non-shear MRT rates set on a running context (the bulk-viscosity knob,
+    lbm_set_mrt_rates): an SRT context switches to the MRT collision with
+    the new energy, energy-square, flux, pi and m rates. Random departures
+    plus a standing density wave on ragged rows, with a body force."""
+    shape = (6, 10, 37)
+    nz, ny, nx = shape
+    N = nz * ny * nx
+    f = workloads.random_populations(N, seed=5, lo=0.052, hi=0.0575)
+    wave = 1.0 + 1e-3 * np.cos(2 * np.pi * np.arange(nx) / nx)
+    f = f * np.broadcast_to(wave, shape).reshape(1, N)
+    g, o = pair(lbm, shape, 0.7, force=(1e-5, -2e-6, 0),
+                storage=lbm.F64 if storage == "f64" else lbm.F32)
+    g.set_populations(f)
+    o.set_populations(f)
+    g.step(5)
+    o.step(5)
+    rates = (0.5, 1.3, 1.1, 1.5, 1.9)
+    g.set_mrt_rates(*rates)
+    o.set_group_rates(*rates)
+    g.step(40)
+    o.step(40)
+    rg, ug = g.macro()
+    ro, uo = o.macro()
+    assert rel(ug, uo) < tol
+    assert rel(rg - 1.0, ro - 1.0) < 10 * tol
+    if storage == "f64":
+        assert rel(g.populations(), o.populations()) < tol
+    with pytest.raises(lbm.LbmError):
+        g.set_mrt_rates(2.5, 1.3, 1.1, 1.5, 1.9)
+    with pytest.raises(lbm.LbmError):
+        g.set_mrt_rates(0.5, 1.3, 0.0, 1.5, 1.9)
+
+
 @pytest.mark.parametrize("rates,tau", [(oracle.RATES_SRT, 0.6), (oracle.RATES_DHUMIERES, 0.51)])
 def test_periodic_hit_f32_200_steps(lbm, rates, tau):
     n = 32
