@@ -14,8 +14,10 @@ equilibrium moments are those of the equilibrium distribution. Readings
   f_eq = w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u);
 - body force by Guo et al. (2002): u = (sum f c + F/2) / rho and the source
   (1 - 1/(2 tau)) w [3 (c - u) + 9 (c.u) c] . F;
-- collision f* = f - (f - f_eq) / tau + source, then pull streaming
-  f(x, t+1) = f*(x - c, t) with periodic wrap.
+- a step is pull streaming f(x) <- f*(x - c) with periodic wrap, then the
+  collision f* = f - (f - f_eq) / tau + source; the stored state is the
+  post-collision one (as for D3Q19), whose velocity is
+  u = (sum f* c - F/2) / rho.
 
 Populations have shape (27, nz, ny, nx), x fastest.
 """
@@ -78,11 +80,16 @@ def stream(f):
 
 
 def step(f, tau, F=(0.0, 0.0, 0.0), n=1):
+    """n steps of the post-collision state: stream, then collide."""
     for _ in range(n):
-        f = stream(collide(f, tau, F))
+        f = collide(stream(f), tau, F)
     return f
 
 
 def macro(f, F=(0.0, 0.0, 0.0)):
-    """rho and u of a post-collision-then-streamed state (the forced velocity)."""
-    return moments(f, F)
+    """rho and u of a post-collision state: the collision added F to the
+    momentum rho u - F/2 of its input, so u = (sum f c - F/2) / rho."""
+    rho = np.sum(f, axis=0)
+    j = np.tensordot(C.T.astype(np.float64), f, axes=(1, 0))
+    u = (j - 0.5 * np.asarray(F, dtype=np.float64).reshape((3,) + (1,) * np.ndim(rho))) / rho
+    return rho, u

@@ -8,7 +8,8 @@ compute:
   all index tuples) and sum w c_x^2 c_y^2 c_z^2 = 1/27;
 - the equilibrium's moments: rho, rho u and rho (u u + I/3), exactly;
 - a step conserves mass exactly and adds F to the momentum of every cell
-  (Guo forcing: the half-force shift and the source add up to F);
+  (Guo forcing: the half-force shift and the source add up to F), and a
+  fluid at rest pushed for n steps moves at (n - 1/2) F;
 - a Taylor-Green vortex decays at 2 nu k^2 with nu = (tau - 1/2)/3, within
   1 % at N = 32, and the error falls about 4x from N = 16 to N = 32;
 - a step commutes with a cubic rotation of the box (x -> y -> z -> x);
@@ -70,6 +71,12 @@ def test_step_conserves_mass_and_adds_the_force():
     assert m1 == pytest.approx(m0, rel=1e-14)
     N = np.prod(shape)
     assert p1 == pytest.approx(p0 + 3 * N * F, abs=1e-12)
+    # a uniform fluid at rest pushed for n steps: the stored (post-collision)
+    # momentum is n F and the velocity of the last collision (n - 1/2) F
+    h = q27.feq(np.ones((2, 2, 2)), np.zeros((3, 2, 2, 2)))
+    rho, u = q27.macro(q27.step(h, 0.7, F, n=4), F)
+    assert np.max(np.abs(u - 3.5 * F.reshape(3, 1, 1, 1))) < 1e-15
+    assert np.max(np.abs(rho - 1.0)) < 1e-15
 
 
 def tgv_rate(n, tau=0.8, u0=1e-3, steps=120, skip=20):
