@@ -80,6 +80,13 @@ typedef struct {
     long long max_links;     /* IBB link capacity (0: derived from the grid and max_particles) */
     long long max_markers;   /* IBM marker capacity (0: derived) */
     long long max_sites;     /* boundary / support cell capacity (0: derived) */
+    int lattice;             /* velocity set: 0 or 19 D3Q19 (every path); 27 D3Q27, the set of the
+                                paper's pipe solver (Sec. 2.1): periodic box (LBM_BC_NONE), BGK
+                                (LBM_RATES_SRT), FP64 or FP32 storage; walls and the MRT rates answer
+                                LBM_EUNSUPPORTED. Populations in and out (lbm_set_populations,
+                                LBM_FIELD_POPS) then hold 27 planes: rest, 6 faces, 12 edges, 8
+                                corners, each group in lexicographic order of (c_x, c_y, c_z) over
+                                {-1, 0, 1}^3, c_x slowest. */
 } lbm_grid;
 
 /* Bytes of device workspace lbm_create needs for this grid. 0 on bad input. */

@@ -65,6 +65,7 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
 }
 
 cudaError_t launch_macro(Ctx &c, int /*mask_mode*/) {
+    if (c.q == 27) return launch_q27_macro(c);
     count_launch(c, G_STATS);
     const unsigned nb = (unsigned)((c.N + 255) / 256);
     const int ibb = c.armed_bc == LBM_BC_IBB;

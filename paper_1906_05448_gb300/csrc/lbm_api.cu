@@ -63,6 +63,10 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     if (g->storage < LBM_F64 || g->storage > LBM_BF16S) return false;
     if (g->rates != LBM_RATES_SRT && g->rates != LBM_RATES_DHUMIERES) return false;
     if (g->max_particles < 0 || g->max_links < 0 || g->max_markers < 0 || g->max_sites < 0) return false;
+    if (g->lattice != 0 && g->lattice != 19 && g->lattice != 27) return false;
+    // D3Q27: periodic box, BGK, FP64 or FP32 storage
+    if (g->lattice == 27 && (g->rates != LBM_RATES_SRT || (g->storage != LBM_F64 && g->storage != LBM_F32)))
+        return false;
     const long long N = (long long)g->nx * g->ny * g->nz;
     if (N >= (1LL << 31) - 4096) return false;
     P.N = N;
@@ -76,8 +80,9 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     const size_t n = (size_t)N, ms = (size_t)P.max_sites, ml = (size_t)P.max_links, mm = (size_t)P.max_markers;
     const size_t np = (size_t)(P.max_np > 0 ? P.max_np : 1);
     Layout L;
-    P.fA = L.take(19 * n * sb);
-    P.fB = L.take(19 * n * sb);
+    const size_t nq = g->lattice == 27 ? 27 : 19;
+    P.fA = L.take(nq * n * sb);
+    P.fB = L.take(nq * n * sb);
     P.flags = L.take(n + 8);
     P.owner = L.take(4 * n);
     P.aux = L.take(4 * n);
@@ -549,6 +554,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     for (int d = 0; d < 3; d++) c.F[d] = force ? force[d] : 0.0;
     c.storage = grid->storage;
     c.rates = grid->rates;
+    c.q = grid->lattice == 27 ? 27 : 19;
     set_rates(c);
     c.stream = (cudaStream_t)cuda_stream;
     c.ws = (char *)dev_workspace;
@@ -662,8 +668,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     if ((e = cudaEventCreateWithFlags(&c.ev_status, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "event");
     const size_t sb = storage_bytes(c.storage);
     // rest state: g = f - w = 0 in every storage format
-    if ((e = cudaMemsetAsync(c.fA, 0, 19 * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
-    if ((e = cudaMemsetAsync(c.fB, 0, 19 * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.fA, 0, c.q * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.fB, 0, c.q * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.flags, 0, (size_t)c.N + 8, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.aux, 0xff, 4 * (size_t)c.N, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.d_counts, 0, 32, c.stream)) != cudaSuccess) return bad(e, "memset");
@@ -685,7 +691,8 @@ lbm_status lbm_init_velocity(lbm_ctx *h, const double *u_host, double rho0) {
     if (c.broken || c.armed_bc >= 0) return fail(c, LBM_ESTATE, "init_velocity only before the first step");
     c.bvals_valid = 0;
     CK(cudaMemcpyAsync(c.u_f, u_host, sizeof(double) * 3 * c.N, cudaMemcpyHostToDevice, c.stream));
-    CK(launch_init_equilibrium(c, c.u_f, rho0));
+    if (c.q == 27) CK(launch_q27_init(c, c.u_f, rho0));
+    else CK(launch_init_equilibrium(c, c.u_f, rho0));
     CK(cudaStreamSynchronize(c.stream));
     return LBM_OK;
 }
@@ -695,9 +702,10 @@ lbm_status lbm_set_populations(lbm_ctx *h, const double *f_host) {
     if (!f_host) return fail(c, LBM_EINVAL, "null populations");
     if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
     c.bvals_valid = 0;
-    for (int i = 0; i < 19; i++) {
+    for (int i = 0; i < c.q; i++) {
         CK(cudaMemcpyAsync(c.rho_f, f_host + (size_t)i * c.N, sizeof(double) * c.N, cudaMemcpyHostToDevice, c.stream));
-        CK(plane_copy(c, i, false));
+        if (c.q == 27) CK(q27_plane_copy(c, i, false));
+        else CK(plane_copy(c, i, false));
     }
     CK(cudaStreamSynchronize(c.stream));
     return LBM_OK;
@@ -705,6 +713,7 @@ lbm_status lbm_set_populations(lbm_ctx *h, const double *f_host) {
 
 lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     CTX_CHECK(h);
+    if (c.q != 19) return fail(c, LBM_EUNSUPPORTED, "walls need the D3Q19 lattice");
     if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe) return fail(c, LBM_ESTATE, "geometry already set");
     if (!(radius > 1.0) || radius > 0.5 * (c.nx < c.ny ? c.nx : c.ny)) return fail(c, LBM_EINVAL, "bad pipe radius");
     c.has_pipe = 1;
@@ -836,6 +845,7 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
 lbm_status lbm_add_spheres(lbm_ctx *h, int n, const double *xyz, const double *radius, double density_ratio,
                            const double *vel, const double *omega, int fixed) {
     CTX_CHECK(h);
+    if (c.q != 19) return fail(c, LBM_EUNSUPPORTED, "walls need the D3Q19 lattice");
     if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe) return fail(c, LBM_ESTATE, "geometry already set");
     if (n <= 0 || !xyz || !radius || !(density_ratio > 0)) return fail(c, LBM_EINVAL, "bad sphere arguments");
     if (n > c.max_np) return fail(c, LBM_ENOMEM, "%d spheres exceed max_particles %d", n, c.max_np);
@@ -885,11 +895,23 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
     lbm_status s = check_status(c, false);
     if (s != LBM_OK) return s;
     if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
+    // refused before the treatment is fixed, so a refused call changes nothing
+    if (c.q == 27 && bc != LBM_BC_NONE) return fail(c, LBM_EUNSUPPORTED, "D3Q27 runs the periodic box only");
     if (c.armed_bc < 0) {
         s = arm(c, bc);
         if (s != LBM_OK) return s;
     } else if (c.armed_bc != bc) {
         return fail(c, LBM_ESTATE, "boundary treatment fixed to %d by the first step", c.armed_bc);
+    }
+    if (c.q == 27) {  // periodic box only (checked above)
+        for (int n = 0; n < nsteps; n++) {
+            cudaEvent_t t0 = pmark(c);
+            CK(launch_q27_step(c));
+            pspan(c, G_BULK, t0, pmark(c));
+            std::swap(c.fA, c.fB);
+            c.step++;
+        }
+        return enqueue_status(c);
     }
     const bool ibm = bc == LBM_BC_IBM_U || bc == LBM_BC_IBM_B;
     const bool moving = c.np > 0 && !c.fixed;
@@ -990,6 +1012,7 @@ lbm_status lbm_pipe_profiles(lbm_ctx *h, int flags, int nbins, double *out) {
 
 lbm_status lbm_set_mrt_rates(lbm_ctx *h, double s_e, double s_eps, double s_q, double s_pi, double s_m) {
     CTX_CHECK(h);
+    if (c.q != 19) return fail(c, LBM_EUNSUPPORTED, "the MRT collision is built for D3Q19");
     const double v[5] = {s_e, s_eps, s_q, s_pi, s_m};
     for (double x : v)
         if (!(x > 0.0 && x < 2.0)) return fail(c, LBM_EINVAL, "relaxation rates must lie in (0, 2)");
@@ -1038,9 +1061,10 @@ lbm_status lbm_get_field(lbm_ctx *h, int which, void *dst, size_t bytes) {
         break;
     }
     case LBM_FIELD_POPS: {
-        if (bytes < 19 * N * sizeof(double)) return fail(c, LBM_EINVAL, "destination too small");
-        for (int i = 0; i < 19; i++) {
-            CK(plane_copy(c, i, true));
+        if (bytes < (size_t)c.q * N * sizeof(double)) return fail(c, LBM_EINVAL, "destination too small");
+        for (int i = 0; i < c.q; i++) {
+            if (c.q == 27) CK(q27_plane_copy(c, i, true));
+            else CK(plane_copy(c, i, true));
             CK(cudaMemcpyAsync((double *)dst + i * N, c.rho_f, N * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         }
         break;

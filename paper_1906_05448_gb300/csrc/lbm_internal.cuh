@@ -20,6 +20,7 @@ struct Ctx {
     long long N;
     double tau, F[3];
     int storage, rates;
+    int q = 19;  // velocity set: 19 (every path) or 27 (periodic box, BGK)
     Rates rt;
     cudaStream_t stream;
     char *ws;
@@ -171,6 +172,11 @@ cudaError_t run_spectrum(Ctx &c, int flags, int nbins, double *E, double *D);
 cudaError_t run_pipe_profiles(Ctx &c, int flags, int nbins, double *out);
 size_t pipe_profile_scratch_bytes(int nbins);
 cudaError_t run_tke_budget(Ctx &c, int flags, int nbins, double *out);
+// D3Q27 periodic box (q27.cu)
+cudaError_t launch_q27_step(Ctx &c);
+cudaError_t launch_q27_init(Ctx &c, const double *u_dev, double rho0);
+cudaError_t q27_plane_copy(Ctx &c, int i, bool to_f64);
+cudaError_t launch_q27_macro(Ctx &c);
 size_t tke_budget_scratch_bytes(int nbins);
 size_t spectrum_scratch_bytes(long long N, int nbins);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);

@@ -43,7 +43,7 @@ GROUPS = ["bulk", "ibb_boundary", "ibm_passes", "ibm_collide", "particles", "geo
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("storage", ctypes.c_int),
                 ("rates", ctypes.c_int), ("max_particles", ctypes.c_int), ("max_links", ctypes.c_longlong),
-                ("max_markers", ctypes.c_longlong), ("max_sites", ctypes.c_longlong)]
+                ("max_markers", ctypes.c_longlong), ("max_sites", ctypes.c_longlong), ("lattice", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -155,10 +155,10 @@ def _c64(a):
 
 
 def make_grid(nx, ny, nz, storage=F32, rates=RATES_SRT, max_particles=0, max_links=0, max_markers=0,
-              max_sites=0) -> Grid:
+              max_sites=0, lattice=19) -> Grid:
     if isinstance(storage, str):
         storage = STORAGE[storage]
-    return Grid(nx, ny, nz, storage, rates, max_particles, max_links, max_markers, max_sites)
+    return Grid(nx, ny, nz, storage, rates, max_particles, max_links, max_markers, max_sites, lattice)
 
 
 def workspace_bytes(grid: Grid) -> int:
@@ -169,13 +169,14 @@ class Lattice:
     """One simulation context (lbm_create ... lbm_destroy)."""
 
     def __init__(self, nx, ny, nz, tau, force=(0.0, 0.0, 0.0), storage=F32, rates=RATES_SRT,
-                 max_particles=0, max_links=0, max_markers=0, max_sites=0, device=None, stream=None):
+                 max_particles=0, max_links=0, max_markers=0, max_sites=0, device=None, stream=None, lattice=19):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the library has no CPU path")
         self.L = load()
-        self.grid = make_grid(nx, ny, nz, storage, rates, max_particles, max_links, max_markers, max_sites)
+        self.grid = make_grid(nx, ny, nz, storage, rates, max_particles, max_links, max_markers, max_sites, lattice)
+        self.q = 27 if lattice == 27 else 19
         self.N = nx * ny * nz
         self.shape = (nz, ny, nx)
         nbytes = workspace_bytes(self.grid)
@@ -215,7 +216,7 @@ class Lattice:
         self._check(self.L.lbm_init_velocity(self.h, _dp(u), float(rho0)))
 
     def set_populations(self, f):
-        f = _c64(f).reshape(19 * self.N)
+        f = _c64(f).reshape(self.q * self.N)
         self._check(self.L.lbm_set_populations(self.h, _dp(f)))
 
     def set_pipe(self, radius):
@@ -277,7 +278,7 @@ class Lattice:
         return rho, u
 
     def populations(self):
-        return self._field(FIELD_POPS, 19 * self.N, np.float64).reshape(19, self.N)
+        return self._field(FIELD_POPS, self.q * self.N, np.float64).reshape(self.q, self.N)
 
     def flags(self):
         return self._field(FIELD_FLAGS, self.N, np.uint8)

@@ -48,6 +48,21 @@ def test_workspace_bytes_host_only(lib):
     assert lbm.workspace_bytes(lbm.make_grid(16, 16, 16, storage=9)) == 0
 
 
+def test_d3q27_workspace_rules(lib):
+    from paper_1906_05448_gb300 import lbm
+    n = (40, 24, 16)
+    N = n[0] * n[1] * n[2]
+    b19 = lbm.workspace_bytes(lbm.make_grid(*n, storage="f32"))
+    b27 = lbm.workspace_bytes(lbm.make_grid(*n, storage="f32", lattice=27))
+    assert b27 - b19 == pytest.approx(2 * 8 * 4 * N, abs=4096)  # two buffers of 8 more FP32 planes
+    assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f64", lattice=27)) > 0
+    # D3Q27 runs BGK on FP64 or FP32 storage only; other velocity sets are refused
+    assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f16s", lattice=27)) == 0
+    assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f32", rates=lbm.RATES_DHUMIERES, lattice=27)) == 0
+    assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f32", lattice=15)) == 0
+    assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f32", lattice=0)) == b19
+
+
 def test_create_rejects_bad_arguments_without_gpu(lib):
     from paper_1906_05448_gb300 import lbm
     g = lbm.make_grid(16, 16, 16)
