@@ -93,3 +93,72 @@ def macro(f, F=(0.0, 0.0, 0.0)):
     j = np.tensordot(C.T.astype(np.float64), f, axes=(1, 0))
     u = (j - 0.5 * np.asarray(F, dtype=np.float64).reshape((3,) + (1,) * np.ndim(rho))) / rho
     return rho, u
+
+
+# ---------------------------------------------------------------- pipe wall --
+# The pipe of the paper's runs (Sec. 2.1) with the linear interpolated
+# bounce-back, read as for D3Q19: a cell is solid iff
+# (x - c_x)^2 + (y - c_y)^2 >= R^2 with the axis at ((nx-1)/2, (ny-1)/2)
+# along z; a link (x_f, i) joins a fluid cell to a solid x_f + c_i, and the
+# wall sits at x_f + q c_i with q the root in (0, 1] of
+# |d + q c_perp|^2 = R^2 (d = (x - c_x, y - c_y), c_perp = (c_x, c_y)).
+# The unknown f_ibar(x_f) after streaming is, with post-collision values f*
+# and a wall at rest (Bouzidi et al. 2001, linear):
+#   q < 1/2: 2q f*_i(x_f) + (1 - 2q) f*_i(x_f - c_i), if x_f - c_i is fluid,
+#            else f*_i(x_f) (halfway bounce-back);
+#   q >= 1/2: f*_i(x_f) / (2q) + (2q - 1) / (2q) f*_ibar(x_f).
+
+OPP = np.array([int(np.flatnonzero((C == -C[i]).all(axis=1))[0]) for i in range(Q)])
+
+
+def pipe_solid(nx, ny, nz, R):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    dx, dy = x - 0.5 * (nx - 1), y - 0.5 * (ny - 1)
+    return dx * dx + dy * dy >= R * R
+
+
+def pipe_links(solid, R):
+    """Per direction i: (mask of fluid cells whose neighbour x + c_i is solid,
+    q at those cells, mask of those whose x - c_i is fluid)."""
+    nz, ny, nx = solid.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    dx, dy = x - 0.5 * (nx - 1), y - 0.5 * (ny - 1)
+    out = []
+    for i in range(Q):
+        cx, cy, cz = (int(v) for v in C[i])
+        nb_solid = np.roll(solid, shift=(-cz, -cy, -cx), axis=(0, 1, 2))   # solid[x + c_i]
+        up_fluid = ~np.roll(solid, shift=(cz, cy, cx), axis=(0, 1, 2))     # fluid at x - c_i
+        m = ~solid & nb_solid
+        a = float(cx * cx + cy * cy)
+        q = np.zeros(solid.shape)
+        if a > 0 and np.any(m):
+            b = cx * dx[m] + cy * dy[m]
+            c0 = dx[m] ** 2 + dy[m] ** 2 - R * R
+            q[m] = (-b + np.sqrt(b * b - a * c0)) / a
+        out.append((m, q, up_fluid))
+    return out
+
+
+def step_pipe(f, solid, links, tau, F=(0.0, 0.0, 0.0)):
+    """One step of the post-collision state with the pipe wall: pull
+    streaming, the bounced populations at the wall links, then the collision
+    of the fluid cells (the body force acts on fluid cells; solid cells keep
+    their values and are never read)."""
+    g = stream(f)
+    for i, (m, q, up) in enumerate(links):
+        if not np.any(m):
+            continue
+        j = OPP[i]
+        lo = m & (q < 0.5)
+        hi = m & (q >= 0.5)
+        v = g[j].copy()
+        lin = lo & up
+        v[lin] = 2 * q[lin] * f[i][lin] + (1 - 2 * q[lin]) * g[i][lin]
+        half = lo & ~up
+        v[half] = f[i][half]
+        v[hi] = f[i][hi] / (2 * q[hi]) + (2 * q[hi] - 1) / (2 * q[hi]) * f[j][hi]
+        g[j] = v
+    fluid = ~solid
+    out = f.copy()
+    out[:, fluid] = collide(g[:, fluid], tau, F)
+    return out
