@@ -263,6 +263,31 @@ def budget_report(lbm, torch, nbins=64, steps=20, reps=5):
             "finite": bool(np.all(np.isfinite(B)))}
 
 
+def q27_report(lbm, torch, n=256, steps=50, warmup=5):
+    """D3Q27 periodic box (the velocity set of the paper's pipe solver), FP32,
+    BGK with a body force, on the HIT field: time per step from CUDA events
+    on the library's stream, MLUPS, and the sweep's algorithmic bandwidth
+    (27 x 4 B read and 27 x 4 B written per cell)."""
+    u = workloads.hit_velocity(n, seed=0, k_peak=8.0, u_rms=0.03, dtype=np.float64)
+    L = lbm.Lattice(n, n, n, 0.6, force=(1e-6, 0, 0), storage=lbm.F32, lattice=27)
+    L.init_velocity(u)
+    L.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(L.stream)
+    L.step(steps)
+    e1.record(L.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    _, v = L.macro()
+    finite = bool(np.all(np.isfinite(v)))
+    L.close()
+    cells = n ** 3
+    return {"grid": f"{n}^3", "storage": "f32", "steps": steps, "ms_per_step": round(ms, 4),
+            "mlups": round(cells / (ms * 1e-3) / 1e6, 1),
+            "algorithmic_gbs": round(2 * 27 * 4 * cells / (ms * 1e-3) / 1e9, 1), "finite": finite}
+
+
 def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
     """Learned closure on the particle-laden 256^3 box (IBM-B): paired
     IBB/IBM-B runs of seeds 0-7 give up to 1e6 training samples, seeds 8-9
@@ -491,6 +516,7 @@ def main():
     closure_res = None
     spectrum_res = None
     budget_res = None
+    q27_res = None
     if not args.no_variants and rank == 0:
         precision = precision_report(lbm, torch)
         closure_res = closure_report(lbm, torch)
@@ -499,6 +525,10 @@ def main():
             budget_res = budget_report(lbm, torch)
         except Exception as ex:  # a diagnostic's failure must not lose the line
             budget_res = {"error": str(ex)[:200]}
+        try:
+            q27_res = q27_report(lbm, torch)
+        except Exception as ex:
+            q27_res = {"error": str(ex)[:200]}
 
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -544,6 +574,7 @@ def main():
             "closure": closure_res,
             "spectrum": spectrum_res,
             "tke_budget": budget_res,
+            "d3q27": q27_res,
         }
         print(json.dumps(line))
     if dist:
