@@ -26,7 +26,8 @@ _lib = None
 
 BC_NONE, BC_IBB, BC_IBM_U, BC_IBM_B = 0, 1, 2, 3
 RATES_SRT, RATES_DHUMIERES = 0, 1
-SCHEME_QUAD, SCHEME_LINEAR, SCHEME_HALFWAY = 0, 1, 2
+SCHEME_QUAD, SCHEME_LINEAR, SCHEME_SINGLE, SCHEME_HALFWAY = 0, 1, 2, 3
+CHAIN_SPHERE, CHAIN_PIPE, CHAIN_SINGLE, CHAIN_HALFWAY = 0, 1, 2, 3
 STATS_UNMASK, STATS_BINS = 1, 4
 NBINS = 40
 
@@ -100,6 +101,7 @@ def lib():
                 "orc_set_populations": (None, [_P, _D]),
                 "orc_get_populations": (None, [_P, _D]),
                 "orc_set_pipe": (None, [_P, ctypes.c_double]),
+                "orc_set_channel": (None, [_P] + [ctypes.c_double] * 4 + [ctypes.c_int]),
                 "orc_add_spheres": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, ctypes.c_int]),
                 "orc_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
                 "orc_macro": (None, [_P, _D, _D]),
@@ -240,6 +242,11 @@ class Sim:
 
     def set_pipe(self, radius):
         self.L.orc_set_pipe(self.h, float(radius))
+
+    def set_channel(self, y_lo, y_hi, u_lo=0.0, u_hi=0.0, chain=CHAIN_SPHERE):
+        """Plane walls at y = y_lo and y = y_hi moving along x (test geometry
+        of the bounce-back schemes; chain selects the schemes of the links)."""
+        self.L.orc_set_channel(self.h, float(y_lo), float(y_hi), float(u_lo), float(u_hi), int(chain))
 
     def add_spheres(self, X, R, density_ratio=1.0, U=None, W=None, fixed=False):
         X = _c64(X).reshape(-1, 3)

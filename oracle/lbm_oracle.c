@@ -234,6 +234,9 @@ struct orc_sim {
     /* pipe */
     int has_pipe;
     double pipe_R, pipe_cx, pipe_cy;
+    /* plane channel (test geometry of the bounce-back schemes) */
+    int has_chan, chan_chain;
+    double chan_ylo, chan_yhi, chan_u[2];
     /* particles (FP64) */
     int np, fixed;
     double dens;
@@ -377,6 +380,14 @@ static void compute_solid(orc_sim *S)
             if (outside_pipe(S, x, y)) S->solid[c] = 1;
         }
     }
+    if (S->has_chan) {
+        for (long long c = 0; c < S->N; c++) {
+            int x, y, z;
+            ccoord(S, c, &x, &y, &z);
+            if ((double)y <= S->chan_ylo) { S->solid[c] = 1; S->owner[c] = -2; }
+            else if ((double)y >= S->chan_yhi) { S->solid[c] = 1; S->owner[c] = -3; }
+        }
+    }
     for (int p = 0; p < S->np; p++) {
         int r = (int)ceil(S->R[p]) + 1;
         int bx = (int)floor(S->X[3 * p]), by = (int)floor(S->X[3 * p + 1]), bz = (int)floor(S->X[3 * p + 2]);
@@ -426,6 +437,17 @@ static double link_q_pipe(const orc_sim *S, int x, int y, int i)
     return t;
 }
 
+/* Channel wall (owner -2: lower plane y = y_lo, -3: upper plane y = y_hi)
+ * along a link from x_f: t = (y_w - y_f) / c_y. */
+static double link_q_channel(const orc_sim *S, int y, int i, int pid)
+{
+    double yw = pid == -2 ? S->chan_ylo : S->chan_yhi;
+    double t = (yw - (double)y) / (double)CV[i][1];
+    if (t > 1.0) t = 1.0;
+    if (t < 0.0) t = 0.0;
+    return t;
+}
+
 /* Boundary links: every (x_f, i) with x_f fluid and x_f + c_i solid. The
  * scheme follows the fallback chain of Sec. 3.1 (quadratic, then linear, then
  * single-node bounce-back) on spheres; the pipe wall uses the linear scheme
@@ -446,16 +468,19 @@ static void build_links(orc_sim *S)
             double q;
             int pid = S->owner[b];
             if (pid >= 0) q = link_q_sphere(S, pid, x, y, z, i);
+            else if (pid <= -2) q = link_q_channel(S, y, i, pid);
             else q = link_q_pipe(S, x, y, i);
             int f1 = !S->solid[cidx(S, x - CV[i][0], y - CV[i][1], z - CV[i][2])];
             int f2 = !S->solid[cidx(S, x - 2 * CV[i][0], y - 2 * CV[i][1], z - 2 * CV[i][2])];
-            int scheme;
-            if (pid >= 0) {
-                if (q < 0.5) scheme = (f1 && f2) ? ORC_SCHEME_QUAD : (f1 ? ORC_SCHEME_LINEAR : ORC_SCHEME_HALFWAY);
+            int scheme, chain = pid >= 0 ? 0 : (pid <= -2 ? S->chan_chain : 1);
+            if (chain == 0) {
+                if (q < 0.5) scheme = (f1 && f2) ? ORC_SCHEME_QUAD : (f1 ? ORC_SCHEME_LINEAR : ORC_SCHEME_SINGLE);
                 else scheme = f1 ? ORC_SCHEME_QUAD : ORC_SCHEME_LINEAR;
-            } else {
-                if (q < 0.5) scheme = f1 ? ORC_SCHEME_LINEAR : ORC_SCHEME_HALFWAY;
+            } else if (chain == 1) {
+                if (q < 0.5) scheme = f1 ? ORC_SCHEME_LINEAR : ORC_SCHEME_SINGLE;
                 else scheme = ORC_SCHEME_LINEAR;
+            } else {
+                scheme = chain == 2 ? ORC_SCHEME_SINGLE : ORC_SCHEME_HALFWAY;
             }
             if (S->nlinks == S->cap_links) {
                 S->cap_links = S->cap_links ? 2 * S->cap_links : 1024;
@@ -466,6 +491,23 @@ static void build_links(orc_sim *S)
             L->cell = c; L->dir = i; L->scheme = scheme; L->pid = pid; L->q = q;
         }
     }
+}
+
+/* Plane channel, a test geometry for the bounce-back schemes: walls normal
+ * to y at y = y_lo and y = y_hi (cells with y <= y_lo or y >= y_hi are
+ * solid), moving along x at u_lo and u_hi. chain picks the schemes of its
+ * links: 0 the sphere chain (quadratic, linear, single-node), 1 the pipe
+ * chain (linear, single-node), 2 single-node only, 3 halfway only. */
+void orc_set_channel(orc_sim *S, double y_lo, double y_hi, double u_lo, double u_hi, int chain)
+{
+    S->has_chan = 1;
+    S->chan_ylo = y_lo;
+    S->chan_yhi = y_hi;
+    S->chan_u[0] = u_lo;
+    S->chan_u[1] = u_hi;
+    S->chan_chain = chain;
+    compute_solid(S);
+    build_links(S);
 }
 
 void orc_set_pipe(orc_sim *S, double R)
@@ -618,6 +660,7 @@ int orc_add_spheres(orc_sim *S, int n, const double *X, const double *R, double 
 
 static void wall_velocity(const orc_sim *S, int p, const double *xw, double *uw)
 {
+    if (p <= -2) { uw[0] = S->chan_u[p == -2 ? 0 : 1]; uw[1] = uw[2] = 0.0; return; }
     if (p < 0) { uw[0] = uw[1] = uw[2] = 0.0; return; }
     double r[3] = {mimg(xw[0] - S->X[3 * p], S->nx), mimg(xw[1] - S->X[3 * p + 1], S->ny),
                    mimg(xw[2] - S->X[3 * p + 2], S->nz)};
@@ -626,10 +669,58 @@ static void wall_velocity(const orc_sim *S, int p, const double *xw, double *uw)
     for (int d = 0; d < 3; d++) uw[d] = S->U[3 * p + d] + wr[d];
 }
 
+/* Single-node bounce-back (the last fallback of Sec. 3.1, after Zhao & Yong
+ * 2017; the formula is this build's reading, see single-node below): the
+ * collision at x_f removed the departure d = M^-1 S (m - m_eq) from its
+ * pre-collision populations. It is recovered here from the post-collision
+ * populations alone, moment by moment:
+ *   m~ = m - S (m - m_eq) + (I - S/2) M F_i
+ *   =>  S (m - m_eq) = S (I - S)^-1 (m~ - m_eq - (I - S/2) M F_i),
+ * with rho = sum f~ and u = (sum f~ c - F/2) / rho (the Guo velocity of that
+ * collision). A moment with rate 0 (conserved) or exactly 1 contributes
+ * nothing (a rate of 1 leaves no trace of its departure in f~). Returns
+ * d_i + d_ibar. */
+static double single_node_pair(const orc_sim *S, const double *A, long long c0, int i, int ib)
+{
+    double f[Q], r = 0.0, j[3] = {0, 0, 0}, F[3], u[3], feq[Q], Fi[Q], a[Q];
+    for (int k = 0; k < Q; k++) {
+        f[k] = A[k * S->N + c0];
+        r += f[k];
+        for (int d = 0; d < 3; d++) j[d] += f[k] * CV[k][d];
+    }
+    for (int d = 0; d < 3; d++) {
+        F[d] = fext_at(S, c0, d);
+        u[d] = (j[d] - 0.5 * F[d]) / r;
+    }
+    orc_feq(r, u, feq);
+    guo_source(u, F, Fi);
+    for (int k = 0; k < Q; k++) {
+        double mt = 0.0, me = 0.0, mF = 0.0, sk = S->s[k];
+        for (int m = 0; m < Q; m++) {
+            mt += S->M[k][m] * f[m];
+            me += S->M[k][m] * feq[m];
+            mF += S->M[k][m] * Fi[m];
+        }
+        a[k] = (sk == 0.0 || sk == 1.0) ? 0.0 : sk / (1.0 - sk) * (mt - me - (1.0 - 0.5 * sk) * mF);
+    }
+    double di = 0.0, db = 0.0;
+    for (int k = 0; k < Q; k++) {
+        di += S->Mi[i][k] * a[k];
+        db += S->Mi[ib][k] * a[k];
+    }
+    return di + db;
+}
+
 /* Population leaving the wall into x_f along -c_i at t+1 (Bouzidi et al.
- * 2001 quadratic / linear interpolation, single-node bounce-back as the last
- * fallback), from post-collision values at t. The moving-wall term
- * D = 6 w_i rho_w (c_ibar . u_w), rho_w = 1, rides on the f_i(x_f) weight. */
+ * 2001 quadratic / linear interpolation, the single-node scheme as the last
+ * fallback; plain halfway bounce-back only for the channel tests), from
+ * post-collision values at t. The moving-wall term D = 6 w_i rho_w
+ * (c_ibar . u_w), rho_w = 1, rides on the f_i(x_f) weight. Single node:
+ * halfway bounce-back plus (1 - 2q)/2 times the symmetric part d_i + d_ibar
+ * of the departure its collision removed at x_f; for a steady flow whose
+ * velocity is linear in space that departure is minus the change of f_eq
+ * along c_i per unit length, so the value is exact there at any q, and at
+ * q = 1/2 it is halfway bounce-back. */
 static double ibb_value(const orc_sim *S, const double *A, const link_t *L)
 {
     int i = L->dir, ib = OPP(i);
@@ -652,6 +743,8 @@ static double ibb_value(const orc_sim *S, const double *A, const link_t *L)
     case ORC_SCHEME_LINEAR:
         if (q < 0.5) return 2.0 * q * fi0 + (1.0 - 2.0 * q) * fi1 + D;
         return fi0 / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fb0 + D / (2.0 * q);
+    case ORC_SCHEME_SINGLE:
+        return fi0 + D + 0.5 * (1.0 - 2.0 * q) * single_node_pair(S, A, c0, i, ib);
     default:
         return fi0 + D;
     }

@@ -23,7 +23,7 @@ typedef struct orc_sim orc_sim;
 
 enum { ORC_BC_NONE = 0, ORC_BC_IBB = 1, ORC_BC_IBM_U = 2, ORC_BC_IBM_B = 3 };
 enum { ORC_RATES_SRT = 0, ORC_RATES_DHUMIERES = 1 };
-enum { ORC_SCHEME_QUAD = 0, ORC_SCHEME_LINEAR = 1, ORC_SCHEME_HALFWAY = 2 };
+enum { ORC_SCHEME_QUAD = 0, ORC_SCHEME_LINEAR = 1, ORC_SCHEME_SINGLE = 2, ORC_SCHEME_HALFWAY = 3 };
 enum { ORC_STATS_UNMASK = 1, ORC_STATS_BINS = 4 };
 
 #define ORC_NBINS 40
@@ -67,6 +67,7 @@ void  orc_init_velocity(orc_sim *S, const double *u, double rho0);
 void  orc_set_populations(orc_sim *S, const double *f);
 void  orc_get_populations(const orc_sim *S, double *f);
 void  orc_set_pipe(orc_sim *S, double R);
+void  orc_set_channel(orc_sim *S, double y_lo, double y_hi, double u_lo, double u_hi, int chain);
 int   orc_add_spheres(orc_sim *S, int n, const double *X, const double *R, double density_ratio,
                       const double *U, const double *W, int fixed);
 int   orc_step(orc_sim *S, int nsteps, int bc);

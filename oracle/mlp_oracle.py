@@ -59,6 +59,61 @@ def forward(w, X):
     return h, cache
 
 
+def round_bf16(a):
+    """Round to the nearest bfloat16, ties to even, through FP32 (the values
+    the kernels hold are FP32), returned as float64."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _fp32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def forward_tc(w, X, rnd=round_bf16):
+    """The forward pass in the operand precision of the tensor-core kernels:
+    the inputs, the weight matrices and each hidden layer's ReLU output are
+    rounded by `rnd` (bfloat16) before their product; biases are FP32;
+    products and sums are wide. Returns Y and the cache of backward_tc."""
+    layers = unpack(_fp32(w))
+    a = rnd(X)
+    cache = []
+    for i, (W, b) in enumerate(layers):
+        z = a @ rnd(W) + b
+        if i < 3:
+            h = np.maximum(z, 0.0)
+            cache.append((a, h))
+            a = rnd(h)
+        else:
+            cache.append((a, None))
+            a = z
+    return a, cache
+
+
+def loss_and_grad_tc(w, X, T, rnd=round_bf16):
+    """loss_and_grad() in the precision of the training kernel: the forward
+    of forward_tc; each weight gradient is the product of the layer's FP32
+    input (the first layer's input rounded by `rnd`, as the product used it)
+    with the wide output gradient; the gradient passed down a layer is the
+    product of the rounded output gradient with the rounded weights, masked
+    by the ReLU. With rnd = identity this is loss_and_grad()."""
+    Y, cache = forward_tc(w, X, rnd)
+    T = np.asarray(T, dtype=np.float64)
+    n = Y.shape[0]
+    L = float(np.mean((Y - T) ** 2))
+    d = 2.0 * (Y - T) / (n * Y.shape[1])
+    layers = unpack(_fp32(w))
+    grads = [None] * 4
+    for i in range(3, -1, -1):
+        h_in = cache[0][0] if i == 0 else cache[i - 1][1]
+        grads[i] = (h_in.T @ d, d.sum(axis=0))
+        if i > 0:
+            d = (rnd(d) @ rnd(layers[i][0]).T) * (cache[i - 1][1] > 0)
+    flat = np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])
+    return L, flat
+
+
 def loss_and_grad(w, X, T):
     """MSE loss L = mean((Y - T)^2) over samples and outputs and dL/dw by
     the chain rule."""

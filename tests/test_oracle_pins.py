@@ -258,7 +258,8 @@ def test_links_match_brute_force(orc):
 def test_uniform_flow_past_moving_sphere_stays_uniform(orc):
     """f = f_eq(1, U) everywhere and a sphere moving with U: every IBB scheme,
     the refill and the rigid-body update must keep the state exactly uniform,
-    and the Galilean-invariant momentum exchange must give zero force."""
+    and the Galilean-invariant momentum exchange must give zero force and
+    zero torque."""
     n = 16
     U = np.array([0.05, 0.02, -0.03])
     S = orc.Sim(n, n, n, 0.6)
@@ -275,6 +276,7 @@ def test_uniform_flow_past_moving_sphere_stays_uniform(orc):
         S.step(1, orc.BC_IBB)
         P = S.particles()
         assert np.max(np.abs(P["F"])) < 1e-13
+        assert np.max(np.abs(P["T"])) < 1e-13
         schemes |= set(S.links()["scheme"].tolist())
     f = S.populations()
     solid = S.solid()[0].astype(bool)
