@@ -51,7 +51,8 @@ typedef enum {
     LBM_EUNSTABLE = 4,   /* the watchdog saw NaN/Inf, rho outside [0.5,2] or |u| > 0.3 */
     LBM_ETIMEOUT = 5,    /* a bounded host wait on the stream ran out */
     LBM_ESTATE = 6,      /* call not allowed in the current state */
-    LBM_EUNSUPPORTED = 7 /* combination not built */
+    LBM_EUNSUPPORTED = 7, /* combination not built */
+    LBM_EIO = 8           /* a checkpoint file could not be opened, read or written, or is truncated */
 } lbm_status;
 
 /* No-slip treatment used by lbm_step (Sec. 2.1, Sec. 3.1). */
@@ -127,6 +128,35 @@ lbm_status lbm_add_spheres(lbm_ctx *ctx, int n, const double *xyz, const double 
  * is reported by the next call that synchronises (lbm_step when the previous
  * check has completed, lbm_stats, lbm_get_*). */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps, int bc);
+
+/* Bound, in seconds, of the host waits on the stream: calls that return
+ * host data first wait for the work already enqueued. Default 600 s. A wait
+ * that runs out returns LBM_ETIMEOUT and leaves the context usable: the
+ * work stays enqueued, and a later call waits for it again. seconds must be
+ * positive and at most 1e6, else LBM_EINVAL. */
+lbm_status lbm_set_wait_limit(lbm_ctx *ctx, double seconds);
+
+/* Checkpoint and restart (Sec. 2.2: the IBM-U pipe run was restarted from
+ * the IBM-B flow field). lbm_checkpoint writes to the file `path` everything
+ * the next step reads: the populations in their storage format, the step
+ * count, the wall treatment, the relaxation rates, the geometry (pipe radius,
+ * or the spheres' centres, radii, density ratio and fixed flag), the FP64
+ * particle state (U, W, the hydrodynamic force and torque of the last two
+ * steps, the contact force, the inner-fluid integrals of the IBM), the IBM
+ * force of the last step per support cell and per marker, and the closure
+ * weights. Syncs.
+ * lbm_restore reads such a file into a context created with the same grid
+ * (nx, ny, nz, storage, lattice), tau and force, capacities at least as
+ * large, and nothing set yet (no populations, geometry or step). The
+ * restored context then steps bit for bit as the saved one would have.
+ * Format: a fixed header and raw arrays in host byte order (not portable
+ * across byte orders). Errors: LBM_EINVAL (null path; restore: a file of
+ * another grid, tau or force), LBM_ESTATE (checkpoint of a context left
+ * unusable by an error; restore into a context that is not fresh),
+ * LBM_ENOMEM (capacities too small), LBM_EIO (open, read or write failed,
+ * truncated file, not a checkpoint), LBM_ECUDA. */
+lbm_status lbm_checkpoint(lbm_ctx *ctx, const char *path);
+lbm_status lbm_restore(lbm_ctx *ctx, const char *path);
 
 #define LBM_STATS_UNMASK 1   /* IBM: statistics on the raw virtual fluid inside particles */
 #define LBM_STATS_BINS 4     /* radial profiles around particles (Sec. 3.2) */
@@ -232,6 +262,9 @@ lbm_status lbm_num_links(lbm_ctx *ctx, long long *n);
 lbm_status lbm_get_links(lbm_ctx *ctx, long long capacity, long long *cell, int *dir, int *scheme, double *q,
                          int *pid);
 
+/* Number of spheres of the context (0 without particles). */
+lbm_status lbm_num_particles(lbm_ctx *ctx, int *n);
+
 /* Particle state (n,3) arrays; any pointer may be NULL. F/T are the
  * hydrodynamic force and torque of the last step. Syncs. */
 lbm_status lbm_get_particles(lbm_ctx *ctx, double *X, double *U, double *W, double *F, double *T);
@@ -317,10 +350,11 @@ lbm_status lbm_closure_set_weights(lbm_ctx *ctx, const float *w_host, int n, dou
 
 /* Kinetic energy and dissipation of a velocity field already in device
  * memory, computed without allocating anything. The paper has no
- * counterpart: this serves callers that cannot call cudaMalloc, e.g. code
- * running while a stream is captured into a CUDA graph, solvers whose
- * device memory belongs to another framework's pool, or loops that must not
- * pay cudaMalloc's implicit device synchronisation.
+ * counterpart: this serves callers that cannot call cudaMalloc, e.g.
+ * solvers whose device memory all belongs to another framework's pool (an
+ * allocation beside it would escape that pool's accounting or exceed its
+ * limit), or loops that must not pay cudaMalloc's implicit device
+ * synchronisation.
  * u_dev: 3*N doubles (component-major, x fastest), N = nx*ny*nz, device.
  * nu: kinematic viscosity. out_dev: 2 doubles on the device, receiving the
  * box averages of 1/2 |u|^2 and 2 nu s_ij s_ij (periodic central
@@ -330,7 +364,9 @@ lbm_status lbm_closure_set_weights(lbm_ctx *ctx, const float *w_host, int n, dou
  * GPU that loads it until exit), shared by all calls: calls that overlap on
  * the GPU race on it. N above lbm_field_energy_noalloc_max_cells()
  * (134,217,728 = 512^3) is refused with LBM_ENOMEM; bad pointers or sizes
- * give LBM_EINVAL. The first call on a device looks the scratch address up
+ * give LBM_EINVAL; a launch that fails gives LBM_ECUDA (an error left
+ * pending by earlier, unrelated work is neither reported nor cleared). The
+ * first call on a device looks the scratch address up
  * (cudaGetSymbolAddress); make that first call before any stream capture. */
 lbm_status lbm_field_energy_noalloc(const double *u_dev, int nx, int ny, int nz, double nu, double *out_dev,
                                     void *cuda_stream);

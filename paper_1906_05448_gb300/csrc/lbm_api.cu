@@ -236,21 +236,22 @@ cudaError_t plane_copy(Ctx &c, int i, bool to_f64) {
 }
 
 // Check the status word copied by the last asynchronous check (bounded
-// host wait: polls the event, gives up after `timeout_s`).
-lbm_status check_status(Ctx &c, bool wait, double timeout_s = 600.0) {
+// host wait: polls the event, gives up after the context's wait limit).
+lbm_status check_status(Ctx &c, bool wait) {
     if (!c.status_pending) return LBM_OK;
+    const double timeout_s = c.wait_limit_s;
     cudaError_t q = cudaEventQuery(c.ev_status);
     if (q == cudaErrorNotReady) {
         if (!wait) return LBM_OK;
         // bounded wait
-        const int sleeps = (int)(timeout_s * 1000.0);
-        for (int k = 0; k < sleeps; k++) {
+        const long long sleeps = (long long)(timeout_s * 1000.0);
+        for (long long k = 0; k < sleeps; k++) {
             q = cudaEventQuery(c.ev_status);
             if (q != cudaErrorNotReady) break;
             struct timespec ts = {0, 1000000};
             nanosleep(&ts, nullptr);
         }
-        if (q == cudaErrorNotReady) return fail(c, LBM_ETIMEOUT, "stream did not finish within %.0f s", timeout_s);
+        if (q == cudaErrorNotReady) return fail(c, LBM_ETIMEOUT, "stream did not finish within %g s", timeout_s);
     }
     if (q != cudaSuccess) return cuda_fail(c, q, "status event");
     c.status_pending = false;
@@ -651,6 +652,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.cl_eps = (float *)(b + P.cl_eps);
     c.max_cl = P.max_cl;
     c.armed_bc = -1;
+    c.wait_limit_s = 600.0;
     c.pipe_cx = 0.5 * (c.nx - 1);
     c.pipe_cy = 0.5 * (c.ny - 1);
     auto bad = [&](cudaError_t e, const char *w) {
@@ -1147,6 +1149,13 @@ lbm_status lbm_get_particles(lbm_ctx *h, double *X, double *U, double *W, double
     return s;
 }
 
+lbm_status lbm_num_particles(lbm_ctx *h, int *n) {
+    CTX_CHECK(h);
+    if (!n) return LBM_EINVAL;
+    *n = c.np;
+    return LBM_OK;
+}
+
 lbm_status lbm_num_markers(lbm_ctx *h, long long *n) {
     CTX_CHECK(h);
     if (!n) return LBM_EINVAL;
@@ -1166,6 +1175,213 @@ lbm_status lbm_get_markers(lbm_ctx *h, long long capacity, double *X, double *F,
     if (pid) CK(cudaMemcpyAsync(pid, c.mpid, 4 * c.nm, cudaMemcpyDeviceToHost, c.stream));
     CK(cudaStreamSynchronize(c.stream));
     return s;
+}
+
+lbm_status lbm_set_wait_limit(lbm_ctx *h, double seconds) {
+    CTX_CHECK(h);
+    if (!(seconds > 0.0 && seconds <= 1e6)) return fail(c, LBM_EINVAL, "wait limit must lie in (0, 1e6] s");
+    c.wait_limit_s = seconds;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace lbmgb {
+namespace {
+
+// Checkpoint file: this header, then raw arrays in host byte order (see
+// lbm_checkpoint in lbm.h for the list and their order).
+struct CkptHeader {
+    char magic[8];  // "LBMCKPT\0"
+    int version, nx, ny, nz, storage, q, rates, armed_bc, has_pipe, np, fixed, cl_ready;
+    double tau, F[3], rt[6];  // rates: e, eps, q, nu, pi, m
+    double pipe_R, dens, cl_uscale, cl_gscale;
+    long long step, nsites, nm;
+};
+constexpr int CKPT_VERSION = 1;
+constexpr size_t CKPT_CHUNK = 64u << 20;  // bytes staged through host memory at a time
+
+struct File {
+    FILE *f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+
+lbm_status io_fail(Ctx &c, const char *what, const char *path) {
+    return fail(c, LBM_EIO, "checkpoint %s failed: %s", what, path);
+}
+
+// device -> file and file -> device through a bounded host buffer
+lbm_status dev_to_file(Ctx &c, FILE *f, const void *dev, size_t bytes, const char *path) {
+    std::vector<char> buf(std::min(bytes, CKPT_CHUNK));
+    for (size_t o = 0; o < bytes; o += CKPT_CHUNK) {
+        const size_t n = std::min(CKPT_CHUNK, bytes - o);
+        CK(cudaMemcpyAsync(buf.data(), (const char *)dev + o, n, cudaMemcpyDeviceToHost, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+        if (fwrite(buf.data(), 1, n, f) != n) return io_fail(c, "write", path);
+    }
+    return LBM_OK;
+}
+lbm_status file_to_dev(Ctx &c, FILE *f, void *dev, size_t bytes, const char *path) {
+    std::vector<char> buf(std::min(bytes, CKPT_CHUNK));
+    for (size_t o = 0; o < bytes; o += CKPT_CHUNK) {
+        const size_t n = std::min(CKPT_CHUNK, bytes - o);
+        if (fread(buf.data(), 1, n, f) != n) return io_fail(c, "read (truncated file)", path);
+        CK(cudaMemcpyAsync((char *)dev + o, buf.data(), n, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
+    return LBM_OK;
+}
+
+#define CKS(call)                                  \
+    do {                                           \
+        lbm_status s_ = (call);                    \
+        if (s_ != LBM_OK) return s_;               \
+    } while (0)
+
+size_t arith_bytes(const Ctx &c) { return c.storage == LBM_F64 ? 8 : 4; }
+
+}  // namespace
+}  // namespace lbmgb
+
+extern "C" {
+
+lbm_status lbm_checkpoint(lbm_ctx *h, const char *path) {
+    CTX_CHECK(h);
+    if (!path) return fail(c, LBM_EINVAL, "null path");
+    if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
+    lbm_status s = sync_all(c);
+    if (s != LBM_OK) return s;
+    CkptHeader H;
+    memset(&H, 0, sizeof(H));
+    memcpy(H.magic, "LBMCKPT", 8);
+    H.version = CKPT_VERSION;
+    H.nx = c.nx;
+    H.ny = c.ny;
+    H.nz = c.nz;
+    H.storage = c.storage;
+    H.q = c.q;
+    H.rates = c.rates;
+    H.armed_bc = c.armed_bc;
+    H.has_pipe = c.has_pipe;
+    H.np = c.np;
+    H.fixed = c.fixed;
+    H.cl_ready = c.cl_ready;
+    H.tau = c.tau;
+    for (int d = 0; d < 3; d++) H.F[d] = c.F[d];
+    const double rt[6] = {c.rt.d_e, c.rt.d_eps, c.rt.d_q, c.rt.d_nu, c.rt.d_pi, c.rt.d_m};
+    for (int k = 0; k < 6; k++) H.rt[k] = rt[k];
+    H.pipe_R = c.pipe_R;
+    H.dens = c.dens;
+    H.cl_uscale = c.cl_uscale;
+    H.cl_gscale = c.cl_gscale;
+    H.step = c.step;
+    const bool ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
+    H.nsites = ibm ? c.nsites : 0;
+    H.nm = ibm ? c.nm : 0;
+    File F;
+    F.f = fopen(path, "wb");
+    if (!F.f) return io_fail(c, "open", path);
+    if (fwrite(&H, sizeof(H), 1, F.f) != 1) return io_fail(c, "write", path);
+    CKS(dev_to_file(c, F.f, c.fA, (size_t)c.q * (size_t)c.N * storage_bytes(c.storage), path));
+    if (c.np > 0) {
+        const size_t b3 = sizeof(double) * 3 * (size_t)c.np;
+        for (const double *p : {c.X, c.U, c.W, c.Fh, c.Th, c.Fprev, c.Tprev, c.Fc, c.Iu, c.Ir})
+            CKS(dev_to_file(c, F.f, p, b3, path));
+        CKS(dev_to_file(c, F.f, c.R, sizeof(double) * (size_t)c.np, path));
+        CKS(dev_to_file(c, F.f, c.has_prev, sizeof(int) * (size_t)c.np, path));
+    }
+    if (H.nsites > 0) CKS(dev_to_file(c, F.f, c.sup_F, 3 * arith_bytes(c) * (size_t)H.nsites, path));
+    if (H.nm > 0) CKS(dev_to_file(c, F.f, c.mFacc, sizeof(double) * 3 * (size_t)H.nm, path));
+    if (c.cl_ready) CKS(dev_to_file(c, F.f, c.cl_w, sizeof(float) * LBM_MLP_NPARAM, path));
+    if (fflush(F.f) != 0) return io_fail(c, "write", path);
+    return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx *h, const char *path) {
+    CTX_CHECK(h);
+    if (!path) return fail(c, LBM_EINVAL, "null path");
+    if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe || c.step != 0)
+        return fail(c, LBM_ESTATE, "restore needs a freshly created context");
+    File F;
+    F.f = fopen(path, "rb");
+    if (!F.f) return io_fail(c, "open", path);
+    CkptHeader H;
+    if (fread(&H, sizeof(H), 1, F.f) != 1 || memcmp(H.magic, "LBMCKPT", 8) != 0 || H.version != CKPT_VERSION)
+        return io_fail(c, "read (not a checkpoint of this version)", path);
+    if (H.nx != c.nx || H.ny != c.ny || H.nz != c.nz || H.storage != c.storage || H.q != c.q || H.tau != c.tau ||
+        H.F[0] != c.F[0] || H.F[1] != c.F[1] || H.F[2] != c.F[2])
+        return fail(c, LBM_EINVAL, "checkpoint of another grid, storage, lattice, tau or force");
+    if (H.np < 0 || H.np > c.max_np) return fail(c, LBM_ENOMEM, "%d particles exceed max_particles %d", H.np, c.max_np);
+    if (H.armed_bc < -1 || H.armed_bc > LBM_BC_IBM_B || H.nsites < 0 || H.nm < 0 || H.step < 0)
+        return io_fail(c, "read (corrupt header)", path);
+    // relaxation rates (lbm_set_mrt_rates may have changed them)
+    c.rates = H.rates;
+    Rates &r = c.rt;
+    r.d_e = H.rt[0];
+    r.d_eps = H.rt[1];
+    r.d_q = H.rt[2];
+    r.d_nu = H.rt[3];
+    r.d_pi = H.rt[4];
+    r.d_m = H.rt[5];
+    r.s_e = (float)r.d_e;
+    r.s_eps = (float)r.d_eps;
+    r.s_q = (float)r.d_q;
+    r.s_nu = (float)r.d_nu;
+    r.s_pi = (float)r.d_pi;
+    r.s_m = (float)r.d_m;
+    const size_t pop_bytes = (size_t)c.q * (size_t)c.N * storage_bytes(c.storage);
+    // the populations come first in the file: skip them to rebuild the geometry
+    if (fseek(F.f, (long)pop_bytes, SEEK_CUR) != 0) return io_fail(c, "seek", path);
+    std::vector<double> P3[10], R;
+    std::vector<int> has;
+    if (H.np > 0) {
+        for (auto &v : P3) {
+            v.resize(3 * (size_t)H.np);
+            if (fread(v.data(), sizeof(double), v.size(), F.f) != v.size()) return io_fail(c, "read", path);
+        }
+        R.resize((size_t)H.np);
+        has.resize((size_t)H.np);
+        if (fread(R.data(), sizeof(double), R.size(), F.f) != R.size()) return io_fail(c, "read", path);
+        if (fread(has.data(), sizeof(int), has.size(), F.f) != has.size()) return io_fail(c, "read", path);
+    }
+    // geometry and wall treatment, rebuilt from the saved positions exactly as the first set-up built them
+    if (H.has_pipe) CKS(lbm_set_pipe(h, H.pipe_R));
+    if (H.np > 0)
+        CKS(lbm_add_spheres(h, H.np, P3[0].data(), R.data(), H.dens, P3[1].data(), P3[2].data(), H.fixed));
+    if (H.armed_bc >= 0) CKS(arm(c, H.armed_bc));
+    // then the saved state over what the set-up computed
+    if (fseek(F.f, (long)sizeof(H), SEEK_SET) != 0) return io_fail(c, "seek", path);
+    CKS(file_to_dev(c, F.f, c.fA, pop_bytes, path));
+    c.bvals_valid = 0;  // the next ghost pass reads the wall cells from the populations
+    if (H.np > 0) {
+        if (fseek(F.f, (long)(sizeof(double) * (10 * 3 + 1) * (size_t)H.np + sizeof(int) * (size_t)H.np), SEEK_CUR) != 0)
+            return io_fail(c, "seek", path);
+        const size_t b3 = sizeof(double) * 3 * (size_t)H.np;
+        double *dst[10] = {c.X, c.U, c.W, c.Fh, c.Th, c.Fprev, c.Tprev, c.Fc, c.Iu, c.Ir};
+        for (int k = 0; k < 10; k++) CK(cudaMemcpyAsync(dst[k], P3[k].data(), b3, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.Xold, P3[0].data(), b3, cudaMemcpyHostToDevice, c.stream));
+        CK(cudaMemcpyAsync(c.has_prev, has.data(), sizeof(int) * has.size(), cudaMemcpyHostToDevice, c.stream));
+        CK(cudaStreamSynchronize(c.stream));
+    }
+    if (H.nsites > 0) {
+        if (H.nsites != c.nsites) return fail(c, LBM_EINVAL, "checkpoint support set differs from the rebuilt one");
+        CKS(file_to_dev(c, F.f, c.sup_F, 3 * arith_bytes(c) * (size_t)H.nsites, path));
+    }
+    if (H.nm > 0) {
+        if (H.nm != c.nm) return fail(c, LBM_EINVAL, "checkpoint markers differ from the rebuilt ones");
+        CKS(file_to_dev(c, F.f, c.mFacc, sizeof(double) * 3 * (size_t)H.nm, path));
+    }
+    if (H.cl_ready) {
+        if (c.max_cl == 0) return fail(c, LBM_EUNSUPPORTED, "closure weights need max_particles > 0");
+        CKS(file_to_dev(c, F.f, c.cl_w, sizeof(float) * LBM_MLP_NPARAM, path));
+        c.cl_uscale = H.cl_uscale;
+        c.cl_gscale = H.cl_gscale;
+        c.cl_ready = 1;
+    }
+    c.step = H.step;
+    return sync_all(c);
 }
 
 lbm_status lbm_closure_set_weights(lbm_ctx *h, const float *w_host, int n, double u_scale, double g_scale) {
@@ -1256,6 +1472,7 @@ const char *lbm_status_string(int s) {
     case LBM_ETIMEOUT: return "timed out waiting for the GPU";
     case LBM_ESTATE: return "call not allowed in this state";
     case LBM_EUNSUPPORTED: return "unsupported";
+    case LBM_EIO: return "checkpoint file error";
     default: return "unknown status";
     }
 }

@@ -348,6 +348,88 @@ __host__ __device__ __forceinline__ void collide(R g[19], R Fx, R Fy, R Fz, cons
     }
 }
 
+// Single-node bounce-back, the last fallback of the scheme chain (Sec. 3.1,
+// after Zhao & Yong 2017; the formula is a reading): halfway bounce-back
+// plus (1 - 2q)/2 (d_l + d_ibar), where d = M^-1 S (m - m_eq) is the
+// departure the collision at the boundary node x_f removed. It is recovered
+// from the node's post-collision populations alone, moment by moment:
+//   S (m - m_eq) = S (I - S)^-1 (m~ - m_eq - (I - S/2) M F_i),
+// with rho and u = (sum f c - F/2)/rho those of that collision. Rates of 0
+// or exactly 1 contribute nothing. Odd moments cancel in d_l + d_ibar, so
+// only the even ones are formed. p: the 19 stored values of x_f, population
+// k at p[k * stride]. Returns d_l + d_ibar.
+template <int S>
+__device__ __noinline__ typename Store<S>::R single_node_pair(const typename Store<S>::T *p, size_t stride, int l,
+                                                              typename Store<S>::R Fx, typename Store<S>::R Fy,
+                                                              typename Store<S>::R Fz, const Rates &rt) {
+    typedef typename Store<S>::R R;
+    R g[19];
+#pragma unroll
+    for (int k = 0; k < 19; k++) g[k] = Store<S>::ld(p + k * stride);
+    R drho = g[0];
+#pragma unroll
+    for (int k = 1; k < 19; k++) drho += g[k];
+    const R jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
+    const R jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
+    const R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
+    const R rho = R(1) + drho, ir = R(1) / rho;
+    const R ux = (jx - R(0.5) * Fx) * ir, uy = (jy - R(0.5) * Fy) * ir, uz = (jz - R(0.5) * Fz) * ir;
+    R Fi[19];
+#pragma unroll
+    for (int k = 0; k < 19; k++) Fi[k] = guo_term<R>(k, ux, uy, uz, Fx, Fy, Fz);
+    // even d'Humieres moments (e, eps, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz) of h
+    auto even = [](const R *h, R *m) {
+        const R Sx = h[1] + h[2], Sy = h[3] + h[4], Sz = h[5] + h[6];
+        const R Sa = h[7] + h[8], Sb = h[9] + h[10], Sc = h[11] + h[12], Sd = h[13] + h[14];
+        const R Se = h[15] + h[16], Sf = h[17] + h[18];
+        const R A = Sx + Sy + Sz, Exy = Sa + Sb, Exz = Sc + Sd, Eyz = Se + Sf, E = Exy + Exz + Eyz;
+        m[0] = R(-30) * h[0] - R(11) * A + R(8) * E;
+        m[1] = R(12) * h[0] - R(4) * A + E;
+        m[2] = R(2) * Sx - Sy - Sz + Exy + Exz - R(2) * Eyz;
+        m[3] = R(-2) * (R(2) * Sx - Sy - Sz) + Exy + Exz - R(2) * Eyz;
+        m[4] = Sy - Sz + Exy - Exz;
+        m[5] = R(-2) * (Sy - Sz) + Exy - Exz;
+        m[6] = Sa - Sb;
+        m[7] = Se - Sf;
+        m[8] = Sc - Sd;
+    };
+    R m[9], mF[9];
+    even(g, m);
+    even(Fi, mF);
+    // equilibrium moments minus those of w
+    const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz, tx = R(2) * uxx - uyy - uzz;
+    const R eq[9] = {R(-11) * drho + R(19) * rho * u2, R(3) * drho - R(5.5) * rho * u2, rho * tx, R(-0.5) * rho * tx,
+                     rho * (uyy - uzz), R(-0.5) * rho * (uyy - uzz), rho * ux * uy, rho * uy * uz, rho * ux * uz};
+    const bool dbl = sizeof(R) == 8;
+    const R se = dbl ? R(rt.d_e) : R(rt.s_e), sep = dbl ? R(rt.d_eps) : R(rt.s_eps);
+    const R snu = dbl ? R(rt.d_nu) : R(rt.s_nu), spi = dbl ? R(rt.d_pi) : R(rt.s_pi);
+    const R s[9] = {se, sep, snu, spi, snu, spi, snu, snu, snu};
+    const R norm[9] = {R(1.0 / 2394.0), R(1.0 / 252.0), R(1.0 / 36.0), R(1.0 / 72.0), R(1.0 / 12.0),
+                       R(1.0 / 24.0), R(0.25), R(0.25), R(0.25)};
+    R a[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const R f = (s[k] == R(0) || s[k] == R(1)) ? R(0) : s[k] / (R(1) - s[k]);
+        a[k] = f * (m[k] - eq[k] - (R(1) - R(0.5) * s[k]) * mF[k]) * norm[k];
+    }
+    // even part of the back-transform for the pair (l, ibar)
+    const R ax = R(-11) * a[0] - R(4) * a[1];
+    const R ed = R(8) * a[0] + a[1];
+    R ev;
+    switch ((l + 1) >> 1) {
+    case 1: ev = ax + R(2) * a[2] - R(4) * a[3]; break;
+    case 2: ev = ax - a[2] + R(2) * a[3] + a[4] - R(2) * a[5]; break;
+    case 3: ev = ax - a[2] + R(2) * a[3] - a[4] + R(2) * a[5]; break;
+    case 4: ev = ed + a[2] + a[3] + a[4] + a[5] + a[6]; break;
+    case 5: ev = ed + a[2] + a[3] + a[4] + a[5] - a[6]; break;
+    case 6: ev = ed + a[2] + a[3] - a[4] - a[5] + a[8]; break;
+    case 7: ev = ed + a[2] + a[3] - a[4] - a[5] - a[8]; break;
+    case 8: ev = ed - R(2) * a[2] - R(2) * a[3] + a[7]; break;
+    default: ev = ed - R(2) * a[2] - R(2) * a[3] - a[7]; break;
+    }
+    return R(2) * ev;
+}
+
 // ------------------------------------------------------------- helpers ----
 // body force component in the arithmetic type R
 template <typename R, typename Args>

@@ -109,6 +109,7 @@ struct Ctx {
     unsigned *h_status;
     cudaEvent_t ev_status;
     bool status_pending;
+    double wait_limit_s;  // bound of the host waits on the stream (lbm_set_wait_limit)
     // geometry
     int has_pipe;
     double pipe_R, pipe_cx, pipe_cy;

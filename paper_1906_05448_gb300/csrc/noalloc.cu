@@ -2,10 +2,10 @@
 // allocation: the per-block partial sums live in a file-scope device array.
 //
 // This is a variant of the statistics reduction behind lbm_stats for
-// callers that cannot allocate device memory: code running while a stream
-// is being captured into a CUDA graph (cudaMalloc is not allowed there),
-// solvers whose device memory is entirely owned by another framework's pool,
-// and loops that must not pay the implicit device synchronisation of
+// callers that cannot allocate device memory: solvers whose device memory
+// is entirely owned by another framework's pool (a cudaMalloc beside it
+// would break that pool's accounting or fail under its limit), and loops
+// that must not pay the implicit device synchronisation of
 // cudaMalloc/cudaFree. The caller passes the field and a device output.
 #include <cuda_runtime.h>
 
@@ -134,10 +134,19 @@ extern "C" lbm_status lbm_field_energy_noalloc(const double *u_dev, int nx, int 
     void *scratch = nullptr;
     if (na_scratch(&scratch) != cudaSuccess) return LBM_ECUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int nblk = (int)((N + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
-    na_partial_kernel<<<nblk, NA_THREADS, 0, s>>>(u_dev, nx, ny, nz, N, nu, (double *)scratch);
-    na_final_kernel<<<1, NA_THREADS, 0, s>>>((const double *)scratch, nblk, N, out_dev);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    int nblk = (int)((N + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
+    // each launch reports its own status (cudaLaunchKernel), so an error left
+    // pending on this thread by unrelated earlier work is neither reported
+    // here nor cleared
+    double *partials = (double *)scratch;
+    void *a1[] = {(void *)&u_dev, (void *)&nx, (void *)&ny, (void *)&nz, (void *)&N, (void *)&nu, (void *)&partials};
+    if (cudaLaunchKernel((const void *)na_partial_kernel, dim3((unsigned)nblk), dim3(NA_THREADS), a1, 0, s) !=
+        cudaSuccess)
+        return LBM_ECUDA;
+    void *a2[] = {(void *)&partials, (void *)&nblk, (void *)&N, (void *)&out_dev};
+    if (cudaLaunchKernel((const void *)na_final_kernel, dim3(1), dim3(NA_THREADS), a2, 0, s) != cudaSuccess)
+        return LBM_ECUDA;
+    return LBM_OK;
 }
 
 extern "C" long long lbm_field_energy_noalloc_max_cells(void) { return NA_MAX_CELLS; }

@@ -28,7 +28,8 @@ __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >=
 // Population bounced back into the fluid node x_f along ibar = opp(l) at time
 // t + 1 from post-collision values at t (Sec. 2.1): quadratic (sch 0) or
 // linear (sch 1) interpolated bounce-back, split at q = 1/2, or the halfway
-// rule (sch 2) where the interpolation nodes are not fluid. fl0 = f*_l(x_f),
+// rule (sch 2, to which the callers add the single-node correction of
+// single_node_pair) where the interpolation nodes are not fluid. fl0 = f*_l(x_f),
 // fi0 = f*_ibar(x_f); c1 = x_f - c_l, c2 = x_f - 2 c_l; D = moving-wall term.
 template <int S>
 __device__ __forceinline__ typename Store<S>::R ibb_value(const typename Store<S>::T *A, size_t N, int l, int i,
@@ -73,6 +74,9 @@ struct LinkArgs {
     int nx, ny, nz;
     long long N;
     FastDiv dx, dxy;  // division by nx and nx*ny
+    double F[3];      // body force on fluid cells (single-node fallback)
+    float Fs[3];
+    Rates rt;
 };
 
 
@@ -105,8 +109,14 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         const int i = opp(l);
         const R fl0 = Store<S>::ld(A + (size_t)l * N + c);  // f*_l(x_f), toward the wall
         const R fi0 = Store<S>::ld(A + (size_t)i * N + c);  // f*_ibar(x_f)
+        // single-node fallback: (1 - 2q)/2 (d_l + d_ibar) from the node's own state
+        auto single = [&](R qq) -> R {
+            return R(0.5) * (R(1) - R(2) * qq) *
+                   single_node_pair<S>(A + c, N, l, body_force<R>(a, 0), body_force<R>(a, 1), body_force<R>(a, 2), a.rt);
+        };
         if constexpr (!PART) {
-            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, R(0), fl0, fi0);
+            R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, R(0), fl0, fi0);
+            if (sch == 2) v += single(R(q));
             Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
         } else if constexpr (sizeof(R) == 8) {
             // FP64 storage: wall velocity and momentum exchange in FP64
@@ -122,7 +132,8 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             }
             // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
             const R Dw = pid >= 0 ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
-            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, Dw, fl0, fi0);
+            R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, Dw, fl0, fi0);
+            if (sch == 2) v += single(R(q));
             Store<S>::st(A + (size_t)i * N + cb, v);
             if (pid >= 0) {
                 // momentum exchange with unshifted f = g + w (w_l = w_ibar)
@@ -159,7 +170,8 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             }
             const float w_l = float(wgt(l));
             const float Dw = pid >= 0 ? -6.0f * w_l * (lx * uw[0] + ly * uw[1] + lz * uw[2]) : 0.0f;
-            const float v = ibb_value<S>(A, N, l, i, sch, qf, c1, c2, Dw, fl0, fi0);
+            float v = ibb_value<S>(A, N, l, i, sch, qf, c1, c2, Dw, fl0, fi0);
+            if (sch == 2) v += single(qf);
             Store<S>::st(A + (size_t)i * N + cb, v);
             if (pid >= 0) {
                 const float fo = fl0 + w_l, fi = v + w_l;
@@ -249,6 +261,9 @@ struct StaticLinkArgs {
     int nx, ny, nz;
     long long N;
     FastDiv dx, dxy;
+    double F[3];  // body force on fluid cells (single-node fallback)
+    float Fs[3];
+    Rates rt;
 };
 
 template <int S>
@@ -281,7 +296,13 @@ __global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
             fl0 = Store<S>::ld(A + (size_t)l * N + c);
             fi0 = Store<S>::ld(A + (size_t)i * N + c);
         }
-        const R v = ibb_value<S>(A, N, l, i, sch, qq, c1, c2, R(0), fl0, fi0);
+        R v = ibb_value<S>(A, N, l, i, sch, qq, c1, c2, R(0), fl0, fi0);
+        if (sch == 2) {  // single-node fallback from the wall cell's own values
+            const T *p = a.bvals ? (const T *)a.bvals + (size_t)19 * __ldg(a.rank + k) : A + c;
+            v += R(0.5) * (R(1) - R(2) * qq) *
+                 single_node_pair<S>(p, a.bvals ? 1 : N, l, body_force<R>(a, 0), body_force<R>(a, 1),
+                                     body_force<R>(a, 2), a.rt);
+        }
         if (a.gvals)
             Store<S>::st((T *)a.gvals + __ldg(a.gidx + k), v);  // read by the sweep in place of the pull
         else
@@ -307,6 +328,11 @@ static cudaError_t launch_links_s(Ctx &c) {
         a.N = c.N;
         a.dx = FastDiv((unsigned)c.nx);
         a.dxy = FastDiv((unsigned)(c.nx * c.ny));
+        for (int d = 0; d < 3; d++) {
+            a.F[d] = c.F[d];
+            a.Fs[d] = (float)c.F[d];
+        }
+        a.rt = c.rt;
         int most = 0;
         for (int l = 0; l < 19; l++) most = std::max(most, c.slink_off[l + 1] - c.slink_off[l]);
         unsigned nbx = (unsigned)((most + 255) / 256);
@@ -317,7 +343,8 @@ static cudaError_t launch_links_s(Ctx &c) {
     }
     LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_dP, c.link_dT,
                c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N,
-               FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny))};
+               FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny)), {c.F[0], c.F[1], c.F[2]},
+               {(float)c.F[0], (float)c.F[1], (float)c.F[2]}, c.rt};
     long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
     if (n > c.max_links) n = c.max_links;
     long long nb = (n + 255) / 256;

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EUNSUPPORTED = range(8)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EUNSUPPORTED, LBM_EIO = range(9)
 BC_NONE, BC_IBB, BC_IBM_U, BC_IBM_B = 0, 1, 2, 3
 F64, F32, F16S, BF16S = 0, 1, 2, 3
 RATES_SRT, RATES_DHUMIERES = 0, 1
@@ -29,8 +29,8 @@ BC = {"none": BC_NONE, "ibb": BC_IBB, "ibm_u": BC_IBM_U, "ibm_b": BC_IBM_B}
 # every entry point declared in include/lbm.h
 EXPORTS = [
     "lbm_workspace_bytes", "lbm_create", "lbm_init_velocity", "lbm_set_populations", "lbm_set_pipe",
-    "lbm_add_spheres", "lbm_step", "lbm_stats", "lbm_spectrum", "lbm_pipe_profiles", "lbm_tke_budget", "lbm_set_mrt_rates", "lbm_get_field", "lbm_num_links", "lbm_get_links",
-    "lbm_get_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile",
+    "lbm_add_spheres", "lbm_step", "lbm_set_wait_limit", "lbm_checkpoint", "lbm_restore", "lbm_stats", "lbm_spectrum", "lbm_pipe_profiles", "lbm_tke_budget", "lbm_set_mrt_rates", "lbm_get_field", "lbm_num_links", "lbm_get_links",
+    "lbm_get_particles", "lbm_num_particles", "lbm_num_markers", "lbm_get_markers", "lbm_profile",
     "lbm_mlp_workspace_bytes", "lbm_mlp_num_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_train",
     "lbm_closure_samples", "lbm_closure_targets", "lbm_closure_set_weights",
     "lbm_field_energy_noalloc", "lbm_field_energy_noalloc_max_cells", "lbm_last_error",
@@ -110,6 +110,9 @@ def load(build_if_missing: bool = False):
         "lbm_set_pipe": (ctypes.c_int, [_P, ctypes.c_double]),
         "lbm_add_spheres": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, ctypes.c_int]),
         "lbm_step": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "lbm_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+        "lbm_checkpoint": (ctypes.c_int, [_P, ctypes.c_char_p]),
+        "lbm_restore": (ctypes.c_int, [_P, ctypes.c_char_p]),
         "lbm_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Stats)]),
         "lbm_spectrum": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D, _D]),
         "lbm_pipe_profiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
@@ -119,6 +122,7 @@ def load(build_if_missing: bool = False):
         "lbm_num_links": (ctypes.c_int, [_P, _L]),
         "lbm_get_links": (ctypes.c_int, [_P, ctypes.c_longlong, _L, _I, _I, _D, _I]),
         "lbm_get_particles": (ctypes.c_int, [_P, _D, _D, _D, _D, _D]),
+        "lbm_num_particles": (ctypes.c_int, [_P, _I]),
         "lbm_num_markers": (ctypes.c_int, [_P, _L]),
         "lbm_get_markers": (ctypes.c_int, [_P, ctypes.c_longlong, _D, _D, _D, _I]),
         "lbm_profile": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(Profile)]),
@@ -236,6 +240,20 @@ class Lattice:
         if isinstance(bc, str):
             bc = BC[bc]
         return self._check(self.L.lbm_step(self.h, int(n), int(bc)))
+
+    def set_wait_limit(self, seconds):
+        """Bound of the host waits on the stream (LBM_ETIMEOUT when it runs out)."""
+        self._check(self.L.lbm_set_wait_limit(self.h, float(seconds)))
+
+    def checkpoint(self, path):
+        self._check(self.L.lbm_checkpoint(self.h, os.fsencode(path)))
+
+    def restore(self, path):
+        """Load a checkpoint into this freshly created context (same grid, tau, force)."""
+        self._check(self.L.lbm_restore(self.h, os.fsencode(path)))
+        n = ctypes.c_int()
+        self._check(self.L.lbm_num_particles(self.h, ctypes.byref(n)))
+        self.np = n.value
 
     def spectrum(self, nbins, flags=0):
         """3D kinetic-energy and dissipation spectra E[K], D[K], K < nbins."""

@@ -94,3 +94,45 @@ def test_profile_counts_launches_and_times(lbm):
     p = S.profile(0)
     assert p["launches"]["bulk"] == 4 and p["launches"]["ibb_boundary"] == 4
     S.close()
+
+
+def test_wait_limit_runs_out_and_context_stays_usable(lbm):
+    """LBM_ETIMEOUT from the bounded host wait: a host function that sleeps
+    1.5 s is enqueued on the library's stream ahead of the status check, and
+    the wait limit is set to 0.2 s. Nothing waits on the GPU: the stream is
+    held on the host. A later call with a longer limit succeeds."""
+    import ctypes
+    import time
+
+    n = 16
+    L = lbm.Lattice(n, n, n, 0.6, storage=lbm.F32)
+    L.step(2)
+    L.stats()  # nothing pending
+    # the CUDA runtime the library itself loaded (matched by soname)
+    cudart = ctypes.CDLL("libcudart.so.13")
+    HOSTFN = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
+    slept = []
+
+    def hold(_):
+        time.sleep(1.5)
+        slept.append(1)
+
+    cb = HOSTFN(hold)
+    cudart.cudaLaunchHostFunc.argtypes = [ctypes.c_void_p, HOSTFN, ctypes.c_void_p]
+    cudart.cudaLaunchHostFunc.restype = ctypes.c_int
+    assert cudart.cudaLaunchHostFunc(ctypes.c_void_p(L.stream.cuda_stream), cb, None) == 0
+    L.step(1)
+    with pytest.raises(lbm.LbmError):
+        L.set_wait_limit(0.0)
+    L.set_wait_limit(0.2)
+    t0 = time.time()
+    with pytest.raises(lbm.LbmError) as e:
+        L.stats()
+    assert e.value.status == lbm.LBM_ETIMEOUT
+    assert time.time() - t0 < 1.4 and not slept
+    L.set_wait_limit(30.0)
+    s = L.stats()
+    assert slept and s["step"] == 3
+    L.step(1)
+    assert L.stats()["step"] == 4
+    L.close()

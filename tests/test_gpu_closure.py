@@ -1,9 +1,14 @@
 """Learned closure on the GPU: tensor-core forward and gradients against the
-FP64 oracle (BF16 operands, FP32 accumulation: about 1e-2 relative), training
-reduces the loss, near-surface samples are well formed."""
+oracle, element by element against its model of the kernels' operand
+precision (BF16 operands, wide accumulation; oracle.mlp_oracle.forward_tc)
+and in norm against the exact FP64 network; training reduces the loss;
+near-surface features and the closure dissipation against a numpy
+restatement on the oracle's own flow field."""
 import numpy as np
 import pytest
 
+import oracle
+import workloads
 from oracle import mlp_oracle as M
 
 pytestmark = pytest.mark.gpu
@@ -35,6 +40,12 @@ def test_forward_matches_oracle(env):
         Y = mlp.forward(torch.from_numpy(X), w).cpu().numpy()
         Yo, _ = M.forward(w.astype(np.float64), X.astype(np.float64))
         assert np.linalg.norm(Y - Yo) / np.linalg.norm(Yo) < 3e-2
+        # element by element against the operand-precision model: what is
+        # left is FP32 accumulation (and a BF16 rounding of a hidden unit
+        # that falls the other way)
+        Yt, _ = M.forward_tc(w, X)
+        err = np.abs(Y - Yt).max() / np.abs(Yt).max()
+        assert err < 2e-3, err
 
 
 def test_loss_gradient_matches_oracle(env):
@@ -53,6 +64,18 @@ def test_loss_gradient_matches_oracle(env):
         k = a * b + b
         assert np.linalg.norm(g[o:o + k] - go[o:o + k]) / np.linalg.norm(go[o:o + k]) < 8e-2
         o += k
+    # element by element, weight and bias blocks apart, against the
+    # kernels' operand-precision model (the inputs and weights rounded to
+    # BF16 as the kernels round them)
+    Lt, gt = M.loss_and_grad_tc(w, X.astype(np.float64), T.astype(np.float64))
+    assert L == pytest.approx(Lt, rel=1e-4)
+    o = 0
+    for a, b in zip(M.SIZES[:-1], M.SIZES[1:]):
+        for k in (a * b, b):
+            blk, ref = g[o:o + k], gt[o:o + k]
+            err = np.abs(blk - ref).max() / np.abs(ref).max()
+            assert err < 1e-2, (a, b, k, err)
+            o += k
 
 
 def test_training_fits_a_teacher(env):
@@ -110,3 +133,92 @@ def test_closure_reduces_near_surface_dissipation_error(env):
     assert last < 0.3 * zero
     e_plain, e_closure = closure.evaluate(64, 30, [100, 101], 100, w.cpu().numpy(), us, gs)
     assert e_closure < 0.8 * e_plain, (e_plain, e_closure)
+
+
+def _nearest_surface(X, R, n, solid):
+    """Per cell: the nearest particle surface on the fluid side (distance
+    |x - X_p| - R_p > 0, ties to the lower index), its distance, and the
+    minimum-image offset x - X_p."""
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).astype(float)
+    best = np.full(n ** 3, np.inf)
+    pid = np.full(n ** 3, -1)
+    off = np.zeros((n ** 3, 3))
+    for p in range(len(R)):
+        r = pos - X[p]
+        r -= n * np.rint(r / n)
+        s = np.sqrt((r ** 2).sum(axis=1)) - R[p]
+        take = (s > 0) & (s < best) & (solid == 0)
+        best[take], pid[take], off[take] = s[take], p, r[take]
+    return pid, best, off
+
+
+def test_closure_features_and_dissipation_match_oracle(env):
+    """An IBM-B run of moving spheres on the GPU and in the oracle (FP64,
+    same inputs). The near-surface nodes and their 85 features
+    (lbm_closure_samples) must be those a numpy restatement builds from the
+    oracle's velocity; the dissipation with the closure
+    (lbm_stats(LBM_STATS_CLOSURE)) must be the oracle's with the
+    central-difference dissipation of those nodes replaced by the one of
+    the oracle network's gradients (operand-precision model)."""
+    torch, lbm = env
+    n, R, us, gs, tau = 28, 4.0, 0.03, 133.0, 0.6
+    Xp = workloads.place_spheres((n, n, n), 3, R, 2.0, seed=3)
+    u0 = workloads.hit_velocity(n, seed=2, k_peak=3.0, u_rms=0.02)
+    g = lbm.Lattice(n, n, n, tau, storage=lbm.F64, rates=lbm.RATES_DHUMIERES, max_particles=3)
+    o = oracle.Sim(n, n, n, tau, rates=oracle.RATES_DHUMIERES)
+    for s in (g, o):
+        s.init_velocity(u0)
+        s.add_spheres(Xp, R, density_ratio=5.0)
+    g.step(10, lbm.BC_IBM_B)
+    o.step(10, oracle.BC_IBM_B)
+    P = o.particles()
+    solid = o.solid()[0]
+    pid, dist, off = _nearest_surface(P["X"], [R] * 3, n, solid)
+    near = np.flatnonzero((pid >= 0) & (dist <= 2.0))
+    Xg, cells = g.closure_samples(us, 20000)
+    Xg, cells = Xg.cpu().numpy(), cells.cpu().numpy()
+    order = np.argsort(cells)
+    Xg, cells = Xg[order], cells[order]
+    assert np.array_equal(cells, near)
+    u = o.macro()[1]
+    feats = np.zeros((len(near), 85))
+    cx, cy, cz = near % n, (near // n) % n, near // (n * n)
+    j = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                q = (cx + dx) % n + n * (((cy + dy) % n) + n * ((cz + dz) % n))
+                sv = off[near] + np.array([dx, dy, dz])
+                ub = P["U"][pid[near]] + np.cross(P["W"][pid[near]], sv)
+                feats[:, j:j + 3] = (u[:, q].T - ub) / us
+                j += 3
+    feats[:, 81] = dist[near]
+    feats[:, 82:85] = feats[:, 39:42]
+    assert np.abs(Xg - feats).max() < 1e-6 * np.abs(feats).max()
+    # dissipation with the closure
+    w = M.init(5).astype(np.float32)
+    g.closure_set_weights(w, us, gs)
+    sg = g.stats(lbm.STATS_CLOSURE)
+    so = o.stats(0)
+    um = o.masked_velocity(0)
+    nu = (tau - 0.5) / 3.0
+
+    def eps_fd(c):
+        x, y, z = c % n, (c // n) % n, c // (n * n)
+        G = np.zeros((len(c), 3, 3))
+        for b, (ex, ey, ez) in enumerate(((1, 0, 0), (0, 1, 0), (0, 0, 1))):
+            qp = (x + ex) % n + n * (((y + ey) % n) + n * ((z + ez) % n))
+            qm = (x - ex) % n + n * (((y - ey) % n) + n * ((z - ez) % n))
+            G[:, :, b] = 0.5 * (um[:, qp] - um[:, qm]).T
+        S = 0.5 * (G + G.transpose(0, 2, 1))
+        return 2 * nu * (S ** 2).sum(axis=(1, 2))
+
+    Y, _ = M.forward_tc(w, feats.astype(np.float32))
+    G = (Y / gs).reshape(-1, 3, 3)
+    S = 0.5 * (G + G.transpose(0, 2, 1))
+    eps_cl = 2 * nu * (S ** 2).sum(axis=(1, 2))
+    expect = so["dissipation"] + (eps_cl - eps_fd(near)).sum() / n ** 3
+    assert abs(expect - so["dissipation"]) > 1e-3 * so["dissipation"]  # the closure changes it
+    assert sg["dissipation"] == pytest.approx(expect, rel=2e-4)
+    g.close()

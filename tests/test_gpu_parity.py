@@ -171,9 +171,13 @@ def test_moving_spheres_ibb_f64(lbm):
         s.add_spheres(X, 3.5, density_ratio=1.5)
     Pg, Po = g.particles(), o.particles()
     assert rel(Pg["U"], Po["U"]) < 1e-12  # release velocity
+    refilled = 0
     for _ in range(3):
         g.step(10, lbm.BC_IBB)
-        o.step(10, oracle.BC_IBB)
+        for _ in range(10):  # the oracle one step at a time, counting uncovered nodes
+            before = o.solid()[0]
+            o.step(1, oracle.BC_IBB)
+            refilled += int(((before == 1) & (o.solid()[0] == 0)).sum())
         Pg, Po = g.particles(), o.particles()
         for k in ("X", "U", "W"):
             assert np.max(np.abs(Pg[k] - Po[k])) < 1e-11 * max(1.0, np.max(np.abs(Po[k]))), k
@@ -181,6 +185,7 @@ def test_moving_spheres_ibb_f64(lbm):
         fluid = o.solid()[0] == 0
         assert np.array_equal(g.flags() & 1, o.solid()[0])
         assert rel(g.populations()[:, fluid], o.populations()[:, fluid]) < 1e-11
+    assert refilled > 0
     # positions now differ in the last bits (forces summed in another order),
     # so q can differ in the last bits too; the list itself must agree
     _links_equal(g.links(), o.links(), q_exact=False)
@@ -194,7 +199,7 @@ def test_moving_spheres_ibb_f64(lbm):
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_pipe_ibb_150_steps(lbm, storage, tol):
+def test_pipe_ibb_200_steps(lbm, storage, tol):
     """Pipe wall by interpolated bounce-back: rows of up to 43 fluid cells,
     i.e. two ragged sweep segments per row, plus the z-periodic ends."""
     nx, ny, nz, R = 47, 46, 12, 21.5
@@ -204,14 +209,15 @@ def test_pipe_ibb_150_steps(lbm, storage, tol):
     for s in (g, o):
         s.init_velocity(u)
         s.set_pipe(R)
-    g.step(150, lbm.BC_IBB)
-    o.step(150, oracle.BC_IBB)
+    g.step(200, lbm.BC_IBB)
+    o.step(200, oracle.BC_IBB)
     fluid = o.solid()[0] == 0  # solid cells hold ghost values on the GPU
     assert rel(g.populations()[:, fluid], o.populations()[:, fluid]) < tol
     rg, ug = g.macro()
     ro, uo = o.macro()
     assert rel(ug[:, fluid], uo[:, fluid]) < tol
     assert rel(rg[fluid], ro[fluid]) < tol
+    assert rel(rg[fluid] - 1.0, ro[fluid] - 1.0) < 100 * tol
 
 
 @pytest.mark.parametrize("bc,nz", [("ibm_u", 4), ("ibm_b", 4), ("ibm_b", 31)])
@@ -235,7 +241,7 @@ def test_pipe_ibm_f64(lbm, bc, nz):
 
 
 @pytest.mark.parametrize("bc", ["ibm_u", "ibm_b"])
-def test_pipe_ibm_f32_150_steps(lbm, bc):
+def test_pipe_ibm_f32_200_steps(lbm, bc):
     """Pipe wall by IBM in FP32 storage: an odd row length (warps of the box
     sweep cross row ends), support cells collided in place after the three
     passes, and the pipe's interpolation and spreading on five z tiles."""
@@ -245,8 +251,8 @@ def test_pipe_ibm_f32_150_steps(lbm, bc):
     for s in (g, o):
         s.init_velocity(u)
         s.set_pipe(R)
-    g.step(150, lbm.BC[bc])
-    o.step(150, oracle.BC_IBM_U if bc == "ibm_u" else oracle.BC_IBM_B)
+    g.step(200, lbm.BC[bc])
+    o.step(200, oracle.BC_IBM_U if bc == "ibm_u" else oracle.BC_IBM_B)
     rg, ug = g.macro()
     ro, uo = o.macro()
     assert rel(ug, uo) < 1e-5
@@ -293,14 +299,16 @@ def test_moving_spheres_ibb_f32_within_tolerance(lbm):
     for s in (g, o):
         s.init_velocity(u)
         s.add_spheres(X, 4.0, density_ratio=5.0)
-    g.step(50, lbm.BC_IBB)
-    o.step(50, oracle.BC_IBB)
+    g.step(200, lbm.BC_IBB)
+    o.step(200, oracle.BC_IBB)
     fluid = (o.solid()[0] == 0) & ((g.flags() & 1) == 0)
     rg, ug = g.macro()
     ro, uo = o.macro()
     assert rel(ug[:, fluid], uo[:, fluid]) < 1e-5
+    assert rel(rg[fluid], ro[fluid]) < 1e-5
     Pg, Po = g.particles(), o.particles()
     assert rel(Pg["U"], Po["U"]) < 1e-5
+    assert rel(Pg["W"], Po["W"]) < 1e-5
 
 
 @pytest.mark.parametrize("storage,tol", [("f16s", 2e-3), ("bf16s", 3e-2)])
@@ -338,3 +346,100 @@ def test_16bit_storage_ragged_rows_and_pipe(lbm, storage, tol):
     o.step(100, oracle.BC_IBB)
     fluid = o.solid()[0] == 0
     assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol
+
+
+def test_moving_spheres_ibm_b_f32_200_steps(lbm):
+    """The particle-laden IBM-B step in FP32 storage (the benchmark's HIT
+    path) over 200 steps: velocity, density and the particles' motion."""
+    n = 32
+    X = workloads.place_spheres((n, n, n), 3, 4.0, 2.0, seed=21)
+    u = workloads.hit_velocity(n, seed=8, k_peak=3.0, u_rms=0.03)
+    g, o = pair(lbm, (n, n, n), 0.55, storage=lbm.F32, rates=oracle.RATES_DHUMIERES, max_particles=3)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.add_spheres(X, 4.0, density_ratio=5.0)
+    g.step(200, lbm.BC_IBM_B)
+    o.step(200, oracle.BC_IBM_B)
+    rg, ug = g.macro()
+    ro, uo = o.macro()
+    assert rel(ug, uo) < 1e-5
+    assert rel(rg, ro) < 1e-5
+    Pg, Po = g.particles(), o.particles()
+    for k in ("U", "W"):
+        assert rel(Pg[k], Po[k]) < 1e-5, k
+    assert np.max(np.abs(Pg["X"] - Po["X"])) < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["ibb", "ibm_b"])
+def test_soft_sphere_contact(lbm, bc):
+    """Two spheres of density ratio 5, 0.5 lu apart and closing: the normal
+    spring-dashpot contact (margin 1 lu) acts from the first step and turns
+    them back; positions and velocities match the oracle through the
+    collision."""
+    n = 32
+    X = np.array([[11.25, 16.0, 15.7], [19.75, 16.3, 16.1]])  # centres 8.5 + apart, radii 4: gap ~0.5
+    U = np.array([[0.02, 0.0, 0.0], [-0.02, 0.0, 0.0]])
+    u = workloads.noise_velocity((n, n, n), 1e-3, seed=1)
+    g, o = pair(lbm, (n, n, n), 0.6, rates=oracle.RATES_DHUMIERES, max_particles=2)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.add_spheres(X, 4.0, density_ratio=5.0, U=U, W=np.zeros((2, 3)))
+    d0 = np.linalg.norm(X[1] - X[0]) - 8.0
+    assert d0 < 1.0  # inside the contact margin at the start
+    obc = oracle.BC_IBB if bc == "ibb" else oracle.BC_IBM_B
+    vrel = []
+    for _ in range(6):
+        g.step(5, lbm.BC[bc])
+        o.step(5, obc)
+        Pg, Po = g.particles(), o.particles()
+        for k in ("X", "U", "W"):
+            assert np.max(np.abs(Pg[k] - Po[k])) < 1e-10 * max(1.0, np.max(np.abs(Po[k]))), k
+        vrel.append(Po["U"][1, 0] - Po["U"][0, 0])
+    assert vrel[0] < 0 and vrel[-1] > 0  # closing at first, separating after the contact
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_single_node_fallback_between_close_spheres(lbm, storage, tol):
+    """Two fixed spheres 0.6 lu apart: links in the gap whose upstream node
+    is solid take the single-node scheme; with a body force and a random
+    flow the GPU matches the oracle."""
+    n = 20
+    X = np.array([[6.3, 10.1, 9.7], [12.1, 10.4, 9.9]])
+    g, o = pair(lbm, (n, n, n), 0.6, force=(1e-5, 2e-6, 0), storage=lbm.STORAGE[storage],
+                rates=oracle.RATES_DHUMIERES, max_particles=2)
+    u = workloads.hit_velocity(n, seed=3, k_peak=2.0, u_rms=0.01)
+    z = np.zeros((2, 3))
+    for s in (g, o):
+        s.init_velocity(u)
+        s.add_spheres(X, 2.6, U=z, W=np.array([[0, 0, 0.01], [0.005, 0, 0]]), fixed=True)
+    L = o.links()
+    assert (L["scheme"] == oracle.SCHEME_SINGLE).sum() >= 10
+    _links_equal(g.links(), o.links())
+    g.step(60, lbm.BC_IBB)
+    o.step(60, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0
+    assert rel(g.populations()[:, fluid], o.populations()[:, fluid]) < tol
+    Fg, Fo = g.particles(), o.particles()
+    assert rel(Fg["F"], Fo["F"]) < (1e-10 if storage == "f64" else 1e-4)
+    assert rel(Fg["T"], Fo["T"]) < (1e-10 if storage == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16s", 3e-2)])
+def test_single_node_fallback_on_pipe_wall(lbm, storage, tol):
+    """A pipe of radius 6.4 in a 16 x 16 section has wall links whose
+    upstream node is outside the pipe (8 per plane): the static wall's ghost
+    pass evaluates the single-node scheme from the wall cell's kept
+    values."""
+    nx, ny, nz, R = 16, 16, 6, 6.4
+    g, o = pair(lbm, (nz, ny, nx), 0.6, force=(0, 0, 5e-6), storage=lbm.STORAGE[storage])
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.01, perturbation=0.1, seed=2)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.set_pipe(R)
+    assert (o.links()["scheme"] == oracle.SCHEME_SINGLE).sum() == 8 * nz
+    g.step(200, lbm.BC_IBB)
+    o.step(200, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0
+    rg, ug = g.macro()
+    ro, uo = o.macro()
+    assert rel(ug[:, fluid], uo[:, fluid]) < tol
