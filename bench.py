@@ -182,6 +182,30 @@ def hit_setup(n, n_particles, seed=0):
     return dict(init=init, max_particles=n_particles)
 
 
+def config4_report(lbm, torch, n=512, n_particles=16000, steps=10, warmup=3):
+    """512^3 particle-laden box with 16000 moving spheres of radius 4 (the
+    3.2 % volume fraction of the 256^3 / 2000-sphere case), IBB, d'Humieres
+    rates, tau = 0.51, under FP32, FP16 and BF16 population storage on the
+    same GPU: MLUPS, step time, the bulk sweep's algorithmic GB/s. The
+    initial field is the 256^3 synthetic HIT field tiled 2 x 2 x 2 (periodic
+    and divergence-free; it sets the flow, not the throughput)."""
+    u = np.tile(workloads.hit_velocity(n // 2, seed=0, k_peak=8.0, u_rms=0.03), (1, 2, 2, 2))
+    X = workloads.place_spheres((n, n, n), n_particles, 4.0, 1.0, seed=0)
+    setup = dict(init=lambda L: (L.init_velocity(u), L.add_spheres(X, 4.0, density_ratio=5.0)),
+                 max_particles=n_particles)
+    out = {"workload": f"{n}^3 D3Q19, {n_particles} moving spheres R=4, IBB, MRT, tau=0.51, {steps} steps"}
+    for name, st in (("f32", lbm.F32), ("f16s", lbm.F16S), ("bf16s", lbm.BF16S)):
+        r = run_case(lbm, torch, "config4_" + name, n, n, n, 0.51, (0, 0, 0), st, lbm.RATES_DHUMIERES, lbm.BC_IBB,
+                     steps, warmup, setup)
+        p = r["prof"]
+        bms = p["ms"]["bulk"] / max(1, p["spans"]["bulk"])
+        out[name] = {"mlups": round(r["mlups"], 1), "ms_per_step": round(r["ms"] / r["steps"], 4),
+                     "bulk_kernel_gbs": round(r["bulk_bytes"] / (bms * 1e-3) / 1e9, 1),
+                     "group_ms_per_step": {k: round(v / r["steps"], 4) for k, v in p["ms"].items() if v > 0},
+                     "finite": r["finite"]}
+    return out
+
+
 def precision_report(lbm, torch, n=64, n_particles=31, steps=200):
     """Population storage precision against FP64 storage (which matches the
     FP64 oracle to 1e-12) on the 64^3 particle-laden box: 31 spheres of
@@ -263,29 +287,32 @@ def budget_report(lbm, torch, nbins=64, steps=20, reps=5):
             "finite": bool(np.all(np.isfinite(B)))}
 
 
-def q27_report(lbm, torch, n=256, steps=50, warmup=5):
-    """D3Q27 periodic box (the velocity set of the paper's pipe solver), FP32,
-    BGK with a body force, on the HIT field: time per step from CUDA events
-    on the library's stream, MLUPS, and the sweep's algorithmic bandwidth
-    (27 x 4 B read and 27 x 4 B written per cell)."""
-    u = workloads.hit_velocity(n, seed=0, k_peak=8.0, u_rms=0.03, dtype=np.float64)
-    L = lbm.Lattice(n, n, n, 0.6, force=(1e-6, 0, 0), storage=lbm.F32, lattice=27)
-    L.init_velocity(u)
-    L.step(warmup)
+def q27_report(lbm, torch, steps=200, warmup=10):
+    """D3Q27 (the velocity set of the paper's pipe solver), FP32, BGK, on the
+    benchmark pipe 148x148x438 with its linear IBB wall inside the sweep and
+    the Re_tau = 180 body force: time per step from CUDA events on the
+    library's stream, MLUPS over the fluid cells, and the sweep's
+    algorithmic bandwidth (27 x 4 B read and 27 x 4 B written per fluid
+    cell)."""
+    nx, ny, nz = PIPE["nx"], PIPE["ny"], NZ
+    L = lbm.Lattice(nx, ny, nz, PP["tau"], force=(0, 0, PP["g"]), storage=lbm.F32, lattice=27)
+    L.init_velocity(pipe_field())
+    L.set_pipe(PIPE["radius"])
+    fluid = int(np.count_nonzero((L.flags() & 1) == 0))
+    L.step(warmup, lbm.BC_IBB)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(L.stream)
-    L.step(steps)
+    L.step(steps, lbm.BC_IBB)
     e1.record(L.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     _, v = L.macro()
     finite = bool(np.all(np.isfinite(v)))
     L.close()
-    cells = n ** 3
-    return {"grid": f"{n}^3", "storage": "f32", "steps": steps, "ms_per_step": round(ms, 4),
-            "mlups": round(cells / (ms * 1e-3) / 1e6, 1),
-            "algorithmic_gbs": round(2 * 27 * 4 * cells / (ms * 1e-3) / 1e9, 1), "finite": finite}
+    return {"workload": f"pipe D=146 in {nx}x{ny}x{nz} D3Q27, linear IBB wall", "storage": "f32", "steps": steps,
+            "ms_per_step": round(ms, 4), "mlups": round(fluid / (ms * 1e-3) / 1e6, 1),
+            "algorithmic_gbs": round(2 * 27 * 4 * fluid / (ms * 1e-3) / 1e9, 1), "finite": finite}
 
 
 def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
@@ -424,6 +451,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=PIPE["nz"],
                     help="pipe length in cells (default 438; shorter only for profiler captures)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16s", "bf16s"],
+                    help="population storage of the main line (default f32; 16-bit only for profiler captures, "
+                         "whose line is then not the benchmark's)")
     ap.add_argument("--wall", default="ibb", choices=["ibb", "ibm_b"],
                     help="wall treatment of the main line (default ibb; ibm_b only for profiler captures "
                          "of the IBM step, whose line is then not the benchmark's)")
@@ -476,8 +506,9 @@ def main():
     torch.cuda.synchronize()
     clocks = Clocks(dev)
     main_bc = lbm.BC_IBB if args.wall == "ibb" else lbm.BC_IBM_B
-    main_res = run_case(lbm, torch, "pipe_" + args.wall + "_f32", PIPE["nx"], PIPE["ny"], NZ, PP["tau"],
-                        (0, 0, PP["g"]), lbm.F32, lbm.RATES_SRT, main_bc, args.steps, args.warmup, setup)
+    main_res = run_case(lbm, torch, "pipe_" + args.wall + "_" + args.storage, PIPE["nx"], PIPE["ny"], NZ, PP["tau"],
+                        (0, 0, PP["g"]), lbm.STORAGE[args.storage], lbm.RATES_SRT, main_bc, args.steps, args.warmup,
+                        setup)
     clk = clocks.stop()
     ms_total = main_res["ms"]
     if dist:
@@ -513,12 +544,17 @@ def main():
                               "finite": r["finite"]}
 
     precision = None
+    config4 = None
     closure_res = None
     spectrum_res = None
     budget_res = None
     q27_res = None
     if not args.no_variants and rank == 0:
         precision = precision_report(lbm, torch)
+        try:
+            config4 = config4_report(lbm, torch)
+        except Exception as ex:  # a variant's failure must not lose the line
+            config4 = {"error": str(ex)[:200]}
         closure_res = closure_report(lbm, torch)
         spectrum_res = spectrum_report(lbm, torch)
         try:
@@ -552,9 +588,9 @@ def main():
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "f32",  # the collision arithmetic; the storage is in config
             "data": "synthetic",
-            "config": {"workload": f"pipe D=146 L={NZ} in 148x148x{NZ} D3Q19, FP32 populations, SRT, nu=0.0032, "
+            "config": {"workload": f"pipe D=146 L={NZ} in 148x148x{NZ} D3Q19, {args.storage.upper()} populations, SRT, nu=0.0032, "
                                    "Re_tau=180 body force, " + ("linear IBB wall" if args.wall == "ibb" else "IBM-B wall"),
                        "fluid_cells": main_res["fluid_cells"], "parallelism": f"replicas x{world}",
                        "l2": "no flush: populations 2x1.46 GB >> 129 MB L2"},
@@ -563,7 +599,9 @@ def main():
                          "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind,
                          "traffic": traffic_for("stream_collide_bulk_pipe_f32") if args.wall == "ibb" else None,
                          "algorithmic_bytes_per_launch": bulk_bytes,
-                         "avg_launch_ms": round(bulk_ms, 5)},
+                         "avg_launch_ms": round(bulk_ms, 5),
+                         "step_achieved": round(bulk_bytes / (ms_total / args.steps * 1e-3) / 1e9, 1),
+                         "step_frac": round(bulk_bytes / (ms_total / args.steps * 1e-3) / 1e9 / hbm_peak, 4)},
             "group_ms_per_step": {k: round(v / args.steps, 4) for k, v in prof["ms"].items() if v > 0},
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -571,6 +609,7 @@ def main():
             "cpu_baseline": cpu,
             "variants": variants,
             "precision_vs_f64": precision,
+            "config4": config4,
             "closure": closure_res,
             "spectrum": spectrum_res,
             "tke_budget": budget_res,

@@ -1,5 +1,6 @@
-// Learned near-surface gradient closure: an 85-64-64-64-9 ReLU perceptron on
-// tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation).
+// Learned near-surface gradient closure: an 85-64-64-64-9 ReLU perceptron.
+// Training on tensor cores with mma.sync m16n8k16 (BF16 operands, FP32
+// accumulation); inference runs on tcgen05 (closure_tc.cu).
 //
 // The paper has no closure; it motivates one: inside IBM's diffused
 // interface the velocity gradients, hence the dissipation, come out too low
@@ -169,28 +170,6 @@ __device__ __forceinline__ void load_params(const __nv_bfloat16 *pk, const float
         sb[i] = v;
     }
     __syncthreads();
-}
-
-__global__ void __launch_bounds__(128) mlp_forward_kernel(const float *X, long long n, const float *w,
-                                                          const __nv_bfloat16 *pk, float *Y) {
-    __shared__ __nv_bfloat16 sw[PK_FWD];
-    __shared__ float sb[208];
-    load_params(pk, w, sw, sb, PK_FWD);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long tiles = (n + 15) / 16;
-    for (long long t = (long long)blockIdx.x * 4 + warp; t < tiles; t += (long long)gridDim.x * 4) {
-        float h1[8][4], h2[8][4], h3[8][4], y[2][4];
-        warp_forward(X, n, t * 16, sw, sb, lane, h1, h2, h3, y);
-        const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-        for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const int col = nt * 8 + tig * 2 + (e & 1);
-                const long long row = t * 16 + gid + ((e & 2) ? 8 : 0);
-                if (col < MOUT && row < n) Y[row * MOUT + col] = y[nt][e];
-            }
-    }
 }
 
 // --------------------------------------------------------------- training --
@@ -407,10 +386,11 @@ namespace {
 struct MlpWs {
     __nv_bfloat16 *pk;
     float *m, *v, *gpart, *lpart;
+    int *err;  // set by the tensor-core forward when a wait runs out
 };
 size_t mlp_ws_bytes() {
     return (((size_t)PK_TOTAL * 2 + 255) / 256) * 256 + 2 * (((size_t)NPARAM * 4 + 255) / 256) * 256 +
-           (((size_t)TRAIN_BLOCKS * NPARAM * 4 + 255) / 256) * 256 + 256 * 4;
+           (((size_t)TRAIN_BLOCKS * NPARAM * 4 + 255) / 256) * 256 + 256 * 4 + 256;
 }
 MlpWs mlp_ws(void *ws) {
     char *b = (char *)ws;
@@ -425,6 +405,8 @@ MlpWs mlp_ws(void *ws) {
     W.gpart = (float *)(b + o);
     o += (((size_t)TRAIN_BLOCKS * NPARAM * 4 + 255) / 256) * 256;
     W.lpart = (float *)(b + o);
+    o += 256 * 4;
+    W.err = (int *)(b + o);
     return W;
 }
 cudaError_t mlp_pack(const float *w, __nv_bfloat16 *pk, cudaStream_t s) {
@@ -443,16 +425,8 @@ cudaError_t set_train_smem() {
 }  // namespace
 
 namespace lbmgb {
-cudaError_t mlp_forward_device(const float *X, long long n, const float *w, void *pk_ws, float *Y, cudaStream_t s) {
-    __nv_bfloat16 *pk = (__nv_bfloat16 *)pk_ws;
-    cudaError_t e = mlp_pack(w, pk, s);
-    if (e != cudaSuccess) return e;
-    if (n == 0) return cudaSuccess;
-    long long nb = ((n + 15) / 16 + 3) / 4;
-    if (nb > 152 * 16) nb = 152 * 16;
-    mlp_forward_kernel<<<(unsigned)nb, 128, 0, s>>>(X, n, w, pk, Y);
-    return cudaGetLastError();
-}
+// BF16 operand copies of the FP32 parameters (the layout described at the top)
+cudaError_t mlp_pack_device(const float *w, void *pk, cudaStream_t s) { return mlp_pack(w, (__nv_bfloat16 *)pk, s); }
 size_t mlp_pack_bytes() { return (size_t)PK_TOTAL * 2; }
 }  // namespace lbmgb
 
@@ -466,7 +440,16 @@ lbm_status lbm_mlp_forward(const float *X_dev, long long n, const float *w_dev, 
     if (!X_dev || !w_dev || !Y_dev || !ws || n < 0) return LBM_EINVAL;
     if (bytes < mlp_ws_bytes()) return LBM_ENOMEM;
     MlpWs W = mlp_ws(ws);
-    return mlp_forward_device(X_dev, n, w_dev, W.pk, Y_dev, (cudaStream_t)stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // tensor-core inference (closure_tc.cu); synchronous: the completion word is checked
+    if (cudaMemsetAsync(W.err, 0, sizeof(int), s) != cudaSuccess || mlp_pack(w_dev, W.pk, s) != cudaSuccess ||
+        mlp_forward_tc(X_dev, n, w_dev, W.pk, Y_dev, W.err, s) != cudaSuccess)
+        return LBM_ECUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, W.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LBM_ECUDA;
+    return err ? LBM_ETIMEOUT : LBM_OK;
 }
 
 lbm_status lbm_mlp_loss_grad(const float *X_dev, const float *T_dev, long long n, const float *w_dev, float *grad_dev,

@@ -1,0 +1,405 @@
+// Learned closure inference on the fifth-generation tensor cores (tcgen05),
+// fused with the near-surface dissipation diagnostic.
+//
+// The closure (an 85-64-64-64-9 ReLU perceptron, see closure.cu) maps the
+// IBM velocity stencil around a near-surface node to its 9 velocity
+// gradients; the paper motivates it by IBM's underestimated dissipation
+// inside the diffused interface (Sec. 3.2, Sec. 4).
+//
+// One CTA of 256 threads works on tiles of 128 samples (the MMA's M):
+// - inputs: either 85 FP32 features per sample read from memory
+//   (lbm_mlp_forward), or, fused, gathered from an FP32 copy of the
+//   velocity field at the listed near-surface cells (the 27-point stencil
+//   of u - u_rb, the distance to the surface, u - u_rb at the node) -- no
+//   feature array in HBM; rounded to BF16 into shared memory;
+// - four layers, each: one elected thread issues tcgen05.mma (kind::f16,
+//   BF16 operands from shared memory, FP32 accumulators in tensor memory)
+//   over K in steps of 16 and commits to an mbarrier; the 8 warps read the
+//   accumulators back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4)..,
+//   columns 32 (w / 4)..), add the FP32 bias, apply ReLU and write the next
+//   layer's BF16 operand;
+// - output: the 9 gradients (FP32), or, fused, the dissipation
+//   2 nu s_ij s_ij of the predicted gradients at the cell.
+// Operands use the no-swizzle K-major layout of 8 x 8 BF16 core matrices
+// (128 B each): consecutive along K 128 B apart, along the rows K/8 x 128 B
+// apart. The weights are the BF16 operand copies of closure.cu's packed
+// block, rearranged into that layout once per CTA.
+// Every wait on the mbarrier is bounded; a wait that runs out sets an error
+// word, and the kernel frees its tensor memory and returns.
+#include "lbm_internal.cuh"
+
+namespace lbmgb {
+
+size_t mlp_pack_bytes();
+
+namespace {
+
+constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16, TC_THREADS = 256;
+constexpr int TC_IN = 85, TC_H = 64, TC_OUT = 9;
+// packed operand block of closure.cu: WT_l [out_pad][in_pad] (BF16)
+constexpr int PW1 = 0, PW2 = PW1 + TC_H * TK1, PW3 = PW2 + TC_H * TC_H, PW4 = PW3 + TC_H * TC_H;
+// flat FP32 parameter offsets of the biases
+constexpr int OB1 = TC_IN * TC_H, OB2 = OB1 + TC_H + TC_H * TC_H, OB3 = OB2 + TC_H + TC_H * TC_H,
+              OB4 = OB3 + TC_H + TC_H * TC_OUT;
+constexpr long long TC_WAIT_LIMIT = 1LL << 24;  // polls of the mbarrier before giving up
+
+struct __align__(128) TcSmem {
+    unsigned short w1[TC_H * TK1];
+    unsigned short w2[TC_H * TKH];
+    unsigned short w3[TC_H * TKH];
+    unsigned short w4[TN4 * TKH];
+    unsigned short a[TM * TK1];  // the layer input (K = 96 for layer 1, 64 after)
+    float b[208];                // b1 @0, b2 @64, b3 @128, b4 @192 (9 used)
+    unsigned long long mbar;
+    unsigned taddr;
+    int err;
+};
+
+// element offset of (row r, column k) in the core-matrix layout of a K-wide operand
+__device__ __forceinline__ int cm(int r, int k, int K) { return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row
+// group) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((smem_u32(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(void *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_wait(void *mbar, uint32_t parity) {
+    const uint32_t m = smem_u32(mbar);
+    for (long long it = 0; it < TC_WAIT_LIMIT; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(m), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t t, float v[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(t));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t t, float v[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(t));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ unsigned bf2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+// 8 values of one core-matrix row as one 16-byte store
+__device__ __forceinline__ void put8(unsigned short *base, int off, const float *v) {
+    *reinterpret_cast<uint4 *>(base + off) = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
+}
+
+__device__ __forceinline__ int twrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ double tmimg(double d, int n) {
+    if (d > 0.5 * n) d -= n;
+    else if (d < -0.5 * n) d += n;
+    return d;
+}
+
+}  // namespace
+
+struct TcArgs {
+    const float *X;           // features (n x 85), or null: gather from the field
+    float *Y;                 // outputs (n x 9), or null: dissipation at the cells
+    const long long *count;   // device sample count (fused), else null
+    long long n, cap;
+    const float *w;           // FP32 parameters (biases)
+    const unsigned short *pk; // packed BF16 operand block
+    // fused: near-surface cells and their nearest particle
+    const int *cells, *pid;
+    const float *u;  // FP32 copy of the velocity field (3 planes of N)
+    const double *Xp, *Up, *Wp, *Rp;
+    int nx, ny, nz;
+    long long N;
+    double inv_us, inv_gs, nu;
+    float *eps_o;
+    int *err;
+};
+
+// The features of one sample, columns [48 h, 48 h + 48) for half h, BF16
+// into row `row` of the layer-1 operand, 8 columns at a time. FP32 is
+// ample here: the features are rounded to BF16 (8 bits) at once, and only
+// the offset to the particle centre is formed in FP64 (positions reach
+// 2^9, where FP32 would keep 1e-4 of a lattice unit).
+template <int H>
+__device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigned short *A, int row) {
+    const int c = a.cells[s], p = a.pid[s];
+    const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
+    const float rx = (float)tmimg(x - a.Xp[3 * p], a.nx), ry = (float)tmimg(y - a.Xp[3 * p + 1], a.ny),
+                rz = (float)tmimg(z - a.Xp[3 * p + 2], a.nz);
+    const float U0 = (float)a.Up[3 * p], U1 = (float)a.Up[3 * p + 1], U2 = (float)a.Up[3 * p + 2];
+    const float W0 = (float)a.Wp[3 * p], W1 = (float)a.Wp[3 * p + 1], W2 = (float)a.Wp[3 * p + 2];
+    const float ius = (float)a.inv_us;
+    const long long N = a.N;
+    float buf[8];
+    int fill = 0, col = 48 * H;
+    auto push = [&](float v) {
+        buf[fill++] = v;
+        if (fill == 8) {
+            put8(A, cm(row, col, TK1), buf);
+            col += 8;
+            fill = 0;
+        }
+    };
+    auto rel = [&](int j) {  // u - u_rb at stencil point j (dz, dy, dx in -1..1, dz outermost)
+        const int dx = j % 3 - 1, dy = (j / 3) % 3 - 1, dz = j / 9 - 1;
+        const long long q = (long long)twrap(x + dx, a.nx) + (long long)a.nx * (twrap(y + dy, a.ny) + (long long)a.ny * twrap(z + dz, a.nz));
+        const float sx = rx + (float)dx, sy = ry + (float)dy, sz = rz + (float)dz;
+        const float u0 = __ldg(a.u + q), u1 = __ldg(a.u + N + q), u2 = __ldg(a.u + 2 * N + q);
+        push((u0 - (U0 + (W1 * sz - W2 * sy))) * ius);
+        push((u1 - (U1 + (W2 * sx - W0 * sz))) * ius);
+        push((u2 - (U2 + (W0 * sy - W1 * sx))) * ius);
+    };
+    if constexpr (H == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) rel(j);  // columns 0..47
+    } else {
+#pragma unroll
+        for (int j = 16; j < 27; j++) rel(j);  // columns 48..80
+        push(sqrtf(rx * rx + ry * ry + rz * rz) - (float)a.Rp[p]);
+        rel(13);  // the node itself again: columns 82..84
+#pragma unroll
+        for (int k = 85; k < 96; k++) push(0.f);
+    }
+}
+
+#ifndef LBM_TC_CTAS
+#define LBM_TC_CTAS 2  // CTAs per SM (each takes 128 of the 512 tensor-memory columns)
+#endif
+
+template <bool FIELD>
+__global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(tc_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long n = FIELD ? (*a.count < a.cap ? *a.count : a.cap) : a.n;
+    const long long tiles = (n + TM - 1) / TM;
+    if ((long long)blockIdx.x >= tiles) return;  // the whole block leaves before any tensor memory is taken
+    // weights into the core-matrix layout, biases
+    for (int e = tid; e < TC_H * TK1; e += TC_THREADS) S.w1[cm(e / TK1, e % TK1, TK1)] = a.pk[PW1 + e];
+    for (int e = tid; e < TC_H * TKH; e += TC_THREADS) {
+        S.w2[cm(e / TKH, e % TKH, TKH)] = a.pk[PW2 + e];
+        S.w3[cm(e / TKH, e % TKH, TKH)] = a.pk[PW3 + e];
+    }
+    for (int e = tid; e < TN4 * TKH; e += TC_THREADS) S.w4[cm(e / TKH, e % TKH, TKH)] = a.pk[PW4 + e];
+    for (int i = tid; i < 208; i += TC_THREADS) {
+        float v = 0.f;
+        if (i < 64) v = a.w[OB1 + i];
+        else if (i < 128) v = a.w[OB2 + i - 64];
+        else if (i < 192) v = a.w[OB3 + i - 128];
+        else if (i - 192 < TC_OUT) v = a.w[OB4 + i - 192];
+        S.b[i] = v;
+    }
+    if (tid == 0) {
+        S.err = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&S.taddr))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t T0 = S.taddr;                               // columns 0..63 and 64..127 of this CTA
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int row = 32 * (warp & 3) + lane;                    // this thread's sample row in the tile
+    const int half = warp >> 2;                                // its column half in the epilogues
+    uint32_t parity = 0;
+    bool ok = true;
+    // one layer: MMA over K into TMEM column base tc, then the epilogue of
+    // 32 columns per thread into the next operand (K = 64)
+    auto run_layer = [&](const unsigned short *w, int K, uint32_t tc, int N) {
+        if (tid == 0) {
+            fence_after();
+            const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+            for (int s = 0; s < K / 16; s++)
+                tc_mma(T0 + tc, sdesc(S.a + 128 * s, 128u, sbo), sdesc(w + 128 * s, 128u, sbo), idesc_bf16(TM, N),
+                       s > 0 ? 1u : 0u);
+            tc_commit(&S.mbar);
+        }
+        if (!mbar_wait(&S.mbar, parity)) ok = false;
+        parity ^= 1u;
+        fence_after();
+    };
+    auto hidden_out = [&](uint32_t tc, int boff) {
+        float v[32];
+        tmem_ld32(T0 + lane_base + tc + 32 * half, v);
+        const int c0 = 32 * half;
+#pragma unroll
+        for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + S.b[boff + c0 + j], 0.f);
+        fence_before();
+        __syncthreads();  // every warp has read the accumulators and the previous operand is no longer read
+#pragma unroll
+        for (int g = 0; g < 4; g++) put8(S.a, cm(row, c0 + 8 * g, TKH), v + 8 * g);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+    };
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long s = tile * TM + row;
+        // layer-1 operand: 85 features (BF16), zero padding to 96, zero rows past n
+        {
+            const int k0 = 48 * half;
+            if (FIELD && s < n) {
+                if (half == 0) gather_put<0>(a, s, S.a, row);
+                else gather_put<1>(a, s, S.a, row);
+            } else {
+                float f[48];
+#pragma unroll
+                for (int k = 0; k < 48; k++) f[k] = (!FIELD && s < n && k0 + k < TC_IN) ? a.X[s * TC_IN + k0 + k] : 0.f;
+#pragma unroll
+                for (int g = 0; g < 6; g++) put8(S.a, cm(row, k0 + 8 * g, TK1), f + 8 * g);
+            }
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        run_layer(S.w1, TK1, 0, TC_H);
+        if (!ok) break;
+        hidden_out(0, 0);
+        run_layer(S.w2, TKH, 64, TC_H);
+        if (!ok) break;
+        hidden_out(64, 64);
+        run_layer(S.w3, TKH, 0, TC_H);
+        if (!ok) break;
+        hidden_out(0, 128);
+        run_layer(S.w4, TKH, 64, TN4);
+        if (!ok) break;
+        if (half == 0) {
+            float y[16];
+            tmem_ld16(T0 + lane_base + 64, y);
+            if (s < n) {
+#pragma unroll
+                for (int j = 0; j < TC_OUT; j++) y[j] += S.b[192 + j];
+                if constexpr (FIELD) {
+                    double ss = 0.0;
+#pragma unroll
+                    for (int p = 0; p < 3; p++)
+#pragma unroll
+                        for (int q = 0; q < 3; q++) {
+                            const double sab = 0.5 * ((double)y[3 * p + q] + (double)y[3 * q + p]) * a.inv_gs;
+                            ss += sab * sab;
+                        }
+                    a.eps_o[a.cells[s]] = (float)(2.0 * a.nu * ss);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TC_OUT; j++) a.Y[s * TC_OUT + j] = y[j];
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();  // the next tile rewrites the operand and the accumulators
+    }
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(T0) : "memory");
+}
+
+static cudaError_t tc_launch(const TcArgs &a, bool field, long long max_tiles, cudaStream_t s) {
+    static bool attr = false;
+    const int smem = (int)sizeof(TcSmem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long nb = (long long)LBM_TC_CTAS * (sms > 0 ? sms : 1);
+    if (nb > max_tiles) nb = max_tiles;
+    if (nb < 1) nb = 1;
+    if (field) mlp_tc_kernel<true><<<(unsigned)nb, TC_THREADS, smem, s>>>(a);
+    else mlp_tc_kernel<false><<<(unsigned)nb, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Y (n x 9) = network(X (n x 85)); pk: the packed BF16 operand block of w.
+cudaError_t mlp_forward_tc(const float *X, long long n, const float *w, const void *pk, float *Y, int *err,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    TcArgs a{};
+    a.X = X;
+    a.Y = Y;
+    a.n = n;
+    a.w = w;
+    a.pk = (const unsigned short *)pk;
+    a.err = err;
+    return tc_launch(a, false, (n + TM - 1) / TM, s);
+}
+
+// dissipation 2 nu s_ij s_ij of the network's gradients (times 1/g_scale)
+// at the listed near-surface cells into eps_o; the count is read on the device
+cudaError_t closure_eps_tc(const Ctx &c, const float *u32, const int *cells, const int *pid, const long long *count,
+                           long long cap, const void *pk, float *eps_o, int *err) {
+    TcArgs a{};
+    a.count = count;
+    a.cap = cap;
+    a.w = c.cl_w;
+    a.pk = (const unsigned short *)pk;
+    a.cells = cells;
+    a.pid = pid;
+    a.u = u32;
+    a.Xp = c.X;
+    a.Up = c.U;
+    a.Wp = c.W;
+    a.Rp = c.R;
+    a.nx = c.nx;
+    a.ny = c.ny;
+    a.nz = c.nz;
+    a.N = c.N;
+    a.inv_us = 1.0 / c.cl_uscale;
+    a.inv_gs = 1.0 / c.cl_gscale;
+    a.nu = (c.tau - 0.5) / 3.0;
+    a.eps_o = eps_o;
+    a.err = err;
+    return tc_launch(a, true, (cap + TM - 1) / TM, c.stream);
+}
+
+}  // namespace lbmgb

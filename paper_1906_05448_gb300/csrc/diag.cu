@@ -22,9 +22,10 @@ __device__ __forceinline__ int dwrap(int a, int n) {
 
 // rho and u of the post-collision state: sum f c = rho u + F/2 after a Guo
 // collision with total force F (body force on fluid cells + IBM force).
+// u32, if not null, receives an FP32 copy of u (the closure's gather input).
 template <int S>
 __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux, const void *sup_Fv, double *rho_o,
-                             double *u_o, long long N, double F0, double F1, double F2, int ibb, int ibm,
+                             double *u_o, float *u32, long long N, double F0, double F1, double F2, int ibb, int ibm,
                              long long max_sites) {
     typedef typename Store<S>::T T;
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,6 +34,7 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
     if (ibb && (fl & FL_SOLID)) {
         rho_o[c] = 0.0;
         u_o[c] = u_o[N + c] = u_o[2 * N + c] = 0.0;
+        if (u32) u32[c] = u32[N + c] = u32[2 * N + c] = 0.f;
         return;
     }
     // arithmetic type of the storage (FP32 for the 32- and 16-bit layouts)
@@ -59,19 +61,25 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
     const R rho = R(1) + r;
     const R ir = R(1) / rho;
     rho_o[c] = double(rho);
-    u_o[c] = double((j0 - R(0.5) * Fx) * ir);
-    u_o[N + c] = double((j1 - R(0.5) * Fy) * ir);
-    u_o[2 * N + c] = double((j2 - R(0.5) * Fz) * ir);
+    const R ux = (j0 - R(0.5) * Fx) * ir, uy = (j1 - R(0.5) * Fy) * ir, uz = (j2 - R(0.5) * Fz) * ir;
+    u_o[c] = double(ux);
+    u_o[N + c] = double(uy);
+    u_o[2 * N + c] = double(uz);
+    if (u32) {
+        u32[c] = float(ux);
+        u32[N + c] = float(uy);
+        u32[2 * N + c] = float(uz);
+    }
 }
 
-cudaError_t launch_macro(Ctx &c, int /*mask_mode*/) {
+cudaError_t launch_macro(Ctx &c, int /*mask_mode*/, float *u32) {
     if (c.q == 27) return launch_q27_macro(c);
     count_launch(c, G_STATS);
     const unsigned nb = (unsigned)((c.N + 255) / 256);
     const int ibb = c.armed_bc == LBM_BC_IBB;
     const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
     switch (c.storage) {
-#define MK(S) macro_kernel<S><<<nb, 256, 0, c.stream>>>(c.fA, c.flags, c.aux, c.sup_F, c.rho_f, c.u_f, c.N, c.F[0], \
+#define MK(S) macro_kernel<S><<<nb, 256, 0, c.stream>>>(c.fA, c.flags, c.aux, c.sup_F, c.rho_f, c.u_f, u32, c.N, c.F[0], \
                                                            c.F[1], c.F[2], ibb, ibm, c.max_sites)
     case LBM_F64: MK(LBM_F64); break;
     case LBM_F32: MK(LBM_F32); break;
@@ -318,6 +326,26 @@ __global__ void closure_target_kernel(const double *u, const uint8_t *flags, con
         for (int b = 0; b < 3; b++) t[3 * a + b] = (float)(0.5 * (u[a * N + nb[b][0]] - u[a * N + nb[b][1]]) * gs);
 }
 
+// the near-surface fluid nodes of the fused closure dissipation: cell and
+// nearest particle (distance to the surface in (0, 2]); order not fixed
+__global__ void closure_list_kernel(const uint8_t *flags, const int *near_pid, const double *X, const double *R,
+                                    int nx, int ny, int nz, long long N, int *cells, int *pids, long long *count,
+                                    long long cap) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        if (flags[c] & FL_SOLID) continue;
+        const int p = near_pid[c];
+        if (p == NO_OWNER) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        const double rx = dmimg(x - X[3 * p], nx), ry = dmimg(y - X[3 * p + 1], ny), rz = dmimg(z - X[3 * p + 2], nz);
+        const double d = sqrt(rx * rx + ry * ry + rz * rz) - R[p];
+        if (!(d > 0.0 && d <= 2.0)) continue;
+        const long long k = (long long)atomicAdd((unsigned long long *)count, 1ULL);
+        if (k >= cap) continue;
+        cells[k] = (int)c;
+        pids[k] = p;
+    }
+}
+
 // dissipation 2 nu s_ij s_ij from predicted gradients (scaled by g_scale)
 __global__ void closure_eps_kernel(const float *Y, const int *cells, long long n, double inv_gs, double nu,
                                    float *eps_o) {
@@ -340,7 +368,6 @@ __global__ void fill_f32(float *p, float v, long long n) {
     if (i < n) p[i] = v;
 }
 
-cudaError_t mlp_forward_device(const float *X, long long n, const float *w, void *pk_ws, float *Y, cudaStream_t s);
 
 static void near_surface(Ctx &c, const unsigned nb) {
     count_launch(c, G_STATS, 4);
@@ -458,35 +485,35 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     memset(o, 0, sizeof(*o));
     const int ibb = c.armed_bc == LBM_BC_IBB;
     const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
-    if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
+    const bool closure = (flags & LBM_STATS_CLOSURE) && c.np > 0 && c.cl_ready && c.max_cl > 0 && c.q == 19;
+    // the closure gathers an FP32 copy of u, kept in the population buffer
+    // that the next step overwrites
+    float *u32 = closure ? (float *)c.fB : nullptr;
+    if ((e = launch_macro(c, 0, u32)) != cudaSuccess) return e;
     count_launch(c, G_STATS, 3);
     mass_kernel<<<SNB, SB, 0, c.stream>>>(c.rho_f, c.u_f, c.flags, c.N, ibb, c.partials);
     const bool mask = !(ibm && (flags & LBM_STATS_UNMASK));
     const unsigned nb = (unsigned)((c.N + 255) / 256);
     const double nu = (c.tau - 0.5) / 3.0;
     const bool bins = (flags & LBM_STATS_BINS) && c.np > 0;
-    const bool closure = (flags & LBM_STATS_CLOSURE) && c.np > 0 && c.cl_ready && c.max_cl > 0;
     const float *eps_o = nullptr;
     if (bins || closure) near_surface(c, nb);
     if (closure) {
-        // learned gradients at the near-surface nodes (unmasked velocity in)
-        count_launch(c, G_STATS, 4);
+        // learned gradients at the near-surface nodes (unmasked velocity in):
+        // list the nodes, then one tensor-core kernel gathers each node's
+        // features, runs the network and writes the dissipation at the cell
+        count_launch(c, G_STATS, 5);
         fill_f32<<<nb, 256, 0, c.stream>>>(c.cl_eps, -1.f, c.N);
         if ((e = cudaMemsetAsync(c.d_counts + 3, 0, sizeof(long long), c.stream)) != cudaSuccess) return e;
-        closure_sample_kernel<<<1024, 256, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.U, c.W, c.R, c.nx, c.ny,
-                                                          c.nz, c.N, 1.0 / c.cl_uscale, c.cl_X, c.cl_cells,
-                                                          c.d_counts + 3, c.max_cl);
-        long long ncl = 0;
-        if ((e = cudaMemcpyAsync(&ncl, c.d_counts + 3, sizeof(long long), cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(c.d_status + 1, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
+        int *pids = (int *)c.cl_X;  // the feature buffer is not needed by the fused path
+        closure_list_kernel<<<1024, 256, 0, c.stream>>>(c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N,
+                                                        c.cl_cells, pids, c.d_counts + 3, c.max_cl);
+        if ((e = mlp_pack_device(c.cl_w, c.cl_pk, c.stream)) != cudaSuccess) return e;
+        if ((e = closure_eps_tc(c, u32, c.cl_cells, pids, c.d_counts + 3, c.max_cl, c.cl_pk, c.cl_eps,
+                                (int *)(c.d_status + 1))) != cudaSuccess)
             return e;
-        if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
-        if (ncl > c.max_cl) ncl = c.max_cl;
-        if ((e = mlp_forward_device(c.cl_X, ncl, c.cl_w, c.cl_pk, c.cl_Y, c.stream)) != cudaSuccess) return e;
-        if (ncl > 0)
-            closure_eps_kernel<<<(unsigned)((ncl + 255) / 256), 256, 0, c.stream>>>(c.cl_Y, c.cl_cells, ncl,
-                                                                                 1.0 / c.cl_gscale, nu, c.cl_eps);
         eps_o = c.cl_eps;
-        c.cl_last_n = ncl;
     }
     if (mask) mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
     energy_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.nx, c.ny, c.nz, c.N, nu, c.has_pipe, c.partials, eps_o);
@@ -513,7 +540,12 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
         cudaMemcpyAsync(mass.data(), c.mass, sizeof(double) * c.np, cudaMemcpyDeviceToHost, c.stream);
         cudaMemcpyAsync(inertia.data(), c.inertia, sizeof(double) * c.np, cudaMemcpyDeviceToHost, c.stream);
     }
+    unsigned tc_err = 0;
+    if (closure && (e = cudaMemcpyAsync(&tc_err, c.d_status + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                        c.stream)) != cudaSuccess)
+        return e;
     if ((e = cudaStreamSynchronize(c.stream)) != cudaSuccess) return e;
+    if (tc_err) return cudaErrorLaunchTimeout;  // a tensor-core wait of the closure ran out
     double s[NP] = {0};
     for (int b = 0; b < SNB; b++)
         for (int k = 0; k < 11; k++) s[k] += part[(size_t)b * NP + k];

@@ -8,6 +8,12 @@
 // run (Sec. 3.1: a sharp interface found by ray-sphere intersection).
 #include "lbm_internal.cuh"
 
+#include <algorithm>
+
+#ifndef LBM_LOCAL_SITES
+#define LBM_LOCAL_SITES 1  // 1: particle boundary cells marked per particle box (see bnd_mark_kernel)
+#endif
+
 namespace lbmgb {
 
 __device__ __forceinline__ double gmimg(double d, int n) {
@@ -140,7 +146,7 @@ struct RefillArgs {
     void *B;
     const uint8_t *flags;
     const int *aux;
-    const double *X, *U, *W, *R;
+    const double *X, *U, *W, *R, *Xold;
     int nx, ny, nz;
     long long N;
     double F[3];
@@ -151,8 +157,9 @@ struct RefillArgs {
 
 __global__ void refill_collect_kernel(RefillArgs a) {
     const int p = blockIdx.x;
-    const double *Xp = a.X + 3 * p;
-    const int r = (int)ceil(a.R[p]) + 3;
+    // uncovered nodes were solid at the old position: the box the clear pass swept
+    const double *Xp = a.Xold + 3 * p;
+    const int r = (int)ceil(a.R[p]) + 1;
     const int bx = (int)floor(Xp[0]) - r, by = (int)floor(Xp[1]) - r, bz = (int)floor(Xp[2]) - r;
     const int w = 2 * r + 2;
     const FastDiv fw((unsigned)w);
@@ -172,13 +179,10 @@ __global__ void refill_collect_kernel(RefillArgs a) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) refill_apply_kernel(RefillArgs a) {
+__device__ __forceinline__ void refill_one(const RefillArgs &a, long long k) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R Rt;
-    const long long n = *a.count < a.cap ? *a.count : a.cap;
-    const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (k >= n) return;
     const size_t N = (size_t)a.N;
     T *B = (T *)a.B;
     const int c = a.list[k], p = a.list_pid[k];
@@ -258,15 +262,25 @@ __global__ void __launch_bounds__(256) refill_apply_kernel(RefillArgs a) {
     Store<S>::st(B + q * N + c, f - Rt(wgt(q)));
 }
 
+template <int S>
+__global__ void __launch_bounds__(256) refill_apply_kernel(RefillArgs a) {
+    const long long n = *a.count < a.cap ? *a.count : a.cap;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps)
+        refill_one<S>(a, k);
+}
+
+
 cudaError_t launch_refill(Ctx &c) {
     if (c.np == 0) return cudaSuccess;
     count_launch(c, G_GEOM, 3);
-    RefillArgs a{c.fB, c.flags, c.aux, c.X, c.U, c.W, c.R, c.nx, c.ny, c.nz, c.N, {c.F[0], c.F[1], c.F[2]},
+    RefillArgs a{c.fB, c.flags, c.aux, c.X, c.U, c.W, c.R, c.Xold, c.nx, c.ny, c.nz, c.N, {c.F[0], c.F[1], c.F[2]},
                  c.d_counts + 2, c.refill_list, c.refill_pid, c.max_refill};
     cudaError_t e = cudaMemsetAsync(c.d_counts + 2, 0, sizeof(long long), c.stream);
     if (e != cudaSuccess) return e;
     refill_collect_kernel<<<c.np, 256, 0, c.stream>>>(a);
-    const unsigned nb = (unsigned)((c.max_refill * 32 + 255) / 256);
+    // warp per node over the listed nodes (the count is on the device): a grid of a few blocks per SM
+    const unsigned nb = (unsigned)std::min<long long>((c.max_refill * 32 + 255) / 256, 152LL * 8);
     switch (c.storage) {
     case LBM_F64: refill_apply_kernel<LBM_F64><<<nb, 256, 0, c.stream>>>(a); break;
     case LBM_F32: refill_apply_kernel<LBM_F32><<<nb, 256, 0, c.stream>>>(a); break;
@@ -276,10 +290,10 @@ cudaError_t launch_refill(Ctx &c) {
     return cudaGetLastError();
 }
 
-// clear WAS_SOLID around each particle after the refill
+// clear WAS_SOLID after the refill: it was set in the box of the old position
 __global__ void finish_kernel(uint8_t *flags, const double *X, const double *R, int nx, int ny, int nz) {
     const int p = blockIdx.x;
-    const int r = (int)ceil(R[p]) + 3;
+    const int r = (int)ceil(R[p]) + 1;
     const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
     const int w = 2 * r + 2;
     const FastDiv fw((unsigned)w);
@@ -295,7 +309,7 @@ __global__ void finish_kernel(uint8_t *flags, const double *X, const double *R, 
 cudaError_t launch_finish_geometry(Ctx &c) {
     if (c.np == 0) return cudaSuccess;
     count_launch(c, G_GEOM);
-    finish_kernel<<<c.np, 256, 0, c.stream>>>(c.flags, c.X, c.R, c.nx, c.ny, c.nz);
+    finish_kernel<<<c.np, 256, 0, c.stream>>>(c.flags, c.Xold, c.R, c.nx, c.ny, c.nz);
     return cudaGetLastError();
 }
 
@@ -327,6 +341,7 @@ struct SiteArgs {
     unsigned *status;
     FastDiv dx, dxy;  // division by nx and nx * ny
     double dn[3], hn[3];  // nx, ny, nz and their halves as doubles
+    int *sn_list;         // links of the single-node scheme (appended, counts[4])
 };
 
 // minimum image with the box size and its half given as doubles (no
@@ -691,9 +706,139 @@ __global__ void __launch_bounds__(256) link_geom_kernel(SiteArgs a) {
         double q;
         int pid, sch;
         link_geometry(a, x, y, z, l, q, pid, sch);
+        if (sch == 2) {  // listed for the single-node pass of the step
+            const long long j = (long long)atomicAdd((unsigned long long *)(a.counts + 4), 1ULL);
+            if (j < a.max_links) a.sn_list[j] = (int)k;
+        }
         a.link_scheme[k] = (int8_t)sch;
         a.link_q[k] = q;
         a.link_pid[k] = pid;
+    }
+}
+
+// ------------------------------------- particle boundary cells, locally --
+// With particles, every boundary cell lies within one link of a particle
+// (|x - X_p| <= R_p + sqrt 2), so the cells of the last list lose their BND
+// flag, each particle's box marks its boundary cells again (BND flag, and
+// the neighbour mask in aux), and the ordered compaction then reads only the
+// grid's flag bytes, 16 per thread, instead of forming every cell's
+// neighbour mask. Order and contents of the lists are those of the
+// full-grid compaction.
+constexpr int VT = 16;          // cells per thread (one 16-byte flag load)
+constexpr int VTILE = CT * VT;  // cells per tile
+
+__global__ void bnd_clear_kernel(uint8_t *flags, const int *site_cell, const long long *counts, long long max_sites) {
+    const long long n = counts[0] < max_sites ? counts[0] : max_sites;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x)
+        atomic_and_flag(flags, site_cell[s], (uint8_t)~FL_BND);
+}
+
+__global__ void __launch_bounds__(256) bnd_mark_kernel(SiteArgs a) {
+    const int p = blockIdx.x;
+    const int r = (int)ceil(a.R[p]) + 2;
+    const int bx = (int)floor(a.X[3 * p]) - r, by = (int)floor(a.X[3 * p + 1]) - r, bz = (int)floor(a.X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    const FastDiv fw((unsigned)w);
+    // a boundary cell of p lies in the shell R_p - 1 < |x - X_p| <= R_p + sqrt 2
+    // (FP32 with margins: cells deeper inside are solid, farther out have no solid neighbour of p)
+    const float Ro = (float)a.R[p] + 1.5f, Ri = fmaxf((float)a.R[p] - 1.5f, 0.f), ro2 = Ro * Ro, ri2 = Ri * Ri;
+    const float fX0 = (float)a.X[3 * p] - bx, fX1 = (float)a.X[3 * p + 1] - by, fX2 = (float)a.X[3 * p + 2] - bz;
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const float ex = ix - fX0, ey = iy - fX1, ez = iz - fX2, e2 = ex * ex + ey * ey + ez * ez;
+        if (e2 > ro2 || e2 < ri2) continue;
+        const int x = gwrap(bx + ix, a.nx), y = gwrap(by + iy, a.ny), z = gwrap(bz + iz, a.nz);
+        const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
+        if (a.flags[c] & FL_SOLID) continue;
+        const unsigned m = solid_mask(a, x, y, z);
+        if (m == 0u) continue;
+        a.aux[c] = (int)m;  // the same value from every box that holds the cell
+        atomic_or_flag(a.flags, c, FL_BND);
+    }
+}
+
+// the VT flag bytes of a thread's cells (zero past the grid's end)
+__device__ __forceinline__ void load_flags16(const SiteArgs &a, long long base, uint8_t f[VT]) {
+    if (base + VT <= a.N) {
+        const uint4 v = __ldg((const uint4 *)(a.flags + base));
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < VT; k++) f[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+    } else {
+#pragma unroll
+        for (int k = 0; k < VT; k++) f[k] = base + k < a.N ? a.flags[base + k] : (uint8_t)0;
+    }
+}
+
+__global__ void __launch_bounds__(CT) bnd_count_kernel(SiteArgs a) {
+    __shared__ long long sh[CT / 32];
+    const long long base = (long long)blockIdx.x * VTILE + (long long)threadIdx.x * VT;
+    long long ns = 0, nl = 0;
+    if (base < a.N) {
+        uint8_t f[VT];
+        load_flags16(a, base, f);
+#pragma unroll
+        for (int k = 0; k < VT; k++)
+            if (f[k] & FL_BND) {
+                ns++;
+                nl += __popc((unsigned)a.aux[base + k]);
+            }
+    }
+    long long ts, tl;
+    block_exclusive_scan<long long>(ns, sh, ts);
+    block_exclusive_scan<long long>(nl, sh, tl);
+    if (threadIdx.x == 0) {
+        a.blk_sites[blockIdx.x] = ts;
+        a.blk_links[blockIdx.x] = tl;
+    }
+}
+
+__global__ void __launch_bounds__(CT) bnd_emit_kernel(SiteArgs a) {
+    __shared__ long long sh[CT / 32];
+    const long long base = (long long)blockIdx.x * VTILE + (long long)threadIdx.x * VT;
+    uint8_t f[VT];
+    long long ns = 0, nl = 0;
+    unsigned bnd = 0;
+    if (base < a.N) {
+        load_flags16(a, base, f);
+#pragma unroll
+        for (int k = 0; k < VT; k++)
+            if (f[k] & FL_BND) {
+                bnd |= 1u << k;
+                ns++;
+                nl += __popc((unsigned)a.aux[base + k]);
+            }
+    }
+    long long ts, tl;
+    long long s0 = block_exclusive_scan<long long>(ns, sh, ts) + a.blk_sites[blockIdx.x];
+    long long l0 = block_exclusive_scan<long long>(nl, sh, tl) + a.blk_links[blockIdx.x];
+    while (bnd) {
+        const int k = __ffs(bnd) - 1;
+        bnd &= bnd - 1;
+        const long long c = base + k;
+        const unsigned m = (unsigned)a.aux[c];
+        const int nl_c = __popc(m);
+        // a site and its links are written only if they fit; otherwise the
+        // status word reports the overflow and the cell loses its BND flag
+        // (this thread owns these flag bytes here)
+        if (s0 < a.max_sites && l0 + nl_c <= a.max_links) {
+            a.site_cell[s0] = (int)c;
+            a.site_first[s0] = (int)l0;
+            a.site_mask[s0] = m;
+            a.aux[c] = (int)s0;
+            long long lk = l0;
+            for (int l = 1; l < 19; l++) {
+                if (!((m >> l) & 1u)) continue;
+                a.link_cell[lk] = (int)c;
+                a.link_dir[lk] = (int8_t)l;
+                lk++;
+            }
+        } else {
+            a.flags[c] = (uint8_t)(a.flags[c] & ~FL_BND);
+        }
+        l0 += nl_c;
+        s0++;
     }
 }
 
@@ -730,17 +875,32 @@ cudaError_t build_sites(Ctx &c, int mode) {
     a.status = c.d_status;
     a.dx = FastDiv((unsigned)c.nx);
     a.dxy = FastDiv((unsigned)(c.nx * c.ny));
+    a.sn_list = c.sn_list;
     const int nd[3] = {c.nx, c.ny, c.nz};
     for (int d = 0; d < 3; d++) {
         a.dn[d] = (double)nd[d];
         a.hn[d] = 0.5 * (double)nd[d];
     }
-    const int nblk = (int)((c.N + TILE - 1) / TILE);
-    count_launch(c, G_GEOM, mode == 1 ? 4 : 3);
-    site_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
-    site_scan_kernel<<<1, ST, 0, c.stream>>>(a, nblk);
-    site_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
+    if (mode == 1 && c.np > 0 && LBM_LOCAL_SITES) {
+        // particles: local marking, then the ordered compaction of the flags
+        const int nblk = (int)((c.N + VTILE - 1) / VTILE);
+        count_launch(c, G_GEOM, 5);
+        bnd_clear_kernel<<<(unsigned)std::min<long long>(152LL * 8, (c.max_sites + 255) / 256), 256, 0, c.stream>>>(
+            c.flags, c.site_cell, c.d_counts, c.max_sites);
+        bnd_mark_kernel<<<c.np, 256, 0, c.stream>>>(a);
+        bnd_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
+        site_scan_kernel<<<1, ST, 0, c.stream>>>(a, nblk);
+        bnd_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
+    } else {
+        const int nblk = (int)((c.N + TILE - 1) / TILE);
+        count_launch(c, G_GEOM, mode == 1 ? 4 : 3);
+        site_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
+        site_scan_kernel<<<1, ST, 0, c.stream>>>(a, nblk);
+        site_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
+    }
     if (mode == 1) {
+        cudaError_t e = cudaMemsetAsync(c.d_counts + 4, 0, sizeof(long long), c.stream);
+        if (e != cudaSuccess) return e;
         long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
         if (n > c.max_links) n = c.max_links;
         long long nb = (n + 255) / 256;

@@ -50,11 +50,12 @@ struct Plan {
     size_t xy_start, xy_j, xy_w, it_k, it_w;
     int max_ring;
     long long max_xy;
-    size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas;
+    size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas, pXf, sn_list;
     size_t mX, mUnit, mdV, mUd, mFaccR, mFacc, mFr, mB, mE, mpid, mfirst;
     size_t rho_f, u_f, partials, near_key, near_pid;
     size_t cl_w, cl_pk, cl_X, cl_Y, cl_cells, cl_eps;
     long long max_cl;
+    size_t q27_colmask;
     size_t total;
 };
 
@@ -117,7 +118,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.gvals = L.take(sb * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
-    P.counts = L.take(32);
+    P.counts = L.take(64);
     P.max_refill = 256LL * (P.max_np > 0 ? P.max_np : 1);
     P.refill = L.take(8 * (size_t)P.max_refill);
     P.status = L.take(16);
@@ -136,6 +137,8 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.pIu = L.take(24 * np);
     P.pIr = L.take(24 * np);
     P.phas = L.take(4 * np);
+    P.pXf = L.take(16 * np);
+    P.sn_list = L.take(4 * ml);
     P.mX = L.take(24 * mm);
     P.mUnit = L.take(24 * mm);
     P.mdV = L.take(8 * mm);
@@ -159,6 +162,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.cl_Y = L.take(4 * 9 * (size_t)P.max_cl);
     P.cl_cells = L.take(4 * (size_t)P.max_cl);
     P.cl_eps = L.take(P.max_cl > 0 ? 4 * n : 0);
+    P.q27_colmask = L.take(g->lattice == 27 ? 4 * (size_t)g->nx * g->ny : 0);
     P.total = L.off;
     return true;
 }
@@ -627,6 +631,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.Iu = (double *)(b + P.pIu);
     c.Ir = (double *)(b + P.pIr);
     c.has_prev = (int *)(b + P.phas);
+    c.Xf = (float4 *)(b + P.pXf);
+    c.sn_list = (int *)(b + P.sn_list);
     c.max_markers = P.max_markers;
     c.mX = (double *)(b + P.mX);
     c.mUnit = (double *)(b + P.mUnit);
@@ -651,6 +657,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.cl_cells = (int *)(b + P.cl_cells);
     c.cl_eps = (float *)(b + P.cl_eps);
     c.max_cl = P.max_cl;
+    c.q27_colmask = (unsigned *)(b + P.q27_colmask);
     c.armed_bc = -1;
     c.wait_limit_s = 600.0;
     c.pipe_cx = 0.5 * (c.nx - 1);
@@ -674,7 +681,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     if ((e = cudaMemsetAsync(c.fB, 0, c.q * (size_t)c.N * sb, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.flags, 0, (size_t)c.N + 8, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.aux, 0xff, 4 * (size_t)c.N, c.stream)) != cudaSuccess) return bad(e, "memset");
-    if ((e = cudaMemsetAsync(c.d_counts, 0, 32, c.stream)) != cudaSuccess) return bad(e, "memset");
+    if ((e = cudaMemsetAsync(c.d_counts, 0, 64, c.stream)) != cudaSuccess) return bad(e, "memset");
     if ((e = cudaMemsetAsync(c.d_status, 0, 16, c.stream)) != cudaSuccess) return bad(e, "memset");
     fill_owner<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.owner, c.N);
     if ((e = cudaGetLastError()) != cudaSuccess) return bad(e, "fill");
@@ -715,9 +722,18 @@ lbm_status lbm_set_populations(lbm_ctx *h, const double *f_host) {
 
 lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
     CTX_CHECK(h);
-    if (c.q != 19) return fail(c, LBM_EUNSUPPORTED, "walls need the D3Q19 lattice");
     if (c.broken || c.armed_bc >= 0 || c.np > 0 || c.has_pipe) return fail(c, LBM_ESTATE, "geometry already set");
     if (!(radius > 1.0) || radius > 0.5 * (c.nx < c.ny ? c.nx : c.ny)) return fail(c, LBM_EINVAL, "bad pipe radius");
+    if (c.q == 27) {
+        // D3Q27: the pipe wall by linear IBB inside the sweep (q27.cu)
+        c.has_pipe = 1;
+        c.pipe_R = radius;
+        CK(launch_pipe_flags(c));
+        std::vector<unsigned> mask;
+        q27_pipe_colmask(c, mask);
+        CK(cudaMemcpy(c.q27_colmask, mask.data(), sizeof(unsigned) * mask.size(), cudaMemcpyHostToDevice));
+        return sync_all(c);
+    }
     c.has_pipe = 1;
     c.pipe_R = radius;
     CK(launch_pipe_flags(c));
@@ -740,6 +756,20 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
         static_assert(sizeof(SweepItem) == sizeof(uint4), "warp item layout");
         CK(cudaMemcpy(c.seg, items.data(), sizeof(SweepItem) * items.size(), cudaMemcpyHostToDevice));
         c.nseg = (long long)items.size();
+    }
+    // single-node links of the wall (their correction runs as its own pass)
+    c.static_single = 0;
+    if (c.nlinks > 0 && c.nlinks <= c.max_links) {
+        std::vector<int8_t> sch((size_t)c.nlinks);
+        CK(cudaMemcpy(sch.data(), c.link_scheme, (size_t)c.nlinks, cudaMemcpyDeviceToHost));
+        for (int8_t v : sch) c.static_single += v == 2;
+    }
+    // the lean sweep needs every fluid cell off the x and y faces (no x/y wrap of a pull)
+    c.pipe_nowrap = 1;
+    for (long long cell = 0; cell < c.N && c.pipe_nowrap; cell++) {
+        if (fl[(size_t)cell] & FL_SOLID) continue;
+        const long long x = cell % c.nx, y = (cell / c.nx) % c.ny;
+        if (x == 0 || x == c.nx - 1 || y == 0 || y == c.ny - 1) c.pipe_nowrap = 0;
     }
     // the wall is static: regroup its links by direction (cell order kept
     // inside a group) so that neighbouring threads of the ghost pass touch
@@ -898,14 +928,15 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
     if (s != LBM_OK) return s;
     if (c.broken) return fail(c, LBM_ESTATE, "context unusable after an error");
     // refused before the treatment is fixed, so a refused call changes nothing
-    if (c.q == 27 && bc != LBM_BC_NONE) return fail(c, LBM_EUNSUPPORTED, "D3Q27 runs the periodic box only");
+    if (c.q == 27 && !(bc == LBM_BC_NONE || (bc == LBM_BC_IBB && c.has_pipe)))
+        return fail(c, LBM_EUNSUPPORTED, "D3Q27 runs the periodic box and the pipe with IBB only");
     if (c.armed_bc < 0) {
         s = arm(c, bc);
         if (s != LBM_OK) return s;
     } else if (c.armed_bc != bc) {
         return fail(c, LBM_ESTATE, "boundary treatment fixed to %d by the first step", c.armed_bc);
     }
-    if (c.q == 27) {  // periodic box only (checked above)
+    if (c.q == 27) {  // periodic box, or the pipe with its wall inside the sweep (checked above)
         for (int n = 0; n < nsteps; n++) {
             cudaEvent_t t0 = pmark(c);
             CK(launch_q27_step(c));
@@ -1242,6 +1273,17 @@ lbm_status file_to_dev(Ctx &c, FILE *f, void *dev, size_t bytes, const char *pat
 
 size_t arith_bytes(const Ctx &c) { return c.storage == LBM_F64 ? 8 : 4; }
 
+// support set of the last IBM step (a moving particle's set is rebuilt at
+// the start of the next step): clear the support flags, then mark the listed cells
+__global__ void clear_support_kernel(uint8_t *flags, long long N) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) flags[c] = (uint8_t)(flags[c] & ~FL_SUP);
+}
+__global__ void mark_support_kernel(uint8_t *flags, const int *cells, long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) flags[cells[k]] = (uint8_t)(flags[cells[k]] | FL_SUP);
+}
+
 }  // namespace
 }  // namespace lbmgb
 
@@ -1292,7 +1334,10 @@ lbm_status lbm_checkpoint(lbm_ctx *h, const char *path) {
         CKS(dev_to_file(c, F.f, c.R, sizeof(double) * (size_t)c.np, path));
         CKS(dev_to_file(c, F.f, c.has_prev, sizeof(int) * (size_t)c.np, path));
     }
-    if (H.nsites > 0) CKS(dev_to_file(c, F.f, c.sup_F, 3 * arith_bytes(c) * (size_t)H.nsites, path));
+    if (H.nsites > 0) {
+        CKS(dev_to_file(c, F.f, c.site_cell, sizeof(int) * (size_t)H.nsites, path));
+        CKS(dev_to_file(c, F.f, c.sup_F, 3 * arith_bytes(c) * (size_t)H.nsites, path));
+    }
     if (H.nm > 0) CKS(dev_to_file(c, F.f, c.mFacc, sizeof(double) * 3 * (size_t)H.nm, path));
     if (c.cl_ready) CKS(dev_to_file(c, F.f, c.cl_w, sizeof(float) * LBM_MLP_NPARAM, path));
     if (fflush(F.f) != 0) return io_fail(c, "write", path);
@@ -1366,7 +1411,19 @@ lbm_status lbm_restore(lbm_ctx *h, const char *path) {
         CK(cudaStreamSynchronize(c.stream));
     }
     if (H.nsites > 0) {
-        if (H.nsites != c.nsites) return fail(c, LBM_EINVAL, "checkpoint support set differs from the rebuilt one");
+        // the support set of the last step (moving particles: the positions
+        // before their last update), whose IBM force the statistics use
+        if (H.nsites > c.max_sites || (size_t)H.nsites * sizeof(int) > 24 * (size_t)c.N)
+            return fail(c, LBM_ENOMEM, "checkpoint support set exceeds max_sites");
+        int *cells = (int *)c.u_f;  // statistics scratch as staging
+        CKS(file_to_dev(c, F.f, cells, sizeof(int) * (size_t)H.nsites, path));
+        clear_support_kernel<<<(unsigned)((c.N + 255) / 256), 256, 0, c.stream>>>(c.flags, c.N);
+        mark_support_kernel<<<(unsigned)((H.nsites + 255) / 256), 256, 0, c.stream>>>(c.flags, cells, H.nsites);
+        CK(cudaGetLastError());
+        CK(build_sites(c, 2));
+        CKS(sync_all(c));
+        if (H.nsites != c.nsites) return fail(c, LBM_EINVAL, "checkpoint support set is not a support set of this grid");
+        c.nsites_hint = c.nsites;
         CKS(file_to_dev(c, F.f, c.sup_F, 3 * arith_bytes(c) * (size_t)H.nsites, path));
     }
     if (H.nm > 0) {

@@ -132,29 +132,40 @@ __host__ __device__ __forceinline__ R guo_term(int i, R ux, R uy, R uz, R Fx, R 
     return R(wgt(i)) * (R(3) * a + R(9) * cu * b);
 }
 
-// BGK with a uniform body force in FP32, force factors folded on the host:
-// g*_i = g_i + omega (w_i P_i - g_i) + (1 - omega/2) w_i [3 c_i.F - 3 u.F
-// + 9 (c_i.u)(c_i.F)] with P_i = drho - 1.5 rho u^2 + 3 rho c_i.u
-// + 4.5 rho (c_i.u)^2: the same BGK + Guo step as collide<float, FORCE,
-// true> in fewer operations (the relaxation keeps its association).
-struct SrtK {
-    float om;     // omega
-    float K[19];  // 3 (1 - omega/2) w_i c_i.F
-    float L[19];  // 9 (1 - omega/2) w_i c_i.F
-    float cw[19]; // (1 - omega/2) w_i
-    float hF[3];  // F / 2
-    float F3[3];  // 3 F
+// BGK + Guo factors per weight class (rest, axis, edge) and direction, in
+// the pair form, with the forcing folded into the departure (divided by
+// omega); factors that scale populations carry the storage scale 2^SC.
+struct PairK {
+    float om;       // omega
+    float q[2];     // 4.5 w (axis, edge)                 [x rho per cell]
+    float t[2];     // 3 w (axis, edge), with 2 t_axis + 8 t_edge = 1 exactly  [x c_i.j']
+    float w[3];     // w (rest, axis, edge)               [x (drho - 1.5 rho u^2)]
+    float cw[3];    // (1 - omega/2) w / omega            [x 3 u.F]
+    float K[19];    // 3 (1 - omega/2) w c_i.F / omega + t_i c_i.F / 2 (the force's share of the odd equilibrium)
+    float L[19];    // 9 (1 - omega/2) w c_i.F / omega
+    float hF[3];    // F / 2 (unscaled)
+    float F3[3];    // 3 F (unscaled)
 };
 
-inline SrtK make_srt_k(double omega, const double F[3]) {
-    SrtK k;
+inline PairK make_pair_k(double omega, const double F[3]) {
+    PairK k;
+    const double c1 = (1.0 - 0.5 * omega) / omega;
+    const double wcls[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     k.om = (float)omega;
-    const double c1 = 1.0 - 0.5 * omega;
+    for (int j = 0; j < 2; j++) k.q[j] = (float)(4.5 * wcls[j + 1]);
+    // 3 w in FP32 with the x-momentum sum 2 t_axis + 8 t_edge exactly 1, so
+    // that the odd equilibrium part carries exactly the momentum j'
+    k.t[1] = (float)(1.0 / 12.0);
+    k.t[0] = (float)((1.0 - 8.0 * (double)k.t[1]) / 2.0);  // exact: 5592405 / 2^25
+    for (int j = 0; j < 3; j++) {
+        k.w[j] = (float)wcls[j];
+        k.cw[j] = (float)(c1 * wcls[j]);
+    }
     for (int i = 0; i < 19; i++) {
         const double cF = cx(i) * F[0] + cy(i) * F[1] + cz(i) * F[2];
-        k.K[i] = (float)(3.0 * c1 * wgt(i) * cF);
+        const double ti = i == 0 ? 0.0 : (double)k.t[i <= 6 ? 0 : 1];
+        k.K[i] = (float)(3.0 * c1 * wgt(i) * cF + 0.5 * ti * cF);
         k.L[i] = (float)(9.0 * c1 * wgt(i) * cF);
-        k.cw[i] = (float)(c1 * wgt(i));
     }
     for (int d = 0; d < 3; d++) {
         k.hF[d] = (float)(0.5 * F[d]);
@@ -163,49 +174,70 @@ inline SrtK make_srt_k(double omega, const double F[3]) {
     return k;
 }
 
-// SC: populations come in and go out multiplied by 2^SC (FP16 storage keeps
-// g * 2^10); every product with 2^SC or 2^-SC is exact, so the results are
-// those of the unscaled step, scaled.
-template <bool FORCE, int SC = 0>
-__device__ __forceinline__ void collide_srt_k(float g[19], const SrtK &k, float &rho_o, float &ux_o, float &uy_o,
-                                              float &uz_o) {
-    constexpr float up = float(1u << SC), down = 1.0f / float(1u << SC);
-    float drho = g[0];
-#pragma unroll
-    for (int i = 1; i < 19; i++) drho += g[i];
-    float jx = (g[1] - g[2]) + (g[7] - g[8]) + (g[9] - g[10]) + (g[11] - g[12]) + (g[13] - g[14]);
-    float jy = (g[3] - g[4]) + (g[7] - g[8]) - (g[9] - g[10]) + (g[15] - g[16]) + (g[17] - g[18]);
-    float jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
-    if (SC != 0) {
-        drho *= down;
-        jx *= down;
-        jy *= down;
-        jz *= down;
-    }
+// BGK + Guo on one cell over opposite pairs, g in/out (x 2^SC); returns rho
+// and |u|^2. The new value is g + omega d with the departure
+// d_i = g_eq,i + F_i / omega - g_i formed at its own (small) scale and
+// rounded into g once. Two choices keep FP32 rounding from accumulating in
+// a near-steady flow, where the same rounding recurs every step:
+// - the odd equilibrium part 3 w_i c_i.(rho u) = 3 w_i c_i.(j + F/2) is
+//   taken from the momentum j itself with FP32 factors whose momentum sum
+//   is exactly 1, so the equilibrium carries exactly the cell's momentum
+//   (with the rounded factors 3 w and rho u = rho (j'/rho), every collision
+//   would add about 3e-8 of it); the force's share 3 w_i c_i.F/2 is a
+//   per-direction constant (adding F/2 to j in FP32 would keep only a few
+//   bits of a small force);
+// - that odd part is subtracted from g_i in one fused step (it nearly
+//   cancels g_i's odd part), and the even part and forcing are added to
+//   the small remainder.
+template <bool FORCE, int SC>
+__device__ __forceinline__ void collide_pairs(float g[19], const PairK &k, float &rho_o, float &u2_o) {
+    constexpr float down = 1.0f / float(1u << SC), up = float(1u << SC);
+    const float s1 = g[1] + g[2], d1 = g[1] - g[2], s3 = g[3] + g[4], d3 = g[3] - g[4];
+    const float s5 = g[5] + g[6], d5 = g[5] - g[6], s7 = g[7] + g[8], d7 = g[7] - g[8];
+    const float s9 = g[9] + g[10], d9 = g[9] - g[10], s11 = g[11] + g[12], d11 = g[11] - g[12];
+    const float s13 = g[13] + g[14], d13 = g[13] - g[14], s15 = g[15] + g[16], d15 = g[15] - g[16];
+    const float s17 = g[17] + g[18], d17 = g[17] - g[18];
+    float drho = g[0] + ((s1 + s3) + s5) + ((s7 + s9) + (s11 + s13)) + (s15 + s17);
+    // momentum j at the scale of g; the Guo velocity is u = (j + F/2) / rho
+    const float jx = d1 + (d7 + d9) + (d11 + d13);
+    const float jy = d3 + (d7 - d9) + (d15 + d17);
+    const float jz = d5 + (d11 - d13) + (d15 - d17);
+    if (SC != 0) drho *= down;
     const float rho = 1.0f + drho;
-    const float irho = __frcp_rn(rho);
-    if (FORCE) {
-        jx += k.hF[0];
-        jy += k.hF[1];
-        jz += k.hF[2];
-    }
-    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    const float ir = __frcp_rn(rho) * down;
+    const float ux = (FORCE ? fmaf(k.hF[0], up, jx) : jx) * ir;
+    const float uy = (FORCE ? fmaf(k.hF[1], up, jy) : jy) * ir;
+    const float uz = (FORCE ? fmaf(k.hF[2], up, jz) : jz) * ir;
+    const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
     rho_o = rho;
-    ux_o = ux;
-    uy_o = uy;
-    uz_o = uz;
-    const float u2 = ux * ux + uy * uy + uz * uz;
-    const float base = drho - 1.5f * rho * u2;
-    const float r3 = 3.0f * rho, r45 = 4.5f * rho;
-    const float uF3 = FORCE ? ux * k.F3[0] + uy * k.F3[1] + uz * k.F3[2] : 0.0f;
-#pragma unroll
-    for (int i = 0; i < 19; i++) {
-        const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-        const float P = fmaf(cu, fmaf(r45, cu, r3), base);
-        float v = fmaf(k.om, fmaf(float(wgt(i)) * up, P, -g[i]), g[i]);
-        if (FORCE) v = fmaf(k.L[i] * up, cu, v) + fmaf(-k.cw[i] * up, uF3, k.K[i] * up);
-        g[i] = v;
-    }
+    u2_o = u2;
+    const float Bv = fmaf(-1.5f * rho, u2, drho);
+    const float uF3 = FORCE ? fmaf(ux, k.F3[0], fmaf(uy, k.F3[1], uz * k.F3[2])) : 0.0f;
+    // even part of the departure without its 4.5 w rho (c.u)^2 and L c.u terms, per class (x 2^SC)
+    const float b0 = (FORCE ? fmaf(k.w[0], Bv, -k.cw[0] * uF3) : k.w[0] * Bv) * up;
+    const float b1 = (FORCE ? fmaf(k.w[1], Bv, -k.cw[1] * uF3) : k.w[1] * Bv) * up;
+    const float b2 = (FORCE ? fmaf(k.w[2], Bv, -k.cw[2] * uF3) : k.w[2] * Bv) * up;
+    const float q1 = k.q[0] * rho * up, q2 = k.q[1] * rho * up;
+    const float t1 = k.t[0], t2 = k.t[1];
+    const float om = k.om;
+    g[0] = fmaf(om, b0 - g[0], g[0]);
+    // even part E = q (c.u)^2 + L c.u + b, odd part t c.j + K
+    auto pair = [&](int i, float cu, float cj, float q, float t, float b) {
+        const float E = FORCE ? fmaf(fmaf(q, cu, k.L[i] * up), cu, b) : fmaf(q * cu, cu, b);
+        const float Ki = FORCE ? k.K[i] * up : 0.0f;
+        const float hi = fmaf(t, cj, -g[i]), hb = fmaf(-t, cj, -g[i + 1]);
+        g[i] = fmaf(om, (E + Ki) + hi, g[i]);
+        g[i + 1] = fmaf(om, (E - Ki) + hb, g[i + 1]);
+    };
+    pair(1, ux, jx, q1, t1, b1);
+    pair(3, uy, jy, q1, t1, b1);
+    pair(5, uz, jz, q1, t1, b1);
+    pair(7, ux + uy, jx + jy, q2, t2, b2);
+    pair(9, ux - uy, jx - jy, q2, t2, b2);
+    pair(11, ux + uz, jx + jz, q2, t2, b2);
+    pair(13, ux - uz, jx - jz, q2, t2, b2);
+    pair(15, uy + uz, jy + jz, q2, t2, b2);
+    pair(17, uy - uz, jy - jz, q2, t2, b2);
 }
 
 // Collide one cell in place. g: shifted populations in, post-collision out.
@@ -224,6 +256,7 @@ __host__ __device__ __forceinline__ void collide(R g[19], R Fx, R Fy, R Fz, cons
     R jz = (g[5] - g[6]) + (g[11] - g[12]) - (g[13] - g[14]) + (g[15] - g[16]) - (g[17] - g[18]);
     const R rho = R(1) + drho;
     const R irho = R(1) / rho;
+    const R jx0 = jx, jy0 = jy, jz0 = jz;  // momentum without the force's half (odd equilibrium part)
     if (FORCE) {
         jx += R(0.5) * Fx;
         jy += R(0.5) * Fy;
@@ -236,25 +269,38 @@ __host__ __device__ __forceinline__ void collide(R g[19], R Fx, R Fy, R Fz, cons
     uz_o = uz;
     const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
     if constexpr (SRT) {
-        // BGK: g* = g - w (g - g_eq) + (1 - w/2) F_i with g_eq = f_eq - w;
-        // with F_i = w_i [3 c.F - 3 u.F + 9 (c.u)(c.F)] the force term costs a
-        // few operations per direction once u.F is known.
+        // BGK: g* = g + om d, d_i = g_eq,i + F_i / om - g_i with g_eq = f_eq - w
+        // and F_i = (1 - om/2) w_i [3 c_i.F - 3 u.F + 9 (c_i.u)(c_i.F)], over
+        // opposite pairs. The odd equilibrium part 3 w rho c_i.u, which nearly
+        // cancels the odd part of g_i, is subtracted from g_i in one fused
+        // step and d is rounded into g once (see collide_pairs).
         const R om = (sizeof(R) == 8) ? R(rt.d_nu) : R(rt.s_nu);
-        const R c1 = R(1) - R(0.5) * om;
-        const R base = drho - rho * R(1.5) * u2;  // direction-independent part of g_eq / w
-        const R r3 = R(3) * rho, r45 = R(4.5) * rho;
+        const R c1 = (R(1) - R(0.5) * om) / om;
+        const R Bv = drho - rho * R(1.5) * u2;
         const R uF3 = FORCE ? R(3) * (ux * Fx + uy * Fy + uz * Fz) : R(0);
-#pragma unroll
-        for (int i = 0; i < 19; i++) {
-            const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
-            const R geq = R(wgt(i)) * (base + cu * (r3 + r45 * cu));
-            R v = g[i] + om * (geq - g[i]);
-            if (FORCE) {
-                const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
-                v += (c1 * R(wgt(i))) * (R(3) * cF - uF3 + R(9) * cu * cF);
-            }
-            g[i] = v;
-        }
+        const R wr[3] = {R(1.0 / 3.0), R(1.0 / 18.0), R(1.0 / 36.0)};
+        // odd part 3 w c.(j + F/2): t c.j with factors whose momentum sum
+        // is exactly 1, and the force's share t c.F/2 beside it (see collide_pairs)
+        const R tE = R(1.0 / 12.0), tA = sizeof(R) == 8 ? R(1.0 / 6.0) : R((1.0 - 8.0 * (double)float(1.0 / 12.0)) / 2.0);
+        g[0] = g[0] + om * ((wr[0] * Bv - c1 * wr[0] * uF3) - g[0]);
+        auto pair = [&](int i, R cu, R cj, R cF, int cls) {
+            const R w = wr[cls];
+            const R E = w * (Bv + R(4.5) * rho * cu * cu) + (FORCE ? c1 * w * (R(9) * cu * cF - uF3) : R(0));
+            const R t = cls == 1 ? tA : tE;
+            const R K = FORCE ? R(3) * c1 * w * cF + R(0.5) * t * cF : R(0);
+            const R hi = fma(t, cj, -g[i]), hb = fma(-t, cj, -g[i + 1]);
+            g[i] = fma(om, (E + K) + hi, g[i]);
+            g[i + 1] = fma(om, (E - K) + hb, g[i + 1]);
+        };
+        pair(1, ux, jx0, Fx, 1);
+        pair(3, uy, jy0, Fy, 1);
+        pair(5, uz, jz0, Fz, 1);
+        pair(7, ux + uy, jx0 + jy0, Fx + Fy, 2);
+        pair(9, ux - uy, jx0 - jy0, Fx - Fy, 2);
+        pair(11, ux + uz, jx0 + jz0, Fx + Fz, 2);
+        pair(13, ux - uz, jx0 - jz0, Fx - Fz, 2);
+        pair(15, uy + uz, jy0 + jz0, Fy + Fz, 2);
+        pair(17, uy - uz, jy0 - jz0, Fy - Fz, 2);
     } else {
     // MRT: g* = g + F_i - M^-1 S (M (g + F_i/2) - (m_eq - M w)).
     R Fi[19];

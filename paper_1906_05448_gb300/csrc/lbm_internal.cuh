@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lbm.h"
 #include "lbm_device.cuh"
 
@@ -20,7 +22,8 @@ struct Ctx {
     long long N;
     double tau, F[3];
     int storage, rates;
-    int q = 19;  // velocity set: 19 (every path) or 27 (periodic box, BGK)
+    int q = 19;  // velocity set: 19 (every path) or 27 (periodic box or pipe with IBB, BGK)
+    unsigned *q27_colmask;  // D3Q27 pipe: per (x, y) column, the directions whose column is solid
     Rates rt;
     cudaStream_t stream;
     char *ws;
@@ -50,6 +53,7 @@ struct Ctx {
     uint2 *slink;
     int slink_off[20];  // first link of each direction, and the total
     int static_links;   // 1: the ghost pass uses slink (FP32-arithmetic storages)
+    long long static_single;  // single-node (scheme 2) links of the static wall
     // wall cells' post-collision populations, written by the sweep for the
     // next ghost pass: 19 values (storage type) per wall cell in cell order
     int *slink_rank;    // per static link: rank of its wall cell
@@ -63,11 +67,13 @@ struct Ctx {
     int *gidx;          // per static link: index of its value
     void *gvals;
     int bvals_ready;    // the tables above are built
+    int pipe_nowrap;    // no fluid cell on an x or y face: pulls wrap only in z (lean pipe sweep)
     int bvals_valid;    // bvals holds the values of the current state
     // compaction scratch
     int nblk;
     long long *blk_sites, *blk_links;
-    long long *d_counts;  // [0] sites, [1] links, [2] refill nodes
+    long long *d_counts;  // [0] sites, [1] links, [2] refill nodes, [3] closure samples, [4] single-node links
+    int *sn_list;         // links of the single-node scheme (link indices), d_counts[4] of them
     int *refill_list, *refill_pid;
     long long max_refill;
     long long nsites, nlinks;   // host copies (valid after a sync)
@@ -78,6 +84,7 @@ struct Ctx {
     double dens;
     double *X, *Xold, *U, *W, *R, *mass, *inertia, *Fh, *Th, *Fprev, *Tprev, *Fc, *Iu, *Ir;
     int *has_prev;
+    float4 *Xf;  // FP32 centre and radius (contact search)
     // markers
     long long max_markers, nm;
     double *mX, *mUnit, *mdV, *mFacc;
@@ -151,6 +158,7 @@ cudaError_t launch_init_equilibrium(Ctx &c, const double *u_dev, double rho0);
 cudaError_t launch_set_populations(Ctx &c, const double *f_dev);
 cudaError_t launch_get_populations(Ctx &c, double *f_dev);
 cudaError_t launch_stream_collide(Ctx &c, int bc);
+bool launch_pipe_sweep(Ctx &c, cudaError_t &err);  // sweep_pipe.cu: false when it does not apply
 cudaError_t launch_ibb_links(Ctx &c);
 cudaError_t launch_ibm_collide(Ctx &c);
 cudaError_t launch_pipe_flags(Ctx &c);
@@ -167,7 +175,7 @@ cudaError_t launch_support_mark(Ctx &c);
 cudaError_t launch_ibm_passes(Ctx &c);
 cudaError_t launch_ibm_particle_sums(Ctx &c, bool init_only);
 cudaError_t launch_ibm_rigid_overwrite(Ctx &c);
-cudaError_t launch_macro(Ctx &c, int mask_mode);
+cudaError_t launch_macro(Ctx &c, int mask_mode, float *u32 = nullptr);
 cudaError_t launch_mask(Ctx &c);  // statistics velocity: solid cells take the rigid-body velocity
 cudaError_t run_spectrum(Ctx &c, int flags, int nbins, double *E, double *D);
 cudaError_t run_pipe_profiles(Ctx &c, int flags, int nbins, double *out);
@@ -178,10 +186,17 @@ cudaError_t launch_q27_step(Ctx &c);
 cudaError_t launch_q27_init(Ctx &c, const double *u_dev, double rho0);
 cudaError_t q27_plane_copy(Ctx &c, int i, bool to_f64);
 cudaError_t launch_q27_macro(Ctx &c);
+void q27_pipe_colmask(const Ctx &c, std::vector<unsigned> &mask);
 size_t tke_budget_scratch_bytes(int nbins);
 size_t spectrum_scratch_bytes(long long N, int nbins);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);
 cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out);
 cudaError_t closure_targets(Ctx &c, const int *cells, long long n, double g_scale, float *T);
 size_t mlp_pack_bytes();
+cudaError_t mlp_pack_device(const float *w, void *pk, cudaStream_t s);
+// tensor-core (tcgen05) closure inference, closure_tc.cu
+cudaError_t mlp_forward_tc(const float *X, long long n, const float *w, const void *pk, float *Y, int *err,
+                           cudaStream_t s);
+cudaError_t closure_eps_tc(const Ctx &c, const float *u32, const int *cells, const int *pid, const long long *count,
+                           long long cap, const void *pk, float *eps_o, int *err);
 }  // namespace lbmgb

@@ -64,9 +64,14 @@ __global__ void __launch_bounds__(PB) gimem_reduce_kernel(GimemArgs a) {
     // each), then the fixed-order FP64 block sum
     Rl v[6] = {0, 0, 0, 0, 0, 0};
     const FastDiv fw((unsigned)w);
+    // a link of p starts within R_p + sqrt 2 of its centre
+    const float reach = (float)a.R[p] + 1.5f, reach2 = reach * reach;
+    const float fX0 = (float)a.X[3 * p] - bx, fX1 = (float)a.X[3 * p + 1] - by, fX2 = (float)a.X[3 * p + 2] - bz;
     for (int t = threadIdx.x; t < w * w * w; t += PB) {
         int ix, iy, iz;
         box_coords(t, fw, w, ix, iy, iz);
+        const float ex = ix - fX0, ey = iy - fX1, ez = iz - fX2;
+        if (ex * ex + ey * ey + ez * ez > reach2) continue;
         const int x = pwrap(bx + ix, a.nx), y = pwrap(by + iy, a.ny), z = pwrap(bz + iz, a.nz);
         const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
         if (!(a.flags[c] & FL_BND)) continue;
@@ -243,7 +248,15 @@ struct EomArgs {
     const double *R, *mass, *inertia;
     int *has_prev;
     int np, nx, ny, nz;
+    float4 *Xf;  // FP32 copies of the centres and radii for the contact search's cull
 };
+
+// FP32 centre and radius of every particle: the contact search culls pairs
+// on these (one FP64-to-FP32 conversion per particle instead of per pair)
+__global__ void xf_kernel(EomArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < a.np) a.Xf[p] = make_float4((float)a.X[3 * p], (float)a.X[3 * p + 1], (float)a.X[3 * p + 2], (float)a.R[p]);
+}
 
 // Normal-only soft-sphere contact (Sec. 3.1): for a gap below zeta = 1, a
 // spring-dashpot along the line of centres, k_n = m (pi^2 + ln^2 e)/Tc^2,
@@ -257,16 +270,16 @@ __global__ void __launch_bounds__(256) contact_kernel(EomArgs a) {
     if (p >= a.np) return;
     const double zeta = 1.0, e = 0.97, Tc = 10.0, PI = 3.14159265358979323846;
     const float hx = 0.5f * a.nx, hy = 0.5f * a.ny, hz = 0.5f * a.nz;
-    const float px = (float)a.X[3 * p], py = (float)a.X[3 * p + 1], pz = (float)a.X[3 * p + 2];
-    const float Rp = (float)a.R[p];
+    const float4 P = a.Xf[p];
     double F[3] = {0.0, 0.0, 0.0};
     for (int q = lane; q < a.np; q += 32) {
         if (q == p) continue;
-        float dx = px - (float)a.X[3 * q], dy = py - (float)a.X[3 * q + 1], dz = pz - (float)a.X[3 * q + 2];
+        const float4 Q = a.Xf[q];
+        float dx = P.x - Q.x, dy = P.y - Q.y, dz = P.z - Q.z;
         dx = dx > hx ? dx - a.nx : (dx < -hx ? dx + a.nx : dx);
         dy = dy > hy ? dy - a.ny : (dy < -hy ? dy + a.ny : dy);
         dz = dz > hz ? dz - a.nz : (dz < -hz ? dz + a.nz : dz);
-        const float reach = Rp + (float)a.R[q] + (float)zeta + 0.01f;
+        const float reach = P.w + Q.w + (float)zeta + 0.01f;
         if (dx * dx + dy * dy + dz * dz >= reach * reach) continue;
         const int ia = q < p ? q : p, ib = q < p ? p : q;  // pair evaluated as (a < b)
         const double d0 = pmimg(a.X[3 * ia] - a.X[3 * ib], a.nx), d1 = pmimg(a.X[3 * ia + 1] - a.X[3 * ib + 1], a.ny),
@@ -321,9 +334,10 @@ __global__ void eom_kernel(EomArgs a) {
 cudaError_t launch_particle_update(Ctx &c) {
     if (c.np == 0) return cudaSuccess;
     EomArgs a{c.X, c.Xold, c.U, c.W, c.Fh, c.Th, c.Fprev, c.Tprev, c.Fc, c.R, c.mass, c.inertia, c.has_prev,
-              c.np, c.nx, c.ny, c.nz};
+              c.np, c.nx, c.ny, c.nz, c.Xf};
     const int tb = 128, nb = (c.np + tb - 1) / tb;
-    count_launch(c, G_PART, 2);
+    count_launch(c, G_PART, 3);
+    xf_kernel<<<nb, tb, 0, c.stream>>>(a);
     contact_kernel<<<(c.np * 32 + 255) / 256, 256, 0, c.stream>>>(a);
     eom_kernel<<<nb, tb, 0, c.stream>>>(a);
     return cudaGetLastError();

@@ -9,6 +9,8 @@
 // Weights 8/27, 2/27, 1/54, 1/216 by |c|^2 = 0 .. 3.
 #include "lbm_internal.cuh"
 
+#include <vector>
+
 namespace lbmgb {
 
 namespace {
@@ -147,6 +149,112 @@ __global__ void __launch_bounds__(256) q27_sweep_kernel(Q27Args a) {
     watchdog(rho, ux, uy, uz, a.status);
 }
 
+__host__ __device__ constexpr int q27opp(int i) {
+    // the opposite velocity has every component negated: search the table
+    int o = 0;
+    for (int j = 0; j < Q27; j++)
+        if (q27x(j) == -q27x(i) && q27y(j) == -q27y(i) && q27z(j) == -q27z(i)) o = j;
+    return o;
+}
+static_assert(q27opp(0) == 0 && q27opp(1) == 6 && q27opp(26) == 19, "opposites");
+
+// The pipe wall of the paper's runs (Sec. 2.1) on D3Q27: cells with
+// (x - c_x)^2 + (y - c_y)^2 >= R^2 are solid. A link (x_f, i) joins a fluid
+// cell to a solid x_f + c_i; the wall sits at x_f + q c_i, q in (0, 1] the
+// exit root of the cylinder equation along c_i (FP64). The population
+// j = opp(i) that cannot be pulled from x_f + c_i is the linear
+// interpolated bounce-back (Bouzidi et al. 2001) from post-collision values
+// at the wall at rest:
+//   q < 1/2: 2q f*_i(x_f) + (1 - 2q) f*_i(x_f - c_i), x_f - c_i fluid, else f*_i(x_f);
+//   q >= 1/2: f*_i(x_f) / (2q) + (2q - 1)/(2q) f*_j(x_f).
+// The geometry is the same in every z plane: per (x, y) column a 27-bit
+// mask (bit i: the column x + c_i, y + c_i is solid; bit 0: the column
+// itself) tells which pulls come from the wall. Solid cells are not swept.
+struct Q27PipeArgs {
+    Q27Args b;
+    const unsigned *colmask;
+    double pcx, pcy, R2;
+};
+
+template <int S, bool FORCE>
+__global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R R;
+    const Q27Args &a = pa.b;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.N) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const unsigned zq = a.fxy.div((unsigned)c), rem = (unsigned)c - zq * (unsigned)(nx * ny);
+    const unsigned yq = a.fx.div(rem);
+    const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * (unsigned)nx);
+    const unsigned m = __ldg(pa.colmask + rem);
+    if (m & 1u) return;  // solid: keeps its values, never read
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const T *__restrict__ A = (const T *)a.A;
+    T *__restrict__ B = (T *)a.B;
+    const size_t N = (size_t)a.N;
+    R g[Q27];
+#pragma unroll
+    for (int i = 0; i < Q27; i++) {
+        const int xs = q27x(i) > 0 ? xm : (q27x(i) < 0 ? xp : x);
+        const int ys = q27y(i) > 0 ? ym : (q27y(i) < 0 ? yp : y);
+        const int zs = q27z(i) > 0 ? zm : (q27z(i) < 0 ? zp : z);
+        g[i] = Store<S>::ld(A + (i * N + (size_t)(xs + nx * (ys + ny * zs))));
+    }
+    if (m) {  // wall cell: the populations coming back from the wall
+        const double dx = (double)x - pa.pcx, dy = (double)y - pa.pcy;
+        const double c0 = dx * dx + dy * dy - pa.R2;
+#pragma unroll
+        for (int i = 1; i < Q27; i++) {
+            if (!((m >> i) & 1u)) continue;
+            const int j = q27opp(i);
+            const double aa = (double)(q27x(i) * q27x(i) + q27y(i) * q27y(i));
+            const double b = q27x(i) * dx + q27y(i) * dy;
+            const double q = (-b + sqrt(b * b - aa * c0)) / aa;
+            const R fi = Store<S>::ld(A + (i * N + (size_t)c));  // f*_i(x_f)
+            R v;
+            if (q < 0.5) {
+                // f*_i(x_f - c_i) is the regular pull of direction i
+                v = ((m >> j) & 1u) ? fi : R(2.0 * q) * fi + R(1.0 - 2.0 * q) * g[i];
+            } else {
+                const R fj = Store<S>::ld(A + (j * N + (size_t)c));  // f*_j(x_f)
+                v = R(1.0 / (2.0 * q)) * fi + R((2.0 * q - 1.0) / (2.0 * q)) * fj;
+            }
+            // the bounce-back acts on f, the storage holds g = f - w with w_i = w_j
+            g[j] = v;
+        }
+    }
+    R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+    for (int i = 0; i < Q27; i++) {
+        drho += g[i];
+        if (q27x(i)) jx += q27x(i) > 0 ? g[i] : -g[i];
+        if (q27y(i)) jy += q27y(i) > 0 ? g[i] : -g[i];
+        if (q27z(i)) jz += q27z(i) > 0 ? g[i] : -g[i];
+    }
+    const R Fx = FORCE ? R(a.F[0]) : R(0), Fy = FORCE ? R(a.F[1]) : R(0), Fz = FORCE ? R(a.F[2]) : R(0);
+    const R rho = R(1) + drho, ir = R(1) / rho;
+    const R ux = (jx + R(0.5) * Fx) * ir, uy = (jy + R(0.5) * Fy) * ir, uz = (jz + R(0.5) * Fz) * ir;
+    const R u2 = ux * ux + uy * uy + uz * uz;
+    const R om = R(a.om), c1 = R(1) - R(0.5) * om;
+    const R base = drho - rho * R(1.5) * u2, r3 = R(3) * rho, r45 = R(4.5) * rho;
+    const R uF3 = FORCE ? R(3) * (ux * Fx + uy * Fy + uz * Fz) : R(0);
+#pragma unroll
+    for (int i = 0; i < Q27; i++) {
+        const R cu = R(q27x(i)) * ux + R(q27y(i)) * uy + R(q27z(i)) * uz;
+        const R geq = R(q27w(i)) * (base + cu * (r3 + r45 * cu));
+        R v = g[i] + om * (geq - g[i]);
+        if (FORCE) {
+            const R cF = R(q27x(i)) * Fx + R(q27y(i)) * Fy + R(q27z(i)) * Fz;
+            v += (c1 * R(q27w(i))) * (R(3) * cF - uF3 + R(9) * cu * cF);
+        }
+        Store<S>::st(B + (i * N + (size_t)c), v);
+    }
+    watchdog(rho, ux, uy, uz, a.status);
+}
+
 }  // namespace
 
 template <int S>
@@ -172,7 +280,39 @@ cudaError_t launch_q27_step(Ctx &c) {
     a.status = c.d_status;
     const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
     count_launch(c, G_BULK);
+    if (c.has_pipe) {
+        Q27PipeArgs pa{a, c.q27_colmask, c.pipe_cx, c.pipe_cy, c.pipe_R * c.pipe_R};
+        const unsigned nb = (unsigned)((c.N + 255) / 256);
+        if (c.storage == LBM_F64) {
+            if (force) q27_pipe_kernel<LBM_F64, true><<<nb, 256, 0, c.stream>>>(pa);
+            else q27_pipe_kernel<LBM_F64, false><<<nb, 256, 0, c.stream>>>(pa);
+        } else {
+            if (force) q27_pipe_kernel<LBM_F32, true><<<nb, 256, 0, c.stream>>>(pa);
+            else q27_pipe_kernel<LBM_F32, false><<<nb, 256, 0, c.stream>>>(pa);
+        }
+        return cudaGetLastError();
+    }
     return c.storage == LBM_F64 ? q27_step_s<LBM_F64>(c, a, force) : q27_step_s<LBM_F32>(c, a, force);
+}
+
+// per (x, y) column: bit i set when the column (x + c_x, y + c_y) of
+// direction i is outside the pipe (bit 0: the column itself); FP64 test as
+// the D3Q19 pipe flags
+void q27_pipe_colmask(const Ctx &c, std::vector<unsigned> &mask) {
+    mask.assign((size_t)c.nx * c.ny, 0u);
+    auto solid = [&](int x, int y) {
+        x = (x % c.nx + c.nx) % c.nx;
+        y = (y % c.ny + c.ny) % c.ny;
+        const double dx = (double)x - c.pipe_cx, dy = (double)y - c.pipe_cy;
+        return dx * dx + dy * dy >= c.pipe_R * c.pipe_R;
+    };
+    for (int y = 0; y < c.ny; y++)
+        for (int x = 0; x < c.nx; x++) {
+            unsigned m = 0;
+            for (int i = 0; i < Q27; i++)
+                if (solid(x + q27x(i), y + q27y(i))) m |= 1u << i;
+            mask[(size_t)x + (size_t)c.nx * y] = m;
+        }
 }
 
 cudaError_t launch_q27_init(Ctx &c, const double *u_dev, double rho0) {

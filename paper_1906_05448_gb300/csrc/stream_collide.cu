@@ -77,6 +77,7 @@ struct LinkArgs {
     double F[3];      // body force on fluid cells (single-node fallback)
     float Fs[3];
     Rates rt;
+    const int *sn_list;  // single-node links (counts[4] of them)
 };
 
 
@@ -109,14 +110,10 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
         const int i = opp(l);
         const R fl0 = Store<S>::ld(A + (size_t)l * N + c);  // f*_l(x_f), toward the wall
         const R fi0 = Store<S>::ld(A + (size_t)i * N + c);  // f*_ibar(x_f)
-        // single-node fallback: (1 - 2q)/2 (d_l + d_ibar) from the node's own state
-        auto single = [&](R qq) -> R {
-            return R(0.5) * (R(1) - R(2) * qq) *
-                   single_node_pair<S>(A + c, N, l, body_force<R>(a, 0), body_force<R>(a, 1), body_force<R>(a, 2), a.rt);
-        };
+        // scheme 2 stores the halfway value here; single_node_fix adds the
+        // single-node correction (and its momentum) afterwards
         if constexpr (!PART) {
-            R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, R(0), fl0, fi0);
-            if (sch == 2) v += single(R(q));
+            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, R(0), fl0, fi0);
             Store<S>::st(A + (size_t)i * N + cb, v);  // pulled by x_f as f_ibar(x_f, t+1)
         } else if constexpr (sizeof(R) == 8) {
             // FP64 storage: wall velocity and momentum exchange in FP64
@@ -132,8 +129,7 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             }
             // moving-wall term 6 w rho_w (c_ibar . u_w), rho_w = 1; c_ibar = -c_l
             const R Dw = pid >= 0 ? R(-6.0 * wgt(l) * (lx * uw[0] + ly * uw[1] + lz * uw[2])) : R(0);
-            R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, Dw, fl0, fi0);
-            if (sch == 2) v += single(R(q));
+            const R v = ibb_value<S>(A, N, l, i, sch, R(q), c1, c2, Dw, fl0, fi0);
             Store<S>::st(A + (size_t)i * N + cb, v);
             if (pid >= 0) {
                 // momentum exchange with unshifted f = g + w (w_l = w_ibar)
@@ -170,8 +166,7 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
             }
             const float w_l = float(wgt(l));
             const float Dw = pid >= 0 ? -6.0f * w_l * (lx * uw[0] + ly * uw[1] + lz * uw[2]) : 0.0f;
-            float v = ibb_value<S>(A, N, l, i, sch, qf, c1, c2, Dw, fl0, fi0);
-            if (sch == 2) v += single(qf);
+            const float v = ibb_value<S>(A, N, l, i, sch, qf, c1, c2, Dw, fl0, fi0);
             Store<S>::st(A + (size_t)i * N + cb, v);
             if (pid >= 0) {
                 const float fo = fl0 + w_l, fi = v + w_l;
@@ -187,6 +182,81 @@ __global__ void __launch_bounds__(256) ibb_links(LinkArgs a) {
                 dT[1] = m2 * dP0 - m0 * dP2;
                 dT[2] = m0 * dP1 - m1 * dP0;
             }
+        }
+    }
+}
+
+// Single-node links (scheme 2): ibb_links stored their halfway value; this
+// pass adds the single-node correction (1 - 2q)/2 (d_l + d_ibar) from the
+// wall node's own post-collision values (single_node_pair), and for
+// particle links the momentum the correction carries, (c_l + u_w) dv, and
+// its torque. Kept out of ibb_links so that the rare scheme costs the
+// common link pass no registers.
+template <int S, bool PART>
+__global__ void __launch_bounds__(256) single_node_fix(LinkArgs a) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R R;
+    // the single-node links of the current list, as listed by the geometry pass
+    const long long ns = a.counts[4] < a.max_links ? a.counts[4] : a.max_links;
+    T *A = (T *)a.A;
+    const size_t N = (size_t)a.N;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < ns;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long k = a.sn_list[j];
+        const int c = a.link_cell[k];
+        const int l = a.link_dir[k];
+        const double q = a.link_q[k];
+        const unsigned zq = a.dxy.div((unsigned)c), rem = (unsigned)c - zq * (unsigned)(nx * ny);
+        const unsigned yq = a.dx.div(rem);
+        const int z = (int)zq, y = (int)yq, x = (int)(rem - yq * (unsigned)nx);
+        const int lx = cx(l), ly = cy(l), lz = cz(l), i = opp(l);
+        const int cb = wrap(x + lx, nx) + nx * (wrap(y + ly, ny) + ny * wrap(z + lz, nz));
+        const R qq = sizeof(R) == 8 ? R(q) : R(float(q));
+        const R dv = R(0.5) * (R(1) - R(2) * qq) *
+                     single_node_pair<S>(A + c, N, l, body_force<R>(a, 0), body_force<R>(a, 1), body_force<R>(a, 2), a.rt);
+        T *slot = A + (size_t)i * N + cb;
+        Store<S>::st(slot, Store<S>::ld(slot) + dv);
+        if constexpr (PART) {
+            const int pid = a.link_pid[k];
+            if (pid < 0) continue;
+            // the wall velocity and lever arm of ibb_links, in the same arithmetic
+            R uw[3], m[3];
+            if constexpr (sizeof(R) == 8) {
+                const double r0 = mimg(x + q * lx - a.X[3 * pid + 0], nx);
+                const double r1 = mimg(y + q * ly - a.X[3 * pid + 1], ny);
+                const double r2 = mimg(z + q * lz - a.X[3 * pid + 2], nz);
+                const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
+                uw[0] = Up[0] + (Wp[1] * r2 - Wp[2] * r1);
+                uw[1] = Up[1] + (Wp[2] * r0 - Wp[0] * r2);
+                uw[2] = Up[2] + (Wp[0] * r1 - Wp[1] * r0);
+                m[0] = mimg(x + 0.5 * lx - a.X[3 * pid + 0], nx);
+                m[1] = mimg(y + 0.5 * ly - a.X[3 * pid + 1], ny);
+                m[2] = mimg(z + 0.5 * lz - a.X[3 * pid + 2], nz);
+            } else {
+                const float d0 = float(mimg(double(x) - a.X[3 * pid + 0], nx));
+                const float d1 = float(mimg(double(y) - a.X[3 * pid + 1], ny));
+                const float d2 = float(mimg(double(z) - a.X[3 * pid + 2], nz));
+                const float qf = float(q);
+                const float r0 = d0 + qf * lx, r1 = d1 + qf * ly, r2 = d2 + qf * lz;
+                const double *Wp = a.W + 3 * pid, *Up = a.U + 3 * pid;
+                const float W0 = float(Wp[0]), W1 = float(Wp[1]), W2 = float(Wp[2]);
+                uw[0] = float(Up[0]) + (W1 * r2 - W2 * r1);
+                uw[1] = float(Up[1]) + (W2 * r0 - W0 * r2);
+                uw[2] = float(Up[2]) + (W0 * r1 - W1 * r0);
+                m[0] = d0 + 0.5f * lx;
+                m[1] = d1 + 0.5f * ly;
+                m[2] = d2 + 0.5f * lz;
+            }
+            // dP = (c_l - u_w) f_out - (c_ibar - u_w) f_in: f_in grew by dv
+            const R e0 = (R(lx) + uw[0]) * dv, e1 = (R(ly) + uw[1]) * dv, e2 = (R(lz) + uw[2]) * dv;
+            R *dP = (R *)a.link_dP + 3 * k, *dT = (R *)a.link_dT + 3 * k;
+            dP[0] += e0;
+            dP[1] += e1;
+            dP[2] += e2;
+            dT[0] += m[1] * e2 - m[2] * e1;
+            dT[1] += m[2] * e0 - m[0] * e2;
+            dT[2] += m[0] * e1 - m[1] * e0;
         }
     }
 }
@@ -266,7 +336,7 @@ struct StaticLinkArgs {
     Rates rt;
 };
 
-template <int S>
+template <int S, bool SN>
 __global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
@@ -297,7 +367,7 @@ __global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
             fi0 = Store<S>::ld(A + (size_t)i * N + c);
         }
         R v = ibb_value<S>(A, N, l, i, sch, qq, c1, c2, R(0), fl0, fi0);
-        if (sch == 2) {  // single-node fallback from the wall cell's own values
+        if (SN && sch == 2) {  // single-node fallback from the wall cell's own values
             const T *p = a.bvals ? (const T *)a.bvals + (size_t)19 * __ldg(a.rank + k) : A + c;
             v += R(0.5) * (R(1) - R(2) * qq) *
                  single_node_pair<S>(p, a.bvals ? 1 : N, l, body_force<R>(a, 0), body_force<R>(a, 1),
@@ -338,13 +408,15 @@ static cudaError_t launch_links_s(Ctx &c) {
         unsigned nbx = (unsigned)((most + 255) / 256);
         if (nbx < 1) nbx = 1;
         count_launch(c, G_BND);
-        ibb_links_static<S><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        // the variant with the single-node scheme only for walls that have such links
+        if (c.static_single > 0) ibb_links_static<S, true><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        else ibb_links_static<S, false><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
         return cudaGetLastError();
     }
     LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_dP, c.link_dT,
                c.X, c.U, c.W, c.d_counts, c.max_links, c.nx, c.ny, c.nz, c.N,
                FastDiv((unsigned)c.nx), FastDiv((unsigned)(c.nx * c.ny)), {c.F[0], c.F[1], c.F[2]},
-               {(float)c.F[0], (float)c.F[1], (float)c.F[2]}, c.rt};
+               {(float)c.F[0], (float)c.F[1], (float)c.F[2]}, c.rt, c.sn_list};
     long long n = c.nlinks_hint > 0 ? c.nlinks_hint : c.max_links;
     if (n > c.max_links) n = c.max_links;
     long long nb = (n + 255) / 256;
@@ -353,7 +425,17 @@ static cudaError_t launch_links_s(Ctx &c) {
     count_launch(c, G_BND);
     if (c.np > 0) ibb_links<S, true><<<(unsigned)nb, 256, 0, c.stream>>>(a);
     else ibb_links<S, false><<<(unsigned)nb, 256, 0, c.stream>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // moving walls may have single-node links at any step; a static wall only if its list has some
+    if (c.np > 0 || c.static_single > 0) {
+        count_launch(c, G_BND);
+        const unsigned nbs = 152u * 2u;  // a few single-node links: a small grid striding over the list
+        if (c.np > 0) single_node_fix<S, true><<<nbs, 256, 0, c.stream>>>(a);
+        else single_node_fix<S, false><<<nbs, 256, 0, c.stream>>>(a);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_ibb_links(Ctx &c) {

@@ -31,7 +31,7 @@ struct SweepArgs {
     double F[3];
     float Fs[3];  // F in single precision (a double-to-single conversion per cell is costly on GB300)
     Rates rt;
-    SrtK sk;  // folded BGK factors (FP32 arithmetic, uniform force)
+    PairK pk;  // BGK + Guo factors in the pair form (FP32 arithmetic, uniform force)
     const uint2 *seg_bnd;  // per item: rank of its first wall cell, wall-cell lanes
     void *bvals;           // wall cells' populations for the next ghost pass (storage type), or null
     const uint2 *wrec;     // per wall cell: first compact ghost value, replaced directions
@@ -237,12 +237,15 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         } else {
             R rho, ux, uy, uz;
             const R fs = fluid ? R(1) : R(0);  // the body force acts on fluid cells only
-            if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED)
-                collide_srt_k<FORCE, scaled ? 10 : 0>(g, a.sk, rho, ux, uy, uz);  // BC 0/1: only fluid cells collide
-            else
+            if constexpr (SRT && sizeof(R) == 4 && BC != 2 && LBM_SRT_FOLDED) {
+                float u2;  // BC 0/1: only fluid cells collide
+                collide_pairs<FORCE, scaled ? 10 : 0>(g, a.pk, rho, u2);
+                if (!(rho > 0.5f && rho < 2.0f && u2 < 0.09f)) atomicOr(a.status, 1u);
+            } else {
                 collide<R, FORCE, SRT>(g, fs * body_force<R>(a, 0), fs * body_force<R>(a, 1), fs * body_force<R>(a, 2),
                                        a.rt, rho, ux, uy, uz);
-            watchdog(rho, ux, uy, uz, a.status);
+                watchdog(rho, ux, uy, uz, a.status);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 19; i++) {
@@ -281,7 +284,7 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
         a.Fs[d] = (float)c.F[d];
     }
     a.rt = c.rt;
-    a.sk = make_srt_k(c.rt.d_nu, c.F);
+    a.pk = make_pair_k(c.rt.d_nu, c.F);
     const bool segs = BC == 1 && c.nseg > 0;
     a.seg_bnd = c.seg_bnd;
     a.bvals = (segs && c.bvals_ready && c.static_links && S != LBM_F64) ? c.bvals : nullptr;
@@ -338,7 +341,15 @@ static cudaError_t launch_bulk_s(Ctx &c, int bc, bool force) {
     return launch_bulk_t<S, false, 2>(c, force);
 }
 
+#ifndef LBM_PIPE_SWEEP
+#define LBM_PIPE_SWEEP 1  // 1: the lean static-wall sweep (sweep_pipe.cu) where it applies
+#endif
+
 cudaError_t launch_stream_collide(Ctx &c, int bc) {
+    if (LBM_PIPE_SWEEP && bc == LBM_BC_IBB) {
+        cudaError_t e = cudaSuccess;
+        if (launch_pipe_sweep(c, e)) return e;
+    }
     const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
     switch (c.storage) {
     case LBM_F64: return launch_bulk_s<LBM_F64>(c, bc, force);

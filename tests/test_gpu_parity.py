@@ -217,7 +217,14 @@ def test_pipe_ibb_200_steps(lbm, storage, tol):
     ro, uo = o.macro()
     assert rel(ug[:, fluid], uo[:, fluid]) < tol
     assert rel(rg[fluid], ro[fluid]) < tol
-    assert rel(rg[fluid] - 1.0, ro[fluid] - 1.0) < 100 * tol
+    # rho - 1 is O(1e-6) here: FP64 resolves it to 1e-8 of itself. In FP32
+    # every step rounds the 19 stored values (|g| <= 0.02, half an ulp
+    # 1e-9), so rho = 1 + sum g random-walks by about
+    # sqrt(19 x 200) x 1e-9 = 6e-8; the bar is three times that.
+    if storage == "f64":
+        assert rel(rg[fluid] - 1.0, ro[fluid] - 1.0) < 1e-8
+    else:
+        assert np.max(np.abs(rg[fluid] - ro[fluid])) < 2e-7
 
 
 @pytest.mark.parametrize("bc,nz", [("ibm_u", 4), ("ibm_b", 4), ("ibm_b", 31)])
@@ -387,7 +394,7 @@ def test_soft_sphere_contact(lbm, bc):
     d0 = np.linalg.norm(X[1] - X[0]) - 8.0
     assert d0 < 1.0  # inside the contact margin at the start
     obc = oracle.BC_IBB if bc == "ibb" else oracle.BC_IBM_B
-    vrel = []
+    vrel = [U[1, 0] - U[0, 0]]
     for _ in range(6):
         g.step(5, lbm.BC[bc])
         o.step(5, obc)
@@ -396,6 +403,7 @@ def test_soft_sphere_contact(lbm, bc):
             assert np.max(np.abs(Pg[k] - Po[k])) < 1e-10 * max(1.0, np.max(np.abs(Po[k]))), k
         vrel.append(Po["U"][1, 0] - Po["U"][0, 0])
     assert vrel[0] < 0 and vrel[-1] > 0  # closing at first, separating after the contact
+    assert max(vrel) > 0.05  # turned back by the spring (the fluid alone could not do it)
 
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])

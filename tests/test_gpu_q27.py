@@ -1,5 +1,6 @@
-"""D3Q27 periodic box on the GPU (lbm_grid.lattice = 27) vs the D3Q27
-oracle (oracle/d3q27.py), element by element on seeded inputs.
+"""D3Q27 on the GPU (lbm_grid.lattice = 27): the periodic box and the pipe
+with its linear IBB wall, vs the D3Q27 oracle (oracle/d3q27.py), element by
+element on seeded inputs.
 
 Tolerances as for D3Q19: FP64 storage 1e-12 and FP32 1e-5, relative to the
 field's largest magnitude.
@@ -71,13 +72,58 @@ def test_shear_wave_f32_100_steps(lbm):
     g.close()
 
 
+def _pipe_pair(lbm, nx, ny, nz, R, tau, F, storage, seed):
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.02, perturbation=0.1, seed=seed)
+    g = lbm.Lattice(nx, ny, nz, tau, force=F, storage=storage, lattice=27)
+    g.init_velocity(u)
+    g.set_pipe(R)
+    solid = q27.pipe_solid(nx, ny, nz, R)
+    links = q27.pipe_links(solid, R)
+    o = q27.feq(np.ones((nz, ny, nx)), u)
+    return g, o, solid, links
+
+
+@pytest.mark.parametrize("R", [10.3, 6.4])
+def test_pipe_wall_f64_step_by_step(lbm, R):
+    """The D3Q27 pipe with the linear interpolated bounce-back on its wall
+    (and the halfway fallback, which the 6.4 radius in a 16 x 16 section
+    reaches), a body force along z: every fluid cell's populations after
+    each step against the oracle's pipe step."""
+    n = 24 if R > 8 else 16
+    nz, F, tau = 5, (0.0, 0.0, 3e-6), 0.62
+    g, o, solid, links = _pipe_pair(lbm, n, n - 1, nz, R, tau, F, lbm.F64, seed=3)
+    fl = ~solid.reshape(-1)
+    for _ in range(4):
+        g.step(1, lbm.BC_IBB)
+        o = q27.step_pipe(o, solid, links, tau, F)
+        assert rel(g.populations()[:, fl], o.reshape(27, -1)[:, fl]) < 1e-12
+    rg, ug = g.macro()
+    ro, uo = q27.macro(o, F)
+    assert rel(ug[:, fl], uo.reshape(3, -1)[:, fl]) < 1e-12
+    g.close()
+
+
+def test_pipe_wall_f32_200_steps(lbm):
+    nx, ny, nz, R, tau, F = 26, 26, 8, 11.6, 0.6, (0.0, 0.0, 2e-6)
+    g, o, solid, links = _pipe_pair(lbm, nx, ny, nz, R, tau, F, lbm.F32, seed=4)
+    g.step(200, lbm.BC_IBB)
+    for _ in range(200):
+        o = q27.step_pipe(o, solid, links, tau, F)
+    fl = ~solid.reshape(-1)
+    rg, ug = g.macro()
+    ro, uo = q27.macro(o, F)
+    assert rel(ug[:, fl], uo.reshape(3, -1)[:, fl]) < 1e-5
+    assert rel(rg[fl], ro.reshape(-1)[fl]) < 1e-6
+    g.close()
+
+
 def test_d3q27_refuses_what_it_does_not_build(lbm):
     g = lbm.Lattice(16, 16, 16, 0.6, storage=lbm.F32, lattice=27)
     g.init_velocity(workloads.noise_velocity((16, 16, 16), 0.01, seed=2))
     with pytest.raises(lbm.LbmError):
-        g.set_pipe(6.0)
+        g.step(1, lbm.BC_IBB)  # IBB without a pipe
     with pytest.raises(lbm.LbmError):
-        g.step(1, lbm.BC_IBB)
+        g.add_spheres(np.array([[8.0, 8.0, 8.0]]), 3.0)
     with pytest.raises(lbm.LbmError):
         g.set_mrt_rates(1.2, 1.3, 1.1, 1.5, 1.9)
     g.step(2)
