@@ -334,11 +334,36 @@ def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     e_plain, e_closure = closure.evaluate(n, n_particles, [8, 9], steps, w.cpu().numpy(), us, gs)
-    # inference cost: the tensor-core forward over one diagnostic's samples
+    # inference cost per diagnostic: (1) fused, the tensor-core kernel inside
+    # lbm_stats(LBM_STATS_CLOSURE) (the library's "closure" event span), and
+    # the whole closure share of the diagnostic (stats with minus without);
+    # (2) the same network over a feature array in HBM (lbm_mlp_forward,
+    # including its weight packing and synchronisation)
     (ibb, bcb), (ibm, bcm) = closure.hit_pair(n, n_particles, 8)
     ibb.close()
     ibm.step(steps, bcm)
     Xs, _ = ibm.closure_samples(us, 1500 * n_particles)
+    ibm.closure_set_weights(w.cpu().numpy(), us, gs)
+    reps = 5
+
+    def stats_ms(flags):
+        ibm.stats(flags)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(reps):
+            ibm.stats(flags)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plain_ms = min(stats_ms(0), stats_ms(0))
+    with_ms = min(stats_ms(lbm.STATS_CLOSURE), stats_ms(lbm.STATS_CLOSURE))
+    ibm.profile_enable(True)
+    for _ in range(reps):
+        ibm.stats(lbm.STATS_CLOSURE)
+    pr = ibm.profile(0)
+    fused_ms = pr["ms"]["closure"] / max(1, pr["spans"]["closure"])
     ibm.close()
     wt = w.to(Xs.device)
     mlp.forward(Xs, wt)
@@ -356,8 +381,12 @@ def closure_report(lbm, torch, n=256, n_particles=2000, steps=100):
             "train_loss": round(last, 4), "zero_predictor_loss": round(float((T ** 2).mean()), 4),
             "near_surface_eps_error_plain_ibm": round(e_plain, 4),
             "near_surface_eps_error_closure": round(e_closure, 4),
-            "inference_samples": int(Xs.shape[0]), "inference_ms_per_diagnostic": round(inf_ms, 4),
-            "inference_tflops": round(flops / (inf_ms * 1e-3) / 1e12, 2)}
+            "inference_samples": int(Xs.shape[0]),
+            "fused_kernel_ms_per_diagnostic": round(fused_ms, 4),
+            "fused_kernel_tflops": round(flops / (fused_ms * 1e-3) / 1e12, 2),
+            "closure_share_of_stats_ms": round(with_ms - plain_ms, 4), "stats_ms": round(plain_ms, 4),
+            "forward_from_hbm_ms": round(inf_ms, 4),
+            "forward_from_hbm_tflops": round(flops / (inf_ms * 1e-3) / 1e12, 2)}
 
 
 def e2e_pipe(lbm, torch, steps):
@@ -415,11 +444,15 @@ def cpu_baseline(target_seconds=12.0):
             "sample": f"FP64 oracle, IBB pipe slab 148x148x16 ({fluid} fluid cells), {steps} steps, {sec:.1f} s"}
 
 
-def source_hash():
-    """Hash of the sweep kernel's sources (kernel, device header, segment
+SWEEP_SOURCES = {"stream_collide_pipe_pipe148_f32": ("sweep_pipe.cu", "lbm_device.cuh", "segments.h"),
+                 "stream_collide_bulk_pipe148_ibm_f32": ("sweep.cu", "lbm_device.cuh")}
+
+
+def source_hash(kernel_key):
+    """Hash of a sweep kernel's sources (kernel, device header, segment
     list): a recorded DRAM traffic figure is used only while it matches."""
     h = hashlib.sha256()
-    for f in ("sweep.cu", "lbm_device.cuh", "segments.h"):
+    for f in SWEEP_SOURCES[kernel_key]:
         with open(os.path.join(ROOT, "paper_1906_05448_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -432,11 +465,43 @@ def traffic_for(kernel_key):
     try:
         d = json.load(open(path))
         e = d[kernel_key]
-        if e.get("source_hash") != source_hash():
+        if e.get("source_hash") != source_hash(kernel_key):
             return None
         return e["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+def profile_case(case, steps, warmup):
+    """One workload alone, for a profiler's launch list or a kernel capture
+    (the bench line itself is not printed): the particle-laden 256^3 box
+    (IBB or IBM-B), or the closure diagnostic on the 256^3 (or 128^3, 250
+    spheres) IBM-B box after `warmup` steps, repeated `steps` times."""
+    import torch
+    from paper_1906_05448_gb300 import build as B
+    from paper_1906_05448_gb300 import lbm
+    B.build()
+    lbm.load()
+    if case.startswith("hit256"):
+        bc = lbm.BC_IBB if case == "hit256_ibb" else lbm.BC_IBM_B
+        r = run_case(lbm, torch, case, 256, 256, 256, 0.51, (0, 0, 0), lbm.F32, lbm.RATES_DHUMIERES, bc, steps,
+                     warmup, hit_setup(256, 2000))
+        p = r["prof"]
+        print(json.dumps({"case": case, "ms_per_step": round(r["ms"] / steps, 4),
+                          "group_ms_per_step": {k: round(v / steps, 4) for k, v in p["ms"].items() if v > 0}}))
+        return
+    from paper_1906_05448_gb300 import closure
+    n, npart = (256, 2000) if case == "closure256" else (128, 250)
+    (ibb, _), (ibm, bcm) = closure.hit_pair(n, npart, 8)
+    ibb.close()
+    ibm.step(warmup, bcm)
+    ibm.closure_set_weights(closure.init_weights(1), 0.03, 4.0 / 0.03)
+    ibm.profile_enable(True)
+    for _ in range(steps):
+        ibm.stats(lbm.STATS_CLOSURE)
+    p = ibm.profile(0)
+    ibm.close()
+    print(json.dumps({"case": case, "closure_kernel_ms": round(p["ms"]["closure"] / max(1, p["spans"]["closure"]), 4)}))
 
 
 # ------------------------------------------------------------------ main ---
@@ -457,9 +522,15 @@ def main():
     ap.add_argument("--wall", default="ibb", choices=["ibb", "ibm_b"],
                     help="wall treatment of the main line (default ibb; ibm_b only for profiler captures "
                          "of the IBM step, whose line is then not the benchmark's)")
+    ap.add_argument("--case", default=None,
+                    choices=["hit256_ibb", "hit256_ibm_b", "closure256", "closure128"],
+                    help="profiler captures only: run this one workload (--steps steps after --warmup) "
+                         "and print its timings instead of the bench line")
     args = ap.parse_args()
     global NZ
     NZ = args.nz
+    if args.case:
+        return profile_case(args.case, args.steps, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -594,10 +665,13 @@ def main():
                                    "Re_tau=180 body force, " + ("linear IBB wall" if args.wall == "ibb" else "IBM-B wall"),
                        "fluid_cells": main_res["fluid_cells"], "parallelism": f"replicas x{world}",
                        "l2": "no flush: populations 2x1.46 GB >> 129 MB L2"},
-            "roofline": {"bound": "hbm", "kernel": "stream_collide_bulk<f32,srt," + args.wall[:3] + ">",
+            "roofline": {"bound": "hbm",
+                         "kernel": ("stream_collide_pipe<" if args.wall == "ibb" else "stream_collide_bulk<") +
+                                   args.storage + ",srt," + args.wall[:3] + ">",
                          "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4), "peak_source": peak_kind,
-                         "traffic": traffic_for("stream_collide_bulk_pipe_f32") if args.wall == "ibb" else None,
+                         "traffic": traffic_for("stream_collide_pipe_pipe148_f32")
+                         if (args.wall == "ibb" and args.storage == "f32" and NZ == PIPE["nz"]) else None,
                          "algorithmic_bytes_per_launch": bulk_bytes,
                          "avg_launch_ms": round(bulk_ms, 5),
                          "step_achieved": round(bulk_bytes / (ms_total / args.steps * 1e-3) / 1e9, 1),

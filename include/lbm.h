@@ -73,17 +73,21 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_BF16S = 3 } lbm_stora
  * d'Humieres et al. 2002 used in Sec. 3.1 (shear moments at 1/tau). */
 typedef enum { LBM_RATES_SRT = 0, LBM_RATES_DHUMIERES = 1 } lbm_rates;
 
+/* Sphere capacity limit: the statistics pack a particle id into 20 bits. */
+#define LBM_MAX_PARTICLES 1048575
+
 typedef struct {
     int nx, ny, nz;          /* grid, each >= 4, nx*ny*nz < 2^31 */
     int storage;             /* lbm_storage */
     int rates;               /* lbm_rates */
-    int max_particles;       /* capacity for spheres (0: none) */
+    int max_particles;       /* capacity for spheres (0: none; at most LBM_MAX_PARTICLES) */
     long long max_links;     /* IBB link capacity (0: derived from the grid and max_particles) */
     long long max_markers;   /* IBM marker capacity (0: derived) */
     long long max_sites;     /* boundary / support cell capacity (0: derived) */
     int lattice;             /* velocity set: 0 or 19 D3Q19 (every path); 27 D3Q27, the set of the
                                 paper's pipe solver (Sec. 2.1): periodic box (LBM_BC_NONE), BGK
-                                (LBM_RATES_SRT), FP64 or FP32 storage; walls and the MRT rates answer
+                                (LBM_RATES_SRT), FP64 or FP32 storage, and the pipe wall
+                                (lbm_set_pipe, LBM_BC_IBB); spheres, IBM and the MRT rates answer
                                 LBM_EUNSUPPORTED. Populations in and out (lbm_set_populations,
                                 LBM_FIELD_POPS) then hold 27 planes: rest, 6 faces, 12 edges, 8
                                 corners, each group in lexicographic order of (c_x, c_y, c_z) over
@@ -278,10 +282,12 @@ lbm_status lbm_get_markers(lbm_ctx *ctx, long long capacity, double *X, double *
  * around each group of launches, and a count of every kernel launch.
  * Groups: 0 bulk stream-collide sweep, 1 IBB boundary cells, 2 IBM forcing
  * passes, 3 IBM support-cell collision, 4 particle force/motion, 5 geometry
- * update (flags, refill, link or support lists), 6 statistics.
+ * update (flags, refill, link or support lists), 6 statistics, 7 other
+ * (the IBM rigid-body overwrite), 8 the closure's tensor-core inference
+ * inside lbm_stats (LBM_STATS_CLOSURE).
  * enable = 1 starts recording (and clears totals), 0 stops; out (nullable)
  * receives the totals since the last enable, after synchronising. */
-#define LBM_NGROUPS 8
+#define LBM_NGROUPS 9
 typedef struct {
     double ms[LBM_NGROUPS];
     long long spans[LBM_NGROUPS];     /* timed spans per group */

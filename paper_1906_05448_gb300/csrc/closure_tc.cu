@@ -34,7 +34,12 @@ size_t mlp_pack_bytes();
 
 namespace {
 
-constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16, TC_THREADS = 256;
+#ifndef LBM_TC_THREADS
+#define LBM_TC_THREADS 128  // threads per CTA: 128 (a sample row each) or 256 (two per row)
+#endif
+constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16, TC_THREADS = LBM_TC_THREADS;
+constexpr int TPR = TC_THREADS / TM;  // threads per sample row
+static_assert(TPR == 1 || TPR == 2, "128 or 256 threads");
 constexpr int TC_IN = 85, TC_H = 64, TC_OUT = 9;
 // packed operand block of closure.cu: WT_l [out_pad][in_pad] (BF16)
 constexpr int PW1 = 0, PW2 = PW1 + TC_H * TK1, PW3 = PW2 + TC_H * TC_H, PW4 = PW3 + TC_H * TC_H;
@@ -128,12 +133,6 @@ __device__ __forceinline__ void put8(unsigned short *base, int off, const float 
     *reinterpret_cast<uint4 *>(base + off) = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
 }
 
-__device__ __forceinline__ int twrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-__device__ __forceinline__ double tmimg(double d, int n) {
-    if (d > 0.5 * n) d -= n;
-    else if (d < -0.5 * n) d += n;
-    return d;
-}
 
 }  // namespace
 
@@ -146,8 +145,8 @@ struct TcArgs {
     const unsigned short *pk; // packed BF16 operand block
     // fused: near-surface cells and their nearest particle
     const int *cells, *pid;
-    const float *u;  // FP32 copy of the velocity field (3 planes of N)
-    const double *Xp, *Up, *Wp, *Rp;
+    const float4 *u;         // FP32 copy of the velocity field, (ux, uy, uz, 0) per cell
+    const float4 *pf;        // per particle: closure_particle_kernel's record (4 float4)
     int nx, ny, nz;
     long long N;
     double inv_us, inv_gs, nu;
@@ -155,23 +154,69 @@ struct TcArgs {
     int *err;
 };
 
-// The features of one sample, columns [48 h, 48 h + 48) for half h, BF16
-// into row `row` of the layer-1 operand, 8 columns at a time. FP32 is
-// ample here: the features are rounded to BF16 (8 bits) at once, and only
-// the offset to the particle centre is formed in FP64 (positions reach
-// 2^9, where FP32 would keep 1e-4 of a lattice unit).
-template <int H>
+// Per particle, for the gather: floor of the centre (int), the FP32
+// offset of the centre from it, the radius, U and W (FP32). The features
+// are rounded to BF16 (8 bits) at once, so FP32 is ample for them; the
+// split centre keeps the offset to the particle exact to about 1e-7 lu at
+// any box size (a plain FP32 centre would lose 3e-5 lu at 2^9).
+__global__ void closure_particle_kernel(const double *X, const double *U, const double *W, const double *R, int np,
+                                        float4 *pf) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double x = X[3 * p], y = X[3 * p + 1], z = X[3 * p + 2];
+    const double fx = floor(x), fy = floor(y), fz = floor(z);
+    pf[4 * p] = make_float4(__int_as_float((int)fx), __int_as_float((int)fy), __int_as_float((int)fz), (float)R[p]);
+    pf[4 * p + 1] = make_float4((float)(x - fx), (float)(y - fy), (float)(z - fz), 0.f);
+    pf[4 * p + 2] = make_float4((float)U[3 * p], (float)U[3 * p + 1], (float)U[3 * p + 2], 0.f);
+    pf[4 * p + 3] = make_float4((float)W[3 * p], (float)W[3 * p + 1], (float)W[3 * p + 2], 0.f);
+}
+
+__device__ __forceinline__ float fmimg(float d, int n) {
+    const float h = 0.5f * (float)n;
+    return d > h ? d - (float)n : (d < -h ? d + (float)n : d);
+}
+
+// The features of one sample, columns [48 H0, 48 H1) (H0 = 0, H1 = 2: all
+// 96), BF16 into row `row` of the layer-1 operand, in two halves of 48
+// columns: stencil points 0-15, then points 16-26, the distance to the
+// surface, the node again and 11 zeros. Each half's 16-byte velocity loads
+// are issued together; the second half's lines are first requested into L2
+// (no registers held), so its loads find them there.
+template <int H0, int H1>
 __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigned short *A, int row) {
-    const int c = a.cells[s], p = a.pid[s];
-    const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
-    const float rx = (float)tmimg(x - a.Xp[3 * p], a.nx), ry = (float)tmimg(y - a.Xp[3 * p + 1], a.ny),
-                rz = (float)tmimg(z - a.Xp[3 * p + 2], a.nz);
-    const float U0 = (float)a.Up[3 * p], U1 = (float)a.Up[3 * p + 1], U2 = (float)a.Up[3 * p + 2];
-    const float W0 = (float)a.Wp[3 * p], W1 = (float)a.Wp[3 * p + 1], W2 = (float)a.Wp[3 * p + 2];
+    const unsigned c = (unsigned)a.cells[s];
+    const int p = a.pid[s];
+    const unsigned nxy = (unsigned)a.nx * (unsigned)a.ny;
+    const unsigned z = c / nxy, rem = c - z * nxy, y = rem / (unsigned)a.nx, x = rem - y * (unsigned)a.nx;
+    const float4 P0 = __ldg(a.pf + 4 * p), P1 = __ldg(a.pf + 4 * p + 1), Uv = __ldg(a.pf + 4 * p + 2),
+                 Wv = __ldg(a.pf + 4 * p + 3);
+    const float rx = fmimg((float)((int)x - __float_as_int(P0.x)) - P1.x, a.nx);
+    const float ry = fmimg((float)((int)y - __float_as_int(P0.y)) - P1.y, a.ny);
+    const float rz = fmimg((float)((int)z - __float_as_int(P0.z)) - P1.z, a.nz);
     const float ius = (float)a.inv_us;
-    const long long N = a.N;
+    const int xm = x == 0 ? a.nx - 1 : (int)x - 1, xp = (int)x + 1 == a.nx ? 0 : (int)x + 1;
+    const int ym = y == 0 ? a.ny - 1 : (int)y - 1, yp = (int)y + 1 == a.ny ? 0 : (int)y + 1;
+    const int zm = z == 0 ? a.nz - 1 : (int)z - 1, zp = (int)z + 1 == a.nz ? 0 : (int)z + 1;
+    auto addr = [&](int j) -> const float4 * {  // u at stencil point j (dz, dy, dx in -1..1, dz outermost)
+        const int dx = j % 3 - 1, dy = (j / 3) % 3 - 1, dz = j / 9 - 1;
+        const int xs = dx < 0 ? xm : (dx > 0 ? xp : (int)x), ys = dy < 0 ? ym : (dy > 0 ? yp : (int)y),
+                  zs = dz < 0 ? zm : (dz > 0 ? zp : (int)z);
+        return a.u + ((long long)xs + (long long)a.nx * (ys + (long long)a.ny * zs));
+    };
+    auto rel = [&](int j, const float4 &u, float *o) {  // u - u_rb at point j, scaled
+        const float sx = rx + (float)(j % 3 - 1), sy = ry + (float)((j / 3) % 3 - 1), sz = rz + (float)(j / 9 - 1);
+        o[0] = (u.x - (Uv.x + (Wv.y * sz - Wv.z * sy))) * ius;
+        o[1] = (u.y - (Uv.y + (Wv.z * sx - Wv.x * sz))) * ius;
+        o[2] = (u.z - (Uv.z + (Wv.x * sy - Wv.y * sx))) * ius;
+    };
+    if constexpr (H0 == 0 && H1 == 2) {
+#pragma unroll
+        for (int j = 16; j < 27; j += 3)  // rows of the second half (x - 1 .. x + 1 share a line or two)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(addr(j)));
+    }
+    // values go out 8 columns at a time (compile-time positions after unrolling)
     float buf[8];
-    int fill = 0, col = 48 * H;
+    int fill = 0, col = 0;
     auto push = [&](float v) {
         buf[fill++] = v;
         if (fill == 8) {
@@ -180,30 +225,37 @@ __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigne
             fill = 0;
         }
     };
-    auto rel = [&](int j) {  // u - u_rb at stencil point j (dz, dy, dx in -1..1, dz outermost)
-        const int dx = j % 3 - 1, dy = (j / 3) % 3 - 1, dz = j / 9 - 1;
-        const long long q = (long long)twrap(x + dx, a.nx) + (long long)a.nx * (twrap(y + dy, a.ny) + (long long)a.ny * twrap(z + dz, a.nz));
-        const float sx = rx + (float)dx, sy = ry + (float)dy, sz = rz + (float)dz;
-        const float u0 = __ldg(a.u + q), u1 = __ldg(a.u + N + q), u2 = __ldg(a.u + 2 * N + q);
-        push((u0 - (U0 + (W1 * sz - W2 * sy))) * ius);
-        push((u1 - (U1 + (W2 * sx - W0 * sz))) * ius);
-        push((u2 - (U2 + (W0 * sy - W1 * sx))) * ius);
+    auto push_rel = [&](int j, const float4 &u) {
+        float o[3];
+        rel(j, u, o);
+        push(o[0]);
+        push(o[1]);
+        push(o[2]);
     };
-    if constexpr (H == 0) {
+    if constexpr (H0 == 0) {
+        float4 u[16];
 #pragma unroll
-        for (int j = 0; j < 16; j++) rel(j);  // columns 0..47
-    } else {
+        for (int t = 0; t < 16; t++) u[t] = __ldg(addr(t));
 #pragma unroll
-        for (int j = 16; j < 27; j++) rel(j);  // columns 48..80
-        push(sqrtf(rx * rx + ry * ry + rz * rz) - (float)a.Rp[p]);
-        rel(13);  // the node itself again: columns 82..84
+        for (int t = 0; t < 16; t++) push_rel(t, u[t]);
+    }
+    if constexpr (H1 == 2) {
+        col = 48;
+        float4 u[12];
+#pragma unroll
+        for (int t = 0; t < 11; t++) u[t] = __ldg(addr(16 + t));
+        u[11] = __ldg(addr(13));
+#pragma unroll
+        for (int t = 0; t < 11; t++) push_rel(16 + t, u[t]);
+        push(sqrtf(rx * rx + ry * ry + rz * rz) - P0.w);
+        push_rel(13, u[11]);
 #pragma unroll
         for (int k = 85; k < 96; k++) push(0.f);
     }
 }
 
 #ifndef LBM_TC_CTAS
-#define LBM_TC_CTAS 2  // CTAs per SM (each takes 128 of the 512 tensor-memory columns)
+#define LBM_TC_CTAS (512 / TC_THREADS)  // CTAs per SM (each takes 128 of the 512 tensor-memory columns)
 #endif
 
 template <bool FIELD>
@@ -246,7 +298,7 @@ __global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs 
     const uint32_t T0 = S.taddr;                               // columns 0..63 and 64..127 of this CTA
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const int row = 32 * (warp & 3) + lane;                    // this thread's sample row in the tile
-    const int half = warp >> 2;                                // its column half in the epilogues
+    const int half = TPR == 2 ? warp >> 2 : 0;                 // its column half in the epilogues (two per row)
     uint32_t parity = 0;
     bool ok = true;
     // one layer: MMA over K into TMEM column base tc, then the epilogue of
@@ -264,16 +316,19 @@ __global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs 
         parity ^= 1u;
         fence_after();
     };
+    // the MMA that read the operand has completed (its mbarrier), so the
+    // epilogue overwrites the operand in place; 32 columns at a time
     auto hidden_out = [&](uint32_t tc, int boff) {
-        float v[32];
-        tmem_ld32(T0 + lane_base + tc + 32 * half, v);
-        const int c0 = 32 * half;
 #pragma unroll
-        for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + S.b[boff + c0 + j], 0.f);
-        fence_before();
-        __syncthreads();  // every warp has read the accumulators and the previous operand is no longer read
+        for (int ch = 0; ch < 2 / TPR; ch++) {
+            const int c0 = 32 * (TPR == 2 ? half : ch);
+            float v[32];
+            tmem_ld32(T0 + lane_base + tc + c0, v);
 #pragma unroll
-        for (int g = 0; g < 4; g++) put8(S.a, cm(row, c0 + 8 * g, TKH), v + 8 * g);
+            for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + S.b[boff + c0 + j], 0.f);
+#pragma unroll
+            for (int g = 0; g < 4; g++) put8(S.a, cm(row, c0 + 8 * g, TKH), v + 8 * g);
+        }
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -282,16 +337,54 @@ __global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs 
         const long long s = tile * TM + row;
         // layer-1 operand: 85 features (BF16), zero padding to 96, zero rows past n
         {
-            const int k0 = 48 * half;
             if (FIELD && s < n) {
-                if (half == 0) gather_put<0>(a, s, S.a, row);
-                else gather_put<1>(a, s, S.a, row);
+                if (TPR == 1) gather_put<0, 2>(a, s, S.a, row);
+                else if (half == 0) gather_put<0, 1>(a, s, S.a, row);
+                else gather_put<1, 2>(a, s, S.a, row);
+            } else if (FIELD) {  // rows past n: zeros
+#pragma unroll
+                for (int h = 0; h < 2 / TPR; h++) {
+                    const int k0 = 48 * (TPR == 2 ? half : h);
+                    const float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int g = 0; g < 6; g++) put8(S.a, cm(row, k0 + 8 * g, TK1), f);
+                }
             } else {
-                float f[48];
-#pragma unroll
-                for (int k = 0; k < 48; k++) f[k] = (!FIELD && s < n && k0 + k < TC_IN) ? a.X[s * TC_IN + k0 + k] : 0.f;
-#pragma unroll
-                for (int g = 0; g < 6; g++) put8(S.a, cm(row, k0 + 8 * g, TK1), f + 8 * g);
+                // the tile's rows are one contiguous run of 85 x rows floats:
+                // read it in coalesced 16-byte words (scalar where the words
+                // would pass the array's end or the base is not 16-byte
+                // aligned), each value to its (row, column) of the operand
+                const long long r0 = tile * TM;
+                const int rows = (int)(n - r0 < TM ? n - r0 : TM);
+                const float *base = a.X + r0 * TC_IN;
+                const int nv = rows * TC_IN;
+                auto put1 = [&](int e, float v) {
+                    const int r = e / TC_IN, k = e - r * TC_IN;
+                    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                    S.a[cm(r, k, TK1)] = *reinterpret_cast<const unsigned short *>(&b);
+                };
+                if ((reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+                    const float4 *b4 = reinterpret_cast<const float4 *>(base);
+                    for (int f = tid; 4 * f + 3 < nv; f += TC_THREADS) {
+                        const float4 v = __ldg(b4 + f);
+                        put1(4 * f, v.x);
+                        put1(4 * f + 1, v.y);
+                        put1(4 * f + 2, v.z);
+                        put1(4 * f + 3, v.w);
+                    }
+                    for (int e = (nv & ~3) + tid; e < nv; e += TC_THREADS) put1(e, __ldg(base + e));
+                } else {
+                    for (int e = tid; e < nv; e += TC_THREADS) put1(e, __ldg(base + e));
+                }
+                // zero padding columns 85..95, and whole rows past n
+                for (int e = tid; e < TM * (TK1 - TC_IN); e += TC_THREADS) {
+                    const int r = e / (TK1 - TC_IN), k = TC_IN + e % (TK1 - TC_IN);
+                    S.a[cm(r, k, TK1)] = 0;
+                }
+                for (int e = rows * TC_IN + tid; e < TM * TC_IN; e += TC_THREADS) {
+                    const int r = e / TC_IN, k = e - r * TC_IN;
+                    S.a[cm(r, k, TK1)] = 0;
+                }
             }
         }
         fence_async_smem();
@@ -315,15 +408,17 @@ __global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs 
 #pragma unroll
                 for (int j = 0; j < TC_OUT; j++) y[j] += S.b[192 + j];
                 if constexpr (FIELD) {
-                    double ss = 0.0;
+                    // 2 nu s_ij s_ij in FP32 (the value is stored as FP32)
+                    const float igs = (float)a.inv_gs;
+                    float ss = 0.f;
 #pragma unroll
                     for (int p = 0; p < 3; p++)
 #pragma unroll
                         for (int q = 0; q < 3; q++) {
-                            const double sab = 0.5 * ((double)y[3 * p + q] + (double)y[3 * q + p]) * a.inv_gs;
-                            ss += sab * sab;
+                            const float sab = 0.5f * (y[3 * p + q] + y[3 * q + p]) * igs;
+                            ss = fmaf(sab, sab, ss);
                         }
-                    a.eps_o[a.cells[s]] = (float)(2.0 * a.nu * ss);
+                    a.eps_o[a.cells[s]] = (float)(2.0 * a.nu) * ss;
                 } else {
 #pragma unroll
                     for (int j = 0; j < TC_OUT; j++) a.Y[s * TC_OUT + j] = y[j];
@@ -385,11 +480,11 @@ cudaError_t closure_eps_tc(const Ctx &c, const float *u32, const int *cells, con
     a.pk = (const unsigned short *)pk;
     a.cells = cells;
     a.pid = pid;
-    a.u = u32;
-    a.Xp = c.X;
-    a.Up = c.U;
-    a.Wp = c.W;
-    a.Rp = c.R;
+    a.u = reinterpret_cast<const float4 *>(u32);
+    // FP32 particle records in the closure's output buffer (unused by the fused path)
+    float4 *pf = (float4 *)c.cl_Y;
+    closure_particle_kernel<<<(c.np + 255) / 256, 256, 0, c.stream>>>(c.X, c.U, c.W, c.R, c.np, pf);
+    a.pf = pf;
     a.nx = c.nx;
     a.ny = c.ny;
     a.nz = c.nz;

@@ -22,7 +22,8 @@ __device__ __forceinline__ int dwrap(int a, int n) {
 
 // rho and u of the post-collision state: sum f c = rho u + F/2 after a Guo
 // collision with total force F (body force on fluid cells + IBM force).
-// u32, if not null, receives an FP32 copy of u (the closure's gather input).
+// u32, if not null, receives an FP32 copy of u, one 16-byte record (ux, uy,
+// uz, 0) per cell (the closure's gather input).
 template <int S>
 __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux, const void *sup_Fv, double *rho_o,
                              double *u_o, float *u32, long long N, double F0, double F1, double F2, int ibb, int ibm,
@@ -34,7 +35,7 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
     if (ibb && (fl & FL_SOLID)) {
         rho_o[c] = 0.0;
         u_o[c] = u_o[N + c] = u_o[2 * N + c] = 0.0;
-        if (u32) u32[c] = u32[N + c] = u32[2 * N + c] = 0.f;
+        if (u32) reinterpret_cast<float4 *>(u32)[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     // arithmetic type of the storage (FP32 for the 32- and 16-bit layouts)
@@ -66,9 +67,7 @@ __global__ void macro_kernel(const void *A, const uint8_t *flags, const int *aux
     u_o[N + c] = double(uy);
     u_o[2 * N + c] = double(uz);
     if (u32) {
-        u32[c] = float(ux);
-        u32[N + c] = float(uy);
-        u32[2 * N + c] = float(uz);
+        reinterpret_cast<float4 *>(u32)[c] = make_float4(float(ux), float(uy), float(uz), 0.f);
     }
 }
 
@@ -193,37 +192,82 @@ __global__ void __launch_bounds__(SB) energy_kernel(const double *u, const uint8
         for (int k = 0; k < 7; k++) part[blockIdx.x * NP + 4 + k] = v[k];
 }
 
-// nearest particle surface: key = bits of (r - R_p) > 0 for fluid cells
+// Nearest particle surface of the fluid cells with 0 < s <= reach, s = r -
+// R_p (reach: the farthest distance a caller needs, the closure's 2 or the
+// last radial bin), in one pass: the 64-bit key of a cell holds the bits
+// of s (positive, so ordered as integers) with its low NEAR_PID_BITS bits
+// replaced by the particle id, and atomicMin keeps the nearest. Particles
+// whose s agree in the upper 44 bits (2^-44 relative) count as tied, and
+// the lower id wins. Every particle that could be the nearest of such a
+// cell has it in its box, so the minimum is over all of them; cells
+// farther out keep the empty key. s is formed in FP32 from the split centre
+// (integer part exact, FP32 fraction: error about 1e-6 lu), and in exact
+// FP64 where it lies within 1e-4 of 0 or of reach, so every cell's
+// membership (0 < s <= reach) is that of the FP64 distance; s itself, the
+// order of two particles within 1e-6 of each other and the distance
+// feature carry the FP32 error. The closure's own threshold (2) is decided
+// the same way when the bins reach farther.
+constexpr int NEAR_PID_BITS = 20;
+constexpr unsigned long long NEAR_PID_MASK = (1ULL << NEAR_PID_BITS) - 1;
+constexpr unsigned long long NEAR_EMPTY = ~0ULL;
+__device__ __forceinline__ int near_pid_of(unsigned long long k) { return (int)(k & NEAR_PID_MASK); }
+__device__ __forceinline__ double near_s_of(unsigned long long k) {
+    return __longlong_as_double((long long)(k & ~NEAR_PID_MASK));
+}
+
 __global__ void near_key_kernel(unsigned long long *key, const uint8_t *flags, const double *X, const double *R,
-                                int nx, int ny, int nz, int pass, int *near_pid) {
+                                int nx, int ny, int nz, double reach) {
     const int p = blockIdx.x;
     const double Rp = R[p];
-    const int r = (int)ceil(3.0 * Rp) + 2;
-    const int bx = (int)floor(X[3 * p]) - r, by = (int)floor(X[3 * p + 1]) - r, bz = (int)floor(X[3 * p + 2]) - r;
+    const int r = (int)ceil(Rp + reach) + 2;
+    const double Xd = X[3 * p], Yd = X[3 * p + 1], Zd = X[3 * p + 2];
+    const int bx = (int)floor(Xd) - r, by = (int)floor(Yd) - r, bz = (int)floor(Zd) - r;
     const int w = 2 * r + 2;
     const FastDiv fw((unsigned)w);
+    // the centre relative to the box corner: integer part exact, fraction in FP32
+    const float fX0 = (float)(Xd - bx), fX1 = (float)(Yd - by), fX2 = (float)(Zd - bz);
+    const float Rf = (float)Rp, reachf = (float)reach;
+    const float lo = fmaxf(Rf - 2e-3f, 0.f), hi = Rf + reachf + 2e-3f, lo2 = lo * lo, hi2 = hi * hi;
     for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
         int ix, iy, iz;
         box_coords(t, fw, w, ix, iy, iz);
+        const float ex = ix - fX0, ey = iy - fX1, ez = iz - fX2, e2 = ex * ex + ey * ey + ez * ez;
+        if (e2 > hi2 || e2 < lo2) continue;
         const int x = dwrap(bx + ix, nx), y = dwrap(by + iy, ny),
                   z = dwrap(bz + iz, nz);
         const long long c = (long long)x + (long long)nx * (y + (long long)ny * z);
         if (flags[c] & FL_SOLID) continue;
-        const double dx = dmimg(__dsub_rn((double)x, X[3 * p]), nx);
-        const double dy = dmimg(__dsub_rn((double)y, X[3 * p + 1]), ny);
-        const double dz = dmimg(__dsub_rn((double)z, X[3 * p + 2]), nz);
-        const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-        const double s = __dsub_rn(rr, Rp);
-        if (s <= 0.0) continue;
-        const unsigned long long k = (unsigned long long)__double_as_longlong(s);
-        if (pass == 0) atomicMin(key + c, k);
-        else if (key[c] == k) atomicMin(near_pid + c, p);
+        const float s32 = sqrtf(e2) - Rf;
+        double sd;
+        if (s32 < 1e-4f || fabsf(s32 - reachf) < 1e-4f || fabsf(s32 - 2.0f) < 1e-4f) {  // 2: the closure's band
+            const double dx = dmimg(__dsub_rn((double)x, Xd), nx);
+            const double dy = dmimg(__dsub_rn((double)y, Yd), ny);
+            const double dz = dmimg(__dsub_rn((double)z, Zd), nz);
+            const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            sd = __dsub_rn(rr, Rp);
+        } else {
+            sd = (double)s32;
+        }
+        if (sd <= 0.0 || sd > reach) continue;
+        const unsigned long long k = ((unsigned long long)__double_as_longlong(sd) & ~NEAR_PID_MASK) | (unsigned)p;
+        atomicMin(key + c, k);
     }
+}
+
+// one counter increment per warp for the lanes with `take`; returns this lane's slot
+__device__ __forceinline__ long long warp_slot(bool take, long long *count) {
+    const unsigned m = __ballot_sync(__activemask(), take);
+    if (!take) return -1;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long *)count, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (long long)base + __popc(m & ((1u << lane) - 1u));
 }
 
 constexpr int NBIN = LBM_NBINS;
 
-__global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t *flags, const int *near_pid,
+__global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t *flags, const unsigned long long *near_key,
                                                   const double *X, const double *R, int nx, int ny, int nz,
                                                   long long N, double nu, double *bpart, const float *eps_o) {
     __shared__ double sk[NBIN], se[NBIN], sc[NBIN];
@@ -233,8 +277,9 @@ __global__ void __launch_bounds__(SB) bins_kernel(const double *u, const uint8_t
     // (per-bin sums of a few values each; order effects stay at round-off)
     for (long long c = (long long)blockIdx.x * SB + threadIdx.x; c < N; c += (long long)SNB * SB) {
         if (flags[c] & FL_SOLID) continue;
-        const int p = near_pid[c];
-        if (p == NO_OWNER) continue;
+        const unsigned long long key = near_key[c];
+        if (key == NEAR_EMPTY) continue;
+        const int p = near_pid_of(key);
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
         const double dx = dmimg(__dsub_rn((double)x, X[3 * p]), nx);
         const double dy = dmimg(__dsub_rn((double)y, X[3 * p + 1]), ny);
@@ -260,30 +305,28 @@ __global__ void fill_u64(unsigned long long *p, unsigned long long v, long long 
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
-__global__ void fill_i32(int *p, int v, long long n) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
-}
 
 // ------------------------------------------------------ learned closure --
 // Near-surface fluid nodes (distance to the nearest particle surface in
 // (0, 2]) and their 85 features: the 27-point stencil of u - u_rb (u_rb the
 // rigid-body velocity of the nearest particle), scaled by 1/u_scale, the
 // signed distance / h, and u - u_rb at the node.
-__global__ void closure_sample_kernel(const double *u, const uint8_t *flags, const int *near_pid, const double *X,
-                                      const double *U, const double *W, const double *R, int nx, int ny, int nz,
+__global__ void closure_sample_kernel(const double *u, const uint8_t *flags, const unsigned long long *near_key,
+                                      const double *X, const double *U, const double *W, int nx, int ny, int nz,
                                       long long N, double inv_us, float *feat, int *cells, long long *count,
                                       long long cap) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        if (flags[c] & FL_SOLID) continue;
-        const int p = near_pid[c];
-        if (p == NO_OWNER) continue;
+    // whole warps per round (the slot counter is taken once per warp)
+    const long long span = (long long)gridDim.x * blockDim.x;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < N; c0 += span) {
+        const long long c = c0 + threadIdx.x;
+        const unsigned long long key = c < N && !(flags[c] & FL_SOLID) ? near_key[c] : NEAR_EMPTY;
+        const double d = near_s_of(key);  // r - R_p of the nearest particle
+        const bool take = key != NEAR_EMPTY && d > 0.0 && d <= 2.0;
+        const long long k = warp_slot(take, count);
+        if (!take || k >= cap) continue;
+        const int p = near_pid_of(key);
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
         const double rx = dmimg(x - X[3 * p], nx), ry = dmimg(y - X[3 * p + 1], ny), rz = dmimg(z - X[3 * p + 2], nz);
-        const double d = sqrt(rx * rx + ry * ry + rz * rz) - R[p];
-        if (!(d > 0.0 && d <= 2.0)) continue;
-        const long long k = (long long)atomicAdd((unsigned long long *)count, 1ULL);
-        if (k >= cap) continue;
         cells[k] = (int)c;
         float *f = feat + k * 85;
         int j = 0;
@@ -328,21 +371,18 @@ __global__ void closure_target_kernel(const double *u, const uint8_t *flags, con
 
 // the near-surface fluid nodes of the fused closure dissipation: cell and
 // nearest particle (distance to the surface in (0, 2]); order not fixed
-__global__ void closure_list_kernel(const uint8_t *flags, const int *near_pid, const double *X, const double *R,
-                                    int nx, int ny, int nz, long long N, int *cells, int *pids, long long *count,
-                                    long long cap) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        if (flags[c] & FL_SOLID) continue;
-        const int p = near_pid[c];
-        if (p == NO_OWNER) continue;
-        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
-        const double rx = dmimg(x - X[3 * p], nx), ry = dmimg(y - X[3 * p + 1], ny), rz = dmimg(z - X[3 * p + 2], nz);
-        const double d = sqrt(rx * rx + ry * ry + rz * rz) - R[p];
-        if (!(d > 0.0 && d <= 2.0)) continue;
-        const long long k = (long long)atomicAdd((unsigned long long *)count, 1ULL);
-        if (k >= cap) continue;
+__global__ void closure_list_kernel(const uint8_t *flags, const unsigned long long *near_key, long long N, int *cells,
+                                    int *pids, long long *count, long long cap) {
+    const long long span = (long long)gridDim.x * blockDim.x;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < N; c0 += span) {
+        const long long c = c0 + threadIdx.x;
+        const unsigned long long key = c < N && !(flags[c] & FL_SOLID) ? near_key[c] : NEAR_EMPTY;
+        const double d = near_s_of(key);  // r - R_p of the nearest particle
+        const bool take = key != NEAR_EMPTY && d > 0.0 && d <= 2.0;
+        const long long k = warp_slot(take, count);
+        if (!take || k >= cap) continue;
         cells[k] = (int)c;
-        pids[k] = p;
+        pids[k] = near_pid_of(key);
     }
 }
 
@@ -369,23 +409,23 @@ __global__ void fill_f32(float *p, float v, long long n) {
 }
 
 
-static void near_surface(Ctx &c, const unsigned nb) {
-    count_launch(c, G_STATS, 4);
-    fill_u64<<<nb, 256, 0, c.stream>>>(c.near_key, ~0ULL, c.N);
-    fill_i32<<<nb, 256, 0, c.stream>>>(c.near_pid, NO_OWNER, c.N);
-    near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 0, c.near_pid);
-    near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, 1, c.near_pid);
+// nearest particle and distance to its surface of the fluid cells within
+// `reach` of a surface (key and pid; others NO_OWNER)
+static void near_surface(Ctx &c, const unsigned nb, double reach) {
+    count_launch(c, G_STATS, 2);
+    fill_u64<<<nb, 256, 0, c.stream>>>(c.near_key, NEAR_EMPTY, c.N);
+    near_key_kernel<<<c.np, 256, 0, c.stream>>>(c.near_key, c.flags, c.X, c.R, c.nx, c.ny, c.nz, reach);
 }
 
 cudaError_t closure_samples(Ctx &c, double u_scale, float *X, int *cells, long long cap, long long *n_out) {
     cudaError_t e;
     if ((e = launch_macro(c, 0)) != cudaSuccess) return e;
     const unsigned nb = (unsigned)((c.N + 255) / 256);
-    near_surface(c, nb);
+    near_surface(c, nb, 2.0);
     count_launch(c, G_STATS);
     if ((e = cudaMemsetAsync(c.d_counts + 3, 0, sizeof(long long), c.stream)) != cudaSuccess) return e;
-    closure_sample_kernel<<<1024, 256, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.U, c.W, c.R, c.nx, c.ny, c.nz,
-                                                      c.N, 1.0 / u_scale, X, cells, c.d_counts + 3, cap);
+    closure_sample_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.near_key, c.X, c.U, c.W, c.nx, c.ny, c.nz,
+                                                    c.N, 1.0 / u_scale, X, cells, c.d_counts + 3, cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     long long n = 0;
     if ((e = cudaMemcpyAsync(&n, c.d_counts + 3, sizeof(long long), cudaMemcpyDeviceToHost, c.stream)) != cudaSuccess)
@@ -486,8 +526,8 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     const int ibb = c.armed_bc == LBM_BC_IBB;
     const int ibm = c.armed_bc == LBM_BC_IBM_U || c.armed_bc == LBM_BC_IBM_B;
     const bool closure = (flags & LBM_STATS_CLOSURE) && c.np > 0 && c.cl_ready && c.max_cl > 0 && c.q == 19;
-    // the closure gathers an FP32 copy of u, kept in the population buffer
-    // that the next step overwrites
+    // the closure gathers an FP32 copy of u (16 B per cell), kept in the
+    // population buffer that the next step overwrites (19 x 2 B per cell or more)
     float *u32 = closure ? (float *)c.fB : nullptr;
     if ((e = launch_macro(c, 0, u32)) != cudaSuccess) return e;
     count_launch(c, G_STATS, 3);
@@ -497,22 +537,28 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     const double nu = (c.tau - 0.5) / 3.0;
     const bool bins = (flags & LBM_STATS_BINS) && c.np > 0;
     const float *eps_o = nullptr;
-    if (bins || closure) near_surface(c, nb);
+    // the bins reach r/R_p = 1 + 0.05 NBIN; the closure 2 lattice units from the surface
+    double reach = bins ? 0.05 * NBIN * c.max_radius : 0.0;
+    if (closure && reach < 2.0) reach = 2.0;
+    if (bins || closure) near_surface(c, nb, reach);
     if (closure) {
         // learned gradients at the near-surface nodes (unmasked velocity in):
         // list the nodes, then one tensor-core kernel gathers each node's
         // features, runs the network and writes the dissipation at the cell
-        count_launch(c, G_STATS, 5);
+        count_launch(c, G_STATS, 4);
         fill_f32<<<nb, 256, 0, c.stream>>>(c.cl_eps, -1.f, c.N);
         if ((e = cudaMemsetAsync(c.d_counts + 3, 0, sizeof(long long), c.stream)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(c.d_status + 1, 0, sizeof(unsigned), c.stream)) != cudaSuccess) return e;
         int *pids = (int *)c.cl_X;  // the feature buffer is not needed by the fused path
-        closure_list_kernel<<<1024, 256, 0, c.stream>>>(c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N,
-                                                        c.cl_cells, pids, c.d_counts + 3, c.max_cl);
+        closure_list_kernel<<<nb, 256, 0, c.stream>>>(c.flags, c.near_key, c.N, c.cl_cells, pids, c.d_counts + 3,
+                                                      c.max_cl);
         if ((e = mlp_pack_device(c.cl_w, c.cl_pk, c.stream)) != cudaSuccess) return e;
+        cudaEvent_t t0 = prof_event(c);
+        count_launch(c, G_CLOSURE, 2);  // particle records, inference
         if ((e = closure_eps_tc(c, u32, c.cl_cells, pids, c.d_counts + 3, c.max_cl, c.cl_pk, c.cl_eps,
                                 (int *)(c.d_status + 1))) != cudaSuccess)
             return e;
+        prof_span(c, G_CLOSURE, t0, prof_event(c));
         eps_o = c.cl_eps;
     }
     if (mask) mask_kernel<<<nb, 256, 0, c.stream>>>(c.u_f, c.flags, c.owner, c.X, c.U, c.W, c.nx, c.ny, c.nz, c.N);
@@ -520,7 +566,7 @@ cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *o) {
     double *bpart = c.partials + SNB * NP;
     if (bins) {
         count_launch(c, G_STATS);
-        bins_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.near_pid, c.X, c.R, c.nx, c.ny, c.nz, c.N, nu, bpart,
+        bins_kernel<<<SNB, SB, 0, c.stream>>>(c.u_f, c.flags, c.near_key, c.X, c.R, c.nx, c.ny, c.nz, c.N, nu, bpart,
                                               eps_o);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -321,6 +321,10 @@ constexpr int CT = 256;        // threads per tile block
 constexpr int CPT = 4;         // cells per thread
 constexpr int TILE = CT * CPT;
 
+struct __align__(32) SiteGeo {
+    double dx, dy, dz, c0;
+};
+
 struct SiteArgs {
     uint8_t *flags;
     const int *owner;
@@ -342,6 +346,11 @@ struct SiteArgs {
     FastDiv dx, dxy;  // division by nx and nx * ny
     double dn[3], hn[3];  // nx, ny, nz and their halves as doubles
     int *sn_list;         // links of the single-node scheme (appended, counts[4])
+    // 32/16-bit storage with particles: per site, the offset d = x - X_p to
+    // its first solid neighbour's particle and c0 = |d|^2 - R_p^2 (FP64),
+    // and that particle; null otherwise (every link forms them itself)
+    SiteGeo *site_geo;
+    int *site_own;
 };
 
 // minimum image with the box size and its half given as doubles (no
@@ -578,7 +587,47 @@ __device__ __forceinline__ double exact_div_c2(double v, double c2) {
     return c2 == 1.0 ? v : (c2 == 2.0 ? v * 0.5 : __ddiv_rn(v, c2));
 }
 
-__device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, double &q, int &pid, int &scheme) {
+// q to FP32 accuracy (32/16-bit storage). The smaller root of
+// a t^2 + 2 b t + c0 = 0 is (-b - s)/a = c0/(s - b), s = sqrt(b^2 - a c0);
+// for a link into the sphere c0 > 0 and b < 0 (the quadratic falls from
+// c0 at t = 0 to <= 0 at t = 1), so s - b adds two positive numbers and
+// the quotient keeps FP32's relative accuracy: with the discriminant in
+// FP64 as in the exact form, the error is below 3e-7. Within 1e-5 of 1/2,
+// where q picks the scheme, the exact FP64 form decides, so the link lists
+// are those of the exact q.
+__device__ __forceinline__ double fast_root(double b, double disc, double c0, bool diag) {
+    const float qf = (float)c0 / (sqrtf((float)disc) - (float)b);
+    if (fabsf(qf - 0.5f) >= 1e-5f) return (double)qf;
+    const double num = __dsub_rn(-b, __dsqrt_rn(disc));
+    return diag ? num * 0.5 : num;
+}
+
+// per site: d and c0 of the particle that owns the site's first solid neighbour
+__global__ void __launch_bounds__(256) site_geo_kernel(SiteArgs a) {
+    const long long ns = a.counts[0] < a.max_sites ? a.counts[0] : a.max_sites;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < ns;
+         s += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = (unsigned)a.site_cell[s];
+        const unsigned m = a.site_mask[s];
+        const unsigned zq = a.dxy.div(c), rem = c - zq * (unsigned)(a.nx * a.ny);
+        const unsigned yq = a.dx.div(rem);
+        const int x = (int)(rem - yq * (unsigned)a.nx), y = (int)yq, z = (int)zq;
+        const int l = m ? __ffs(m) - 1 : 1;
+        const int xb = gwrap(x + cx(l), a.nx), yb = gwrap(y + cy(l), a.ny), zb = gwrap(z + cz(l), a.nz);
+        const int own = a.owner[(long long)xb + (long long)a.nx * (yb + (long long)a.ny * zb)];
+        a.site_own[s] = own;
+        if (own == NO_OWNER) continue;
+        const double *Xp = a.X + 3 * own;
+        const double Rp = a.R[own];
+        const double dx = gmimg_d(__dsub_rn((double)x, Xp[0]), a.dn[0], a.hn[0]);
+        const double dy = gmimg_d(__dsub_rn((double)y, Xp[1]), a.dn[1], a.hn[1]);
+        const double dz = gmimg_d(__dsub_rn((double)z, Xp[2]), a.dn[2], a.hn[2]);
+        a.site_geo[s] = SiteGeo{dx, dy, dz, __dsub_rn(dist2(dx, dy, dz), __dmul_rn(Rp, Rp))};
+    }
+}
+
+__device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, double &q, int &pid, int &scheme,
+                              long long site = -1) {
     const int xb = gwrap(x + cx(l), a.nx), yb = gwrap(y + cy(l), a.ny), zb = gwrap(z + cz(l), a.nz);
     const long long cb = (long long)xb + (long long)a.nx * (yb + (long long)a.ny * zb);
     const int own = a.owner[cb];
@@ -594,11 +643,21 @@ __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, dou
     double t;
     if (own != NO_OWNER) {
         pid = own;
-        const double *Xp = a.X + 3 * own;
-        const double Rp = a.R[own];
-        const double dx = gmimg_d(__dsub_rn((double)x, Xp[0]), a.dn[0], a.hn[0]);
-        const double dy = gmimg_d(__dsub_rn((double)y, Xp[1]), a.dn[1], a.hn[1]);
-        const double dz = gmimg_d(__dsub_rn((double)z, Xp[2]), a.dn[2], a.hn[2]);
+        double dx, dy, dz, c0;
+        if (site >= 0 && a.site_own[site] == own) {
+            const SiteGeo g = a.site_geo[site];
+            dx = g.dx;
+            dy = g.dy;
+            dz = g.dz;
+            c0 = g.c0;
+        } else {
+            const double *Xp = a.X + 3 * own;
+            const double Rp = a.R[own];
+            dx = gmimg_d(__dsub_rn((double)x, Xp[0]), a.dn[0], a.hn[0]);
+            dy = gmimg_d(__dsub_rn((double)y, Xp[1]), a.dn[1], a.hn[1]);
+            dz = gmimg_d(__dsub_rn((double)z, Xp[2]), a.dn[2], a.hn[2]);
+            c0 = __dsub_rn(dist2(dx, dy, dz), __dmul_rn(Rp, Rp));
+        }
         // b = c_l . d as ((c0 dx + c1 dy) + c2 dz): with components in
         // {-1, 0, 1} this is the sum of the one or two nonzero terms, which
         // gives the same bits whenever that sum is not zero; a zero sum takes
@@ -607,11 +666,14 @@ __device__ void link_geometry(const SiteArgs &a, int x, int y, int z, int l, dou
         const double v = !diag ? 0.0 : (i2 ? (i2 > 0 ? dz : -dz) : (i1 > 0 ? dy : -dy));
         double b = __dadd_rn(u, v);
         if (b == 0.0) b = __dadd_rn(__dadd_rn(__dmul_rn(cl0, dx), __dmul_rn(cl1, dy)), __dmul_rn(cl2, dz));
-        const double c0 = __dsub_rn(dist2(dx, dy, dz), __dmul_rn(Rp, Rp));
         double disc = __dsub_rn(__dmul_rn(b, b), __dmul_rn(aa, c0));
         if (disc < 0.0) disc = 0.0;
-        const double num = __dsub_rn(-b, __dsqrt_rn(disc));
-        t = diag ? num * 0.5 : num;  // division by |c_l|^2 = 1 or 2, exact
+        if (site >= 0) {
+            t = fast_root(b, disc, c0, diag);
+        } else {
+            const double num = __dsub_rn(-b, __dsqrt_rn(disc));
+            t = diag ? num * 0.5 : num;  // division by |c_l|^2 = 1 or 2, exact
+        }
     } else {
         pid = -1;
         const double a2 = (double)(cx(l) * cx(l) + cy(l) * cy(l));
@@ -705,7 +767,7 @@ __global__ void __launch_bounds__(256) link_geom_kernel(SiteArgs a) {
         const int x = (int)(rem - yq * (unsigned)a.nx), y = (int)yq, z = (int)zq;
         double q;
         int pid, sch;
-        link_geometry(a, x, y, z, l, q, pid, sch);
+        link_geometry(a, x, y, z, l, q, pid, sch, a.site_geo ? (long long)a.aux[c] : -1LL);
         if (sch == 2) {  // listed for the single-node pass of the step
             const long long j = (long long)atomicAdd((unsigned long long *)(a.counts + 4), 1ULL);
             if (j < a.max_links) a.sn_list[j] = (int)k;
@@ -876,6 +938,11 @@ cudaError_t build_sites(Ctx &c, int mode) {
     a.dx = FastDiv((unsigned)c.nx);
     a.dxy = FastDiv((unsigned)(c.nx * c.ny));
     a.sn_list = c.sn_list;
+    // per-site geometry for 32/16-bit storage with particles, kept in the
+    // IBM per-site arrays (unused by IBB)
+    const bool fast_q = mode == 1 && c.np > 0 && c.storage != LBM_F64;
+    a.site_geo = fast_q ? (SiteGeo *)c.sup_ru : nullptr;
+    a.site_own = fast_q ? (int *)c.sup_F : nullptr;
     const int nd[3] = {c.nx, c.ny, c.nz};
     for (int d = 0; d < 3; d++) {
         a.dn[d] = (double)nd[d];
@@ -884,7 +951,7 @@ cudaError_t build_sites(Ctx &c, int mode) {
     if (mode == 1 && c.np > 0 && LBM_LOCAL_SITES) {
         // particles: local marking, then the ordered compaction of the flags
         const int nblk = (int)((c.N + VTILE - 1) / VTILE);
-        count_launch(c, G_GEOM, 5);
+        count_launch(c, G_GEOM, 6);  // with the link pass below
         bnd_clear_kernel<<<(unsigned)std::min<long long>(152LL * 8, (c.max_sites + 255) / 256), 256, 0, c.stream>>>(
             c.flags, c.site_cell, c.d_counts, c.max_sites);
         bnd_mark_kernel<<<c.np, 256, 0, c.stream>>>(a);
@@ -906,6 +973,13 @@ cudaError_t build_sites(Ctx &c, int mode) {
         long long nb = (n + 255) / 256;
         if (nb < 1) nb = 1;
         if (nb > 152LL * 64) nb = 152LL * 64;
+        if (a.site_geo) {
+            long long sb = ((c.nlinks_hint > 0 ? c.nlinks_hint : c.max_sites) + 255) / 256;
+            if (sb > 152LL * 16) sb = 152LL * 16;
+            if (sb < 1) sb = 1;
+            count_launch(c, G_GEOM);
+            site_geo_kernel<<<(unsigned)sb, 256, 0, c.stream>>>(a);
+        }
         link_geom_kernel<<<(unsigned)nb, 256, 0, c.stream>>>(a);
     }
     return cudaGetLastError();

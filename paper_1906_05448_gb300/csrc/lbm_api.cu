@@ -52,10 +52,10 @@ struct Plan {
     long long max_xy;
     size_t pX, pXold, pU, pW, pR, pmass, pinertia, pFh, pTh, pFprev, pTprev, pFc, pIu, pIr, phas, pXf, sn_list;
     size_t mX, mUnit, mdV, mUd, mFaccR, mFacc, mFr, mB, mE, mpid, mfirst;
-    size_t rho_f, u_f, partials, near_key, near_pid;
+    size_t rho_f, u_f, partials, near_key;
     size_t cl_w, cl_pk, cl_X, cl_Y, cl_cells, cl_eps;
     long long max_cl;
-    size_t q27_colmask;
+    size_t q27_colmask, q27_hmask, q27_coef;
     size_t total;
 };
 
@@ -64,6 +64,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     if (g->storage < LBM_F64 || g->storage > LBM_BF16S) return false;
     if (g->rates != LBM_RATES_SRT && g->rates != LBM_RATES_DHUMIERES) return false;
     if (g->max_particles < 0 || g->max_links < 0 || g->max_markers < 0 || g->max_sites < 0) return false;
+    if (g->max_particles > LBM_MAX_PARTICLES) return false;
     if (g->lattice != 0 && g->lattice != 19 && g->lattice != 27) return false;
     // D3Q27: periodic box, BGK, FP64 or FP32 storage
     if (g->lattice == 27 && (g->rates != LBM_RATES_SRT || (g->storage != LBM_F64 && g->storage != LBM_F32)))
@@ -154,7 +155,6 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.u_f = L.take(24 * n);
     P.partials = L.take(8 * stats_partials_doubles());
     P.near_key = L.take(8 * n);
-    P.near_pid = L.take(4 * n);
     P.max_cl = P.max_np > 0 ? 1500LL * P.max_np : 0;
     P.cl_w = L.take(4 * 14409);
     P.cl_pk = L.take(mlp_pack_bytes());
@@ -163,6 +163,8 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.cl_cells = L.take(4 * (size_t)P.max_cl);
     P.cl_eps = L.take(P.max_cl > 0 ? 4 * n : 0);
     P.q27_colmask = L.take(g->lattice == 27 ? 4 * (size_t)g->nx * g->ny : 0);
+    P.q27_hmask = L.take(g->lattice == 27 ? 4 * (size_t)g->nx * g->ny : 0);
+    P.q27_coef = L.take(g->lattice == 27 ? 2 * sb * 27 * (size_t)g->nx * g->ny : 0);
     P.total = L.off;
     return true;
 }
@@ -526,6 +528,9 @@ lbm_status arm(Ctx &c, int bc) {
 }
 
 }  // namespace
+
+cudaEvent_t prof_event(Ctx &c) { return pmark(c); }
+void prof_span(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b) { pspan(c, g, a, b); }
 }  // namespace lbmgb
 
 using namespace lbmgb;
@@ -649,7 +654,6 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.u_f = (double *)(b + P.u_f);
     c.partials = (double *)(b + P.partials);
     c.near_key = (unsigned long long *)(b + P.near_key);
-    c.near_pid = (int *)(b + P.near_pid);
     c.cl_w = (float *)(b + P.cl_w);
     c.cl_pk = b + P.cl_pk;
     c.cl_X = (float *)(b + P.cl_X);
@@ -658,6 +662,8 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.cl_eps = (float *)(b + P.cl_eps);
     c.max_cl = P.max_cl;
     c.q27_colmask = (unsigned *)(b + P.q27_colmask);
+    c.q27_hmask = (unsigned *)(b + P.q27_hmask);
+    c.q27_coef = (void *)(b + P.q27_coef);
     c.armed_bc = -1;
     c.wait_limit_s = 600.0;
     c.pipe_cx = 0.5 * (c.nx - 1);
@@ -732,6 +738,7 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
         std::vector<unsigned> mask;
         q27_pipe_colmask(c, mask);
         CK(cudaMemcpy(c.q27_colmask, mask.data(), sizeof(unsigned) * mask.size(), cudaMemcpyHostToDevice));
+        CK(launch_q27_coef(c));
         return sync_all(c);
     }
     c.has_pipe = 1;

@@ -24,6 +24,8 @@ struct Ctx {
     int storage, rates;
     int q = 19;  // velocity set: 19 (every path) or 27 (periodic box or pipe with IBB, BGK)
     unsigned *q27_colmask;  // D3Q27 pipe: per (x, y) column, the directions whose column is solid
+    unsigned *q27_hmask;    // D3Q27 pipe: per column, the wall directions with q >= 1/2
+    void *q27_coef;         // D3Q27 pipe: per column and direction, the two wall weights
     Rates rt;
     cudaStream_t stream;
     char *ws;
@@ -109,8 +111,7 @@ struct Ctx {
     int pipe_sp, pipe_max_ring;
     // statistics scratch
     double *rho_f, *u_f, *partials;
-    unsigned long long *near_key;
-    int *near_pid;
+    unsigned long long *near_key;  // nearest particle surface per cell (diag.cu)
     // status
     unsigned *d_status;
     unsigned *h_status;
@@ -144,7 +145,7 @@ inline void count_launch(Ctx &c, int group, int n = 1) {
     c.launches += n;
     c.group_launches[group] += n;
 }
-enum { G_BULK = 0, G_BND = 1, G_IBM = 2, G_IBMCOL = 3, G_PART = 4, G_GEOM = 5, G_STATS = 6, G_OTHER = 7 };
+enum { G_BULK = 0, G_BND = 1, G_IBM = 2, G_IBMCOL = 3, G_PART = 4, G_GEOM = 5, G_STATS = 6, G_OTHER = 7, G_CLOSURE = 8 };
 
 }  // namespace lbmgb
 
@@ -160,6 +161,8 @@ cudaError_t launch_get_populations(Ctx &c, double *f_dev);
 cudaError_t launch_stream_collide(Ctx &c, int bc);
 bool launch_pipe_sweep(Ctx &c, cudaError_t &err);  // sweep_pipe.cu: false when it does not apply
 cudaError_t launch_ibb_links(Ctx &c);
+cudaEvent_t prof_event(Ctx &c);  // profiling event on the stream (null when off)
+void prof_span(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b);  // time from a to b into group g
 cudaError_t launch_ibm_collide(Ctx &c);
 cudaError_t launch_pipe_flags(Ctx &c);
 cudaError_t launch_sphere_mark(Ctx &c, bool clear_old);
@@ -187,6 +190,7 @@ cudaError_t launch_q27_init(Ctx &c, const double *u_dev, double rho0);
 cudaError_t q27_plane_copy(Ctx &c, int i, bool to_f64);
 cudaError_t launch_q27_macro(Ctx &c);
 void q27_pipe_colmask(const Ctx &c, std::vector<unsigned> &mask);
+cudaError_t launch_q27_coef(Ctx &c);
 size_t tke_budget_scratch_bytes(int nbins);
 size_t spectrum_scratch_bytes(long long N, int nbins);
 cudaError_t run_stats(Ctx &c, int flags, lbm_stats_t *out);

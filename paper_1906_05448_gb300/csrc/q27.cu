@@ -170,11 +170,58 @@ static_assert(q27opp(0) == 0 && q27opp(1) == 6 && q27opp(26) == 19, "opposites")
 // The geometry is the same in every z plane: per (x, y) column a 27-bit
 // mask (bit i: the column x + c_i, y + c_i is solid; bit 0: the column
 // itself) tells which pulls come from the wall. Solid cells are not swept.
+// The weights of the two populations of each wall link are formed once, at
+// set-up (q27_coef_kernel), per column and direction: (2q, 1 - 2q) with
+// f*_i(x_f - c_i), (1, 0) for the halfway fallback, and
+// (1/(2q), (2q - 1)/(2q)) with f*_j(x_f), the last flagged in hmask.
 struct Q27PipeArgs {
     Q27Args b;
-    const unsigned *colmask;
-    double pcx, pcy, R2;
+    const unsigned *colmask, *hmask;
+    const void *coef;  // per column x 27 directions: two weights in the arithmetic type
 };
+
+template <typename R>
+struct Q27Coef {
+    R k1, k2;
+};
+
+template <int S>
+__global__ void q27_coef_kernel(const unsigned *colmask, unsigned *hmask, void *coefv, int nx, int ny, double pcx,
+                                double pcy, double R2) {
+    typedef typename Store<S>::R R;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nx * ny) return;
+    const unsigned m = colmask[col];
+    Q27Coef<R> *coef = (Q27Coef<R> *)coefv + (size_t)col * Q27;
+    unsigned h = 0;
+    if (!(m & 1u) && m) {
+        const int x = col % nx, y = col / nx;
+        const double dx = (double)x - pcx, dy = (double)y - pcy;
+        const double c0 = dx * dx + dy * dy - R2;
+        for (int i = 1; i < Q27; i++) {
+            if (!((m >> i) & 1u)) continue;
+            const double aa = (double)(q27x(i) * q27x(i) + q27y(i) * q27y(i));
+            const double b = q27x(i) * dx + q27y(i) * dy;
+            const double q = (-b + sqrt(b * b - aa * c0)) / aa;
+            Q27Coef<R> k;
+            if (q < 0.5) {
+                if ((m >> q27opp(i)) & 1u) {  // x_f - c_i solid too: halfway
+                    k.k1 = R(1);
+                    k.k2 = R(0);
+                } else {
+                    k.k1 = R(2.0 * q);
+                    k.k2 = R(1.0 - 2.0 * q);
+                }
+            } else {
+                k.k1 = R(1.0 / (2.0 * q));
+                k.k2 = R((2.0 * q - 1.0) / (2.0 * q));
+                h |= 1u << i;
+            }
+            coef[i] = k;
+        }
+    }
+    hmask[col] = h;
+}
 
 template <int S, bool FORCE>
 __global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
@@ -204,26 +251,19 @@ __global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
         g[i] = Store<S>::ld(A + (i * N + (size_t)(xs + nx * (ys + ny * zs))));
     }
     if (m) {  // wall cell: the populations coming back from the wall
-        const double dx = (double)x - pa.pcx, dy = (double)y - pa.pcy;
-        const double c0 = dx * dx + dy * dy - pa.R2;
+        const unsigned h = __ldg(pa.hmask + rem);
+        const Q27Coef<R> *kc = (const Q27Coef<R> *)pa.coef + (size_t)rem * Q27;
 #pragma unroll
         for (int i = 1; i < Q27; i++) {
             if (!((m >> i) & 1u)) continue;
             const int j = q27opp(i);
-            const double aa = (double)(q27x(i) * q27x(i) + q27y(i) * q27y(i));
-            const double b = q27x(i) * dx + q27y(i) * dy;
-            const double q = (-b + sqrt(b * b - aa * c0)) / aa;
+            const Q27Coef<R> k = kc[i];
             const R fi = Store<S>::ld(A + (i * N + (size_t)c));  // f*_i(x_f)
-            R v;
-            if (q < 0.5) {
-                // f*_i(x_f - c_i) is the regular pull of direction i
-                v = ((m >> j) & 1u) ? fi : R(2.0 * q) * fi + R(1.0 - 2.0 * q) * g[i];
-            } else {
-                const R fj = Store<S>::ld(A + (j * N + (size_t)c));  // f*_j(x_f)
-                v = R(1.0 / (2.0 * q)) * fi + R((2.0 * q - 1.0) / (2.0 * q)) * fj;
-            }
+            // q < 1/2: f*_i(x_f - c_i), the regular pull of direction i
+            // (weight 0 for the halfway fallback); q >= 1/2: f*_j(x_f)
+            const R second = ((h >> i) & 1u) ? Store<S>::ld(A + (j * N + (size_t)c)) : g[i];
             // the bounce-back acts on f, the storage holds g = f - w with w_i = w_j
-            g[j] = v;
+            g[j] = k.k1 * fi + k.k2 * second;
         }
     }
     R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
@@ -281,7 +321,7 @@ cudaError_t launch_q27_step(Ctx &c) {
     const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
     count_launch(c, G_BULK);
     if (c.has_pipe) {
-        Q27PipeArgs pa{a, c.q27_colmask, c.pipe_cx, c.pipe_cy, c.pipe_R * c.pipe_R};
+        Q27PipeArgs pa{a, c.q27_colmask, c.q27_hmask, c.q27_coef};
         const unsigned nb = (unsigned)((c.N + 255) / 256);
         if (c.storage == LBM_F64) {
             if (force) q27_pipe_kernel<LBM_F64, true><<<nb, 256, 0, c.stream>>>(pa);
@@ -313,6 +353,19 @@ void q27_pipe_colmask(const Ctx &c, std::vector<unsigned> &mask) {
                 if (solid(x + q27x(i), y + q27y(i))) m |= 1u << i;
             mask[(size_t)x + (size_t)c.nx * y] = m;
         }
+}
+
+// the wall weights of the pipe (after the column masks are uploaded)
+cudaError_t launch_q27_coef(Ctx &c) {
+    const unsigned nb = (unsigned)((c.nx * c.ny + 255) / 256);
+    const double R2 = c.pipe_R * c.pipe_R;
+    if (c.storage == LBM_F64)
+        q27_coef_kernel<LBM_F64><<<nb, 256, 0, c.stream>>>(c.q27_colmask, c.q27_hmask, c.q27_coef, c.nx, c.ny,
+                                                            c.pipe_cx, c.pipe_cy, R2);
+    else
+        q27_coef_kernel<LBM_F32><<<nb, 256, 0, c.stream>>>(c.q27_colmask, c.q27_hmask, c.q27_coef, c.nx, c.ny,
+                                                            c.pipe_cx, c.pipe_cy, R2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_q27_init(Ctx &c, const double *u_dev, double rho0) {

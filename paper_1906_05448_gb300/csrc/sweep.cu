@@ -36,6 +36,10 @@ struct SweepArgs {
     void *bvals;           // wall cells' populations for the next ghost pass (storage type), or null
     const uint2 *wrec;     // per wall cell: first compact ghost value, replaced directions
     const void *gvals;     // compact ghost values of this step (storage type)
+    // plane bases A + i N and B + i N: one address operation per access
+    // (as in the pipe sweep, where it cut the sweep from 0.2273 to 0.2144 ms)
+    const void *Ap[19];
+    void *Bp[19];
 };
 
 // BC: 0 periodic, 1 IBB, 2 IBM
@@ -79,7 +83,6 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
     const long long items = segs ? a.nseg : a.nflat;
     const long long stride = segs ? (long long)gridDim.x * (blockDim.x / 32) : (long long)gridDim.x;
     const T *__restrict__ A = (const T *)a.A;
-    T *__restrict__ B = (T *)a.B;
     // element index type: 32-bit when every index fits (19 N < 2^32), so an
     // address is one 32-bit add and one scaled add to the plane base
     typedef typename std::conditional<IDX32, unsigned, size_t>::type IX;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         if (zero) {
             const long long cz = (long long)row * nx + x;
 #pragma unroll
-            for (int i = 0; i < 19; i++) Store<S>::st(B + (IX(i) * N + IX(cz)), R(0));
+            for (int i = 0; i < 19; i++) Store<S>::st((T *)a.Bp[i] + IX(cz), R(0));
             continue;
         }
         if (x >= nx) continue;
@@ -188,24 +191,24 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
                 return pull;
         };
         g[0] = ld(A + IX(c));
-        g[1] = ld(pick(1, A + (IX(1) * N + IX(r00 + xm))));
-        g[2] = ld(pick(2, A + (IX(2) * N + IX(r00 + xp))));
-        g[3] = ld(pick(3, A + (IX(3) * N + IX(rM0 + x))));
-        g[4] = ld(pick(4, A + (IX(4) * N + IX(rP0 + x))));
-        g[5] = ld(pick(5, A + (IX(5) * N + IX(r0M + x))));
-        g[6] = ld(pick(6, A + (IX(6) * N + IX(r0P + x))));
-        g[7] = ld(pick(7, A + (IX(7) * N + IX(rM0 + xm))));
-        g[8] = ld(pick(8, A + (IX(8) * N + IX(rP0 + xp))));
-        g[9] = ld(pick(9, A + (IX(9) * N + IX(rP0 + xm))));
-        g[10] = ld(pick(10, A + (IX(10) * N + IX(rM0 + xp))));
-        g[11] = ld(pick(11, A + (IX(11) * N + IX(r0M + xm))));
-        g[12] = ld(pick(12, A + (IX(12) * N + IX(r0P + xp))));
-        g[13] = ld(pick(13, A + (IX(13) * N + IX(r0P + xm))));
-        g[14] = ld(pick(14, A + (IX(14) * N + IX(r0M + xp))));
-        g[15] = ld(pick(15, A + (IX(15) * N + IX(rMM + x))));
-        g[16] = ld(pick(16, A + (IX(16) * N + IX(rPP + x))));
-        g[17] = ld(pick(17, A + (IX(17) * N + IX(rMP + x))));
-        g[18] = ld(pick(18, A + (IX(18) * N + IX(rPM + x))));
+        g[1] = ld(pick(1, (const T *)a.Ap[1] + IX(r00 + xm)));
+        g[2] = ld(pick(2, (const T *)a.Ap[2] + IX(r00 + xp)));
+        g[3] = ld(pick(3, (const T *)a.Ap[3] + IX(rM0 + x)));
+        g[4] = ld(pick(4, (const T *)a.Ap[4] + IX(rP0 + x)));
+        g[5] = ld(pick(5, (const T *)a.Ap[5] + IX(r0M + x)));
+        g[6] = ld(pick(6, (const T *)a.Ap[6] + IX(r0P + x)));
+        g[7] = ld(pick(7, (const T *)a.Ap[7] + IX(rM0 + xm)));
+        g[8] = ld(pick(8, (const T *)a.Ap[8] + IX(rP0 + xp)));
+        g[9] = ld(pick(9, (const T *)a.Ap[9] + IX(rP0 + xm)));
+        g[10] = ld(pick(10, (const T *)a.Ap[10] + IX(rM0 + xp)));
+        g[11] = ld(pick(11, (const T *)a.Ap[11] + IX(r0M + xm)));
+        g[12] = ld(pick(12, (const T *)a.Ap[12] + IX(r0P + xp)));
+        g[13] = ld(pick(13, (const T *)a.Ap[13] + IX(r0P + xm)));
+        g[14] = ld(pick(14, (const T *)a.Ap[14] + IX(r0M + xp)));
+        g[15] = ld(pick(15, (const T *)a.Ap[15] + IX(rMM + x)));
+        g[16] = ld(pick(16, (const T *)a.Ap[16] + IX(rPP + x)));
+        g[17] = ld(pick(17, (const T *)a.Ap[17] + IX(rMP + x)));
+        g[18] = ld(pick(18, (const T *)a.Ap[18] + IX(rPM + x)));
 
         if (LBM_BULK_SPEC && BC == 1 && (fl & FL_SOLID)) continue;
         const bool fluid = !(fl & FL_SOLID);
@@ -249,8 +252,8 @@ __global__ void __launch_bounds__(256, bulk_min_blocks(S, SRT, BC)) stream_colli
         }
 #pragma unroll
         for (int i = 0; i < 19; i++) {
-            if constexpr (scaled) Store<LBM_F16S>::st_scaled(B + (IX(i) * N + IX(c)), g[i]);
-            else Store<S>::st(B + (IX(i) * N + IX(c)), g[i]);
+            if constexpr (scaled) Store<LBM_F16S>::st_scaled((T *)a.Bp[i] + IX(c), g[i]);
+            else Store<S>::st((T *)a.Bp[i] + IX(c), g[i]);
         }
         if (keep_walls && ((bd.y >> lane) & 1u)) {
             // a wall cell: the same 19 stored values, contiguous, for the ghost pass
@@ -270,6 +273,10 @@ static cudaError_t launch_bulk_t(Ctx &c, bool force) {
     SweepArgs a{};
     a.A = c.fA;
     a.B = c.fB;
+    for (int i = 0; i < 19; i++) {
+        a.Ap[i] = (const void *)((const char *)c.fA + storage_bytes(c.storage) * (size_t)i * (size_t)c.N);
+        a.Bp[i] = (void *)((char *)c.fB + storage_bytes(c.storage) * (size_t)i * (size_t)c.N);
+    }
     a.flags = c.flags;
     a.aux = c.aux;
     a.sup_ru = c.sup_ru;

@@ -8,9 +8,10 @@
 //   default: two spill registers and measured slower), with the pulls of
 //   all of them requested before any is collided, and the next round's
 //   records loaded one round ahead.
-// - Addresses: a pull is the cell index plus a per-direction constant
-//   (plane base minus the direction's offset, a kernel parameter); only the
-//   periodic z ends need a correction (rows of the first and last plane).
+// - Addresses: a pull is a per-direction base pointer (plane base minus
+//   the direction's offset, a kernel parameter) plus the cell index; only
+//   the periodic z ends need a correction (rows of the first and last
+//   plane). Stores likewise from per-direction plane pointers.
 // - Wall cells: an item without wall cells loads plain pulls; an item with
 //   some (a warp-uniform branch) takes, at its wall lanes, the bounced
 //   populations of the step from the compact ghost values in place of the
@@ -37,8 +38,13 @@ struct PipeArgs {
     int nx;
     unsigned N;        // cells; 19 N < 2^32
     unsigned rz0, rz1; // rows y + ny z of the first plane: < rz0; of the last: >= rz1
-    unsigned dbase[19];  // i N - (c_x + nx c_y + nx ny c_z), mod 2^32
     PairK k;
+    // per-direction base pointers: the pull of direction i for cell c is
+    // Ap[i][c] (plus the z-end correction), its store Bp[i][c]; one address
+    // operation per access (measured: sweep 0.2273 -> 0.2144 ms against
+    // 32-bit offsets added to one base)
+    const void *Ap[19];  // A + i N - (c_x + nx c_y + nx ny c_z)
+    void *Bp[19];        // B + i N
 };
 
 #ifndef LBM_PIPE_ITEMS
@@ -73,7 +79,6 @@ __global__ void __launch_bounds__(256, pipe_min_blocks(S)) stream_collide_pipe(P
     const long long items = a.nseg;
     const long long gw = (long long)gridDim.x * (blockDim.x / 32);  // warps in the grid
     const T *__restrict__ A = (const T *)a.A;
-    T *__restrict__ B = (T *)a.B;
     const unsigned N = a.N;
     const bool keep_walls = a.bvals != nullptr;
     auto wall_record = [&](uint2 bdv) -> uint2 {
@@ -125,28 +130,30 @@ __global__ void __launch_bounds__(256, pipe_min_blocks(S)) stream_collide_pipe(P
             // periodic z ends: pulls with c_z = +1 from the first plane, c_z = -1 from the last
             const unsigned zp = row[j] < a.rz0 ? N : 0u, zm = row[j] >= a.rz1 ? N : 0u;
             const unsigned cj = c[j];
-            auto src = [&](int i) -> unsigned {
-                return cj + a.dbase[i] + (cz(i) > 0 ? zp : 0u) - (cz(i) < 0 ? zm : 0u);
+            auto pull = [&](int i) -> const T * {
+                const int o = (int)cj + (cz(i) > 0 ? (int)zp : 0) - (cz(i) < 0 ? (int)zm : 0);
+                return (const T *)a.Ap[i] + o;
             };
             if (bd[j].y == 0u) {  // no wall cell in this item (uniform over the warp)
 #pragma unroll
-                for (int i = 0; i < 19; i++) raw[j][i] = __ldg(A + src(i));
+                for (int i = 0; i < 19; i++) raw[j][i] = __ldg(pull(i));
             } else {
                 const T *gv = keep_walls ? (const T *)a.gvals + wr[j].x : A;
                 const unsigned m = wr[j].y;
 #pragma unroll
                 for (int i = 0; i < 19; i++)
-                    raw[j][i] = __ldg(((m >> i) & 1u) ? gv + __popc(m & ((1u << i) - 1u)) : A + src(i));
+                    raw[j][i] = __ldg(((m >> i) & 1u) ? gv + __popc(m & ((1u << i) - 1u)) : pull(i));
             }
         }
 #pragma unroll
         for (int j = 0; j < NI; j++) {
             if (state[j] == 0) continue;
             const unsigned cj = c[j];
+            auto dst = [&](int i) -> T * { return (T *)a.Bp[i] + cj; };
             if (state[j] == 1) {
                 // zero lanes complete the run's end sectors (dead or ghost-overwritten slots)
 #pragma unroll
-                for (int i = 0; i < 19; i++) st(B + (i * N + cj), 0.0f);
+                for (int i = 0; i < 19; i++) st(dst(i), 0.0f);
                 continue;
             }
             float g[19];
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(256, pipe_min_blocks(S)) stream_collide_pipe(P
             collide_pairs<FORCE, SC>(g, a.k, rho, u2);
             if (!(rho > 0.5f && rho < 2.0f && u2 < 0.09f)) atomicOr(a.status, 1u);
 #pragma unroll
-            for (int i = 0; i < 19; i++) st(B + (i * N + cj), g[i]);
+            for (int i = 0; i < 19; i++) st(dst(i), g[i]);
             if (keep_walls && ((bd[j].y >> lane) & 1u)) {
                 T *wv = (T *)a.bvals + (size_t)19 * (bd[j].x + __popc(bd[j].y & ((1u << lane) - 1u)));
 #pragma unroll
@@ -185,7 +192,8 @@ static cudaError_t launch_pipe_t(Ctx &c, bool force) {
     const long long nxy = (long long)c.nx * c.ny;
     for (int i = 0; i < 19; i++) {
         const long long off = cx(i) + (long long)c.nx * cy(i) + nxy * cz(i);
-        a.dbase[i] = (unsigned)((long long)i * c.N - off);
+        a.Ap[i] = (const void *)((const char *)c.fA + storage_bytes(c.storage) * (size_t)((long long)i * c.N - off));
+        a.Bp[i] = (void *)((char *)c.fB + storage_bytes(c.storage) * (size_t)((long long)i * c.N));
     }
     a.k = make_pair_k(c.rt.d_nu, c.F);
     static int resident[4][2];

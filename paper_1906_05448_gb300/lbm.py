@@ -36,8 +36,8 @@ EXPORTS = [
     "lbm_field_energy_noalloc", "lbm_field_energy_noalloc_max_cells", "lbm_last_error",
     "lbm_status_string", "lbm_destroy",
 ]
-NGROUPS = 8
-GROUPS = ["bulk", "ibb_boundary", "ibm_passes", "ibm_collide", "particles", "geometry", "stats", "other"]
+NGROUPS = 9
+GROUPS = ["bulk", "ibb_boundary", "ibm_passes", "ibm_collide", "particles", "geometry", "stats", "other", "closure"]
 
 
 class Grid(ctypes.Structure):

@@ -54,7 +54,10 @@ def test_d3q27_workspace_rules(lib):
     N = n[0] * n[1] * n[2]
     b19 = lbm.workspace_bytes(lbm.make_grid(*n, storage="f32"))
     b27 = lbm.workspace_bytes(lbm.make_grid(*n, storage="f32", lattice=27))
-    assert b27 - b19 == pytest.approx(2 * 8 * 4 * N, abs=4096)  # two buffers of 8 more FP32 planes
+    # two buffers of 8 more FP32 planes, and per (x, y) column the pipe wall's
+    # direction masks (2 x 4 B) and two FP32 weights per direction
+    cols = n[0] * n[1]
+    assert b27 - b19 == pytest.approx(2 * 8 * 4 * N + cols * (8 + 2 * 4 * 27), abs=4096)
     assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f64", lattice=27)) > 0
     # D3Q27 runs BGK on FP64 or FP32 storage only; other velocity sets are refused
     assert lbm.workspace_bytes(lbm.make_grid(*n, storage="f16s", lattice=27)) == 0
