@@ -92,12 +92,14 @@ def forward_tc(w, X, rnd=round_bf16):
 
 
 def loss_and_grad_tc(w, X, T, rnd=round_bf16):
-    """loss_and_grad() in the precision of the training kernel: the forward
-    of forward_tc; each weight gradient is the product of the layer's FP32
-    input (the first layer's input rounded by `rnd`, as the product used it)
-    with the wide output gradient; the gradient passed down a layer is the
-    product of the rounded output gradient with the rounded weights, masked
-    by the ReLU. With rnd = identity this is loss_and_grad()."""
+    """loss_and_grad() in the operand precision of the training kernel
+    (tensor-core products take BF16 operands and add wide): the forward of
+    forward_tc; each weight gradient is the product of the layer's rounded
+    input (the operand the forward used) with the rounded output gradient,
+    and the bias gradient the sum of the rounded output gradient; the
+    gradient passed down a layer is the product of the rounded output
+    gradient with the rounded weights, masked by the ReLU. With rnd =
+    identity this is loss_and_grad()."""
     Y, cache = forward_tc(w, X, rnd)
     T = np.asarray(T, dtype=np.float64)
     n = Y.shape[0]
@@ -106,10 +108,10 @@ def loss_and_grad_tc(w, X, T, rnd=round_bf16):
     layers = unpack(_fp32(w))
     grads = [None] * 4
     for i in range(3, -1, -1):
-        h_in = cache[0][0] if i == 0 else cache[i - 1][1]
-        grads[i] = (h_in.T @ d, d.sum(axis=0))
+        dr = rnd(d)
+        grads[i] = (cache[i][0].T @ dr, dr.sum(axis=0))
         if i > 0:
-            d = (rnd(d) @ rnd(layers[i][0]).T) * (cache[i - 1][1] > 0)
+            d = (dr @ rnd(layers[i][0]).T) * (cache[i - 1][1] > 0)
     flat = np.concatenate([np.concatenate([g[0].ravel(), g[1]]) for g in grads])
     return L, flat
 

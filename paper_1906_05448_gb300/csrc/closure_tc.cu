@@ -455,6 +455,332 @@ static cudaError_t tc_launch(const TcArgs &a, bool field, long long max_tiles, c
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ training --
+// Loss and gradient of a batch on tcgen05. One CTA (128 threads, a sample
+// row each; one CTA per SM: 185 KB of shared memory, all 512 tensor-memory
+// columns) runs tiles of 128 samples:
+// - forward as in inference, keeping the three hidden activations (BF16);
+// - the output gradient dZ4 = 2 (Y - T) / (9 n), then per layer k = 4..1
+//   the weight gradient  dW_k += [H_{k-1}; 1]^T dZ_k  (M = 128 input rows
+//   with a row of ones whose product is the bias gradient, N = units,
+//   K = the 128 samples) accumulated in tensor memory over the CTA's tiles,
+//   and the data gradient dH_{k-1} = dZ_k W_k^T masked by the ReLU;
+// - both products take BF16 operands (the activations, dZ_k and the
+//   weights, as the tensor cores require) and add in FP32.
+// The transposed operands are written by the epilogues (each thread holds
+// one sample, so it writes one column of [H_{k-1}; 1]^T and of dZ_k^T).
+// At the end every thread reads its row of the four accumulators and
+// writes this CTA's gradient slot; the Adam kernel sums the slots in a
+// fixed order.
+// Tensor-memory columns: 0-63 the layer product, 64-127 dW1, 128-191 dW2,
+// 192-255 dW3, 256-271 dW4.
+namespace {
+constexpr int PB2 = PW4 + TN4 * TKH, PB3 = PB2 + TC_H * TC_H, PB4 = PB3 + TC_H * TC_H;  // backward operand blocks
+constexpr int TK_T = 128;  // K of the weight-gradient products (samples of a tile)
+
+struct __align__(128) TrainTcSmem {
+    unsigned short w1[TC_H * TK1], w2[TC_H * TKH], w3[TC_H * TKH], w4[TN4 * TKH];  // forward B: [out][in]
+    unsigned short v2[TC_H * TC_H], v3[TC_H * TC_H], v4[TC_H * TN4];              // backward B: [in][out]
+    unsigned short x0[TM * TK1];      // layer-1 operand
+    unsigned short h[3][TM * TKH];    // hidden activations
+    unsigned short at[TM * TK_T];     // [H_{k-1}; 1]^T, rows padded to 128 with zeros
+    unsigned short dz[TM * TKH];      // dZ_k (A of the data gradient), K = units
+    unsigned short dzt[TC_H * TK_T];  // dZ_k^T (B of the weight gradient), K = samples
+    float b[208];
+    unsigned long long mbar;
+    unsigned taddr;
+    float loss[4];
+};
+
+__device__ __forceinline__ unsigned short bf16_bits(float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const unsigned short *>(&b);
+}
+}  // namespace
+
+struct TrainTcArgs {
+    const float *X, *T;
+    long long s0, s1;
+    float inv;  // 2 / (9 n) of the batch
+    const float *w;
+    const unsigned short *pk;
+    float *gpart, *lpart;
+    int *err;
+};
+
+__global__ void __launch_bounds__(TM, 1) mlp_train_tc_kernel(TrainTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char tt_smem_raw[];
+    TrainTcSmem &S = *reinterpret_cast<TrainTcSmem *>(tt_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long n = a.s1 - a.s0;
+    const long long tiles = (n + TM - 1) / TM;
+    for (int e = tid; e < TC_H * TK1; e += TM) S.w1[cm(e / TK1, e % TK1, TK1)] = a.pk[PW1 + e];
+    for (int e = tid; e < TC_H * TKH; e += TM) {
+        S.w2[cm(e / TKH, e % TKH, TKH)] = a.pk[PW2 + e];
+        S.w3[cm(e / TKH, e % TKH, TKH)] = a.pk[PW3 + e];
+        S.v2[cm(e / TC_H, e % TC_H, TC_H)] = a.pk[PB2 + e];
+        S.v3[cm(e / TC_H, e % TC_H, TC_H)] = a.pk[PB3 + e];
+    }
+    for (int e = tid; e < TN4 * TKH; e += TM) {
+        S.w4[cm(e / TKH, e % TKH, TKH)] = a.pk[PW4 + e];
+        S.v4[cm(e / TN4, e % TN4, TN4)] = a.pk[PB4 + e];
+    }
+    for (int i = tid; i < 208; i += TM) {
+        float v = 0.f;
+        if (i < 64) v = a.w[OB1 + i];
+        else if (i < 128) v = a.w[OB2 + i - 64];
+        else if (i < 192) v = a.w[OB3 + i - 128];
+        else if (i - 192 < TC_OUT) v = a.w[OB4 + i - 192];
+        S.b[i] = v;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&S.taddr))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t T0 = S.taddr;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int row = tid;  // this thread's sample in the tile, and its row of the weight-gradient accumulators
+    uint32_t parity = 0;
+    bool ok = true;
+    float lsum = 0.f;
+    bool first = true;  // the CTA's first weight-gradient product overwrites the accumulators
+    auto sync_operands = [&]() {  // generic shared-memory writes -> the tensor cores
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+    };
+    auto wait_mma = [&]() {
+        if (!mbar_wait(&S.mbar, parity)) ok = false;
+        parity ^= 1u;
+        fence_after();
+    };
+    // D (TMEM column tc) = A (K-major, K columns) x B^T (N rows, K-major)
+    auto mma = [&](uint32_t tc, const unsigned short *A, const unsigned short *B, int K, int N, bool acc) {
+        const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+        for (int s = 0; s < K / 16; s++)
+            tc_mma(T0 + tc, sdesc(A + 128 * s, 128u, sbo), sdesc(B + 128 * s, 128u, sbo), idesc_bf16(TM, N),
+                   (acc || s > 0) ? 1u : 0u);
+    };
+    auto issue = [&](auto &&body) {  // one thread issues, commits; all wait
+        if (tid == 0) {
+            fence_after();
+            body();
+            tc_commit(&S.mbar);
+        }
+        wait_mma();
+    };
+    // hidden epilogue: relu(D + b) -> h[k] (this thread's row)
+    auto hidden = [&](unsigned short *H, int boff) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            float v[32];
+            tmem_ld32(T0 + lane_base + 32 * ch, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + S.b[boff + 32 * ch + j], 0.f);
+#pragma unroll
+            for (int g = 0; g < 4; g++) put8(H, cm(row, 32 * ch + 8 * g, TKH), v + 8 * g);
+        }
+        sync_operands();
+    };
+    // column `row` of [src; 1]^T (src: this thread's row of a K-major operand with `cols` columns)
+    auto transpose_in = [&](const unsigned short *src, int cols, int ones_row) {
+        for (int j0 = 0; j0 < cols; j0 += 8) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(src + cm(row, j0, cols));
+            const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int t = 0; t < 8; t++) S.at[cm(j0 + t, row, TK_T)] = (unsigned short)(w4[t >> 1] >> (16 * (t & 1)));
+        }
+        S.at[cm(ones_row, row, TK_T)] = bf16_bits(1.f);
+        for (int j = ones_row + 1; j < TM; j++) S.at[cm(j, row, TK_T)] = 0;
+    };
+    // data-gradient epilogue: dZ = D masked by relu'(h) -> dz (unless last) and dz^T
+    auto backward = [&](const unsigned short *H, bool keep_dz) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            float v[32];
+            tmem_ld32(T0 + lane_base + 32 * ch, v);
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                const int j0 = 32 * ch + 8 * g;
+                const uint4 q = *reinterpret_cast<const uint4 *>(H + cm(row, j0, TKH));
+                const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const unsigned short hb = (unsigned short)(w4[t >> 1] >> (16 * (t & 1)));
+                    if (hb == 0 || (hb & 0x8000u)) v[8 * g + t] = 0.f;  // relu'(h) = 0 where h <= 0
+                    S.dzt[cm(j0 + t, row, TK_T)] = bf16_bits(v[8 * g + t]);
+                }
+                if (keep_dz) put8(S.dz, cm(row, j0, TKH), v + 8 * g);
+            }
+        }
+    };
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long r0 = tile * TM;
+        const int rows = (int)(n - r0 < TM ? n - r0 : TM);
+        const long long srow = a.s0 + r0 + row;
+        // layer-1 operand: coalesced 16-byte words when the rows start aligned
+        {
+            const float *base = a.X + (a.s0 + r0) * TC_IN;
+            const int nv = rows * TC_IN;
+            auto put1 = [&](int e, float v) {
+                const int r = e / TC_IN, k = e - r * TC_IN;
+                S.x0[cm(r, k, TK1)] = bf16_bits(v);
+            };
+            if ((reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+                const float4 *b4 = reinterpret_cast<const float4 *>(base);
+                for (int f = tid; 4 * f + 3 < nv; f += TM) {
+                    const float4 v = __ldg(b4 + f);
+                    put1(4 * f, v.x);
+                    put1(4 * f + 1, v.y);
+                    put1(4 * f + 2, v.z);
+                    put1(4 * f + 3, v.w);
+                }
+                for (int e = (nv & ~3) + tid; e < nv; e += TM) put1(e, __ldg(base + e));
+            } else {
+                for (int e = tid; e < nv; e += TM) put1(e, __ldg(base + e));
+            }
+            for (int k = TC_IN; k < TK1; k++) S.x0[cm(row, k, TK1)] = 0;
+            if (row >= rows)
+                for (int k = 0; k < TC_IN; k++) S.x0[cm(row, k, TK1)] = 0;
+        }
+        sync_operands();
+        // forward
+        issue([&] { mma(0, S.x0, S.w1, TK1, TC_H, false); });
+        if (!ok) break;
+        hidden(S.h[0], 0);
+        issue([&] { mma(0, S.h[0], S.w2, TKH, TC_H, false); });
+        if (!ok) break;
+        hidden(S.h[1], 64);
+        issue([&] { mma(0, S.h[1], S.w3, TKH, TC_H, false); });
+        if (!ok) break;
+        hidden(S.h[2], 128);
+        issue([&] { mma(0, S.h[2], S.w4, TKH, TN4, false); });
+        if (!ok) break;
+        // output gradient of the tile (zero for rows past the batch)
+        {
+            float y[16], d[16];
+            tmem_ld16(T0 + lane_base, y);
+#pragma unroll
+            for (int o = 0; o < 16; o++) {
+                d[o] = 0.f;
+                if (o < TC_OUT && row < rows) {
+                    const float r = y[o] + S.b[192 + o] - __ldg(a.T + srow * TC_OUT + o);
+                    lsum = fmaf(r, r, lsum);
+                    d[o] = a.inv * r;
+                }
+            }
+            put8(S.dz, cm(row, 0, TN4), d);
+            put8(S.dz, cm(row, 8, TN4), d + 8);
+#pragma unroll
+            for (int o = 0; o < 16; o++) S.dzt[cm(o, row, TK_T)] = bf16_bits(d[o]);
+            transpose_in(S.h[2], TKH, TC_H);
+        }
+        sync_operands();
+        // layer 4: dW4 += [H3; 1]^T dZ4, dH3 = dZ4 W4^T
+        issue([&] {
+            mma(256, S.at, S.dzt, TK_T, TN4, !first);
+            mma(0, S.dz, S.v4, TN4, TC_H, false);
+        });
+        if (!ok) break;
+        backward(S.h[2], true);
+        transpose_in(S.h[1], TKH, TC_H);
+        sync_operands();
+        // layer 3
+        issue([&] {
+            mma(192, S.at, S.dzt, TK_T, TC_H, !first);
+            mma(0, S.dz, S.v3, TKH, TC_H, false);
+        });
+        if (!ok) break;
+        backward(S.h[1], true);
+        transpose_in(S.h[0], TKH, TC_H);
+        sync_operands();
+        // layer 2
+        issue([&] {
+            mma(128, S.at, S.dzt, TK_T, TC_H, !first);
+            mma(0, S.dz, S.v2, TKH, TC_H, false);
+        });
+        if (!ok) break;
+        backward(S.h[0], false);
+        transpose_in(S.x0, TK1, TK1);  // the 85 inputs (zero-padded to 96), ones at row 96
+        sync_operands();
+        // layer 1
+        issue([&] { mma(64, S.at, S.dzt, TK_T, TC_H, !first); });
+        if (!ok) break;
+        first = false;
+    }
+    // this CTA's gradient slot: thread `row` holds row `row` of each accumulator
+    if (ok) {
+        float *g = a.gpart + (size_t)blockIdx.x * (size_t)(OB4 + TC_OUT);
+#pragma unroll 1
+        for (int L = 0; L < 3; L++) {
+            const int nin = L == 0 ? TC_IN : TC_H, ones = L == 0 ? TK1 : TC_H;
+            const int offw = L == 0 ? 0 : (L == 1 ? OB1 + TC_H : OB2 + TC_H), offb = L == 0 ? OB1 : (L == 1 ? OB2 : OB3);
+            for (int ch = 0; ch < 2; ch++) {
+                float v[32];
+                tmem_ld32(T0 + lane_base + 64 * (L + 1) + 32 * ch, v);
+                if (row < nin)
+                    for (int o = 0; o < 32; o++) g[offw + row * TC_H + 32 * ch + o] = first ? 0.f : v[o];
+                else if (row == ones)
+                    for (int o = 0; o < 32; o++) g[offb + 32 * ch + o] = first ? 0.f : v[o];
+            }
+        }
+        {
+            float v[16];
+            tmem_ld16(T0 + lane_base + 256, v);
+            if (row < TC_H)
+                for (int o = 0; o < TC_OUT; o++) g[OB3 + TC_H + row * TC_OUT + o] = first ? 0.f : v[o];
+            else if (row == TC_H)
+                for (int o = 0; o < TC_OUT; o++) g[OB4 + o] = first ? 0.f : v[o];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) S.loss[warp] = lsum;
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    fence_before();
+    __syncthreads();
+    if (tid == 0) a.lpart[blockIdx.x] = S.loss[0] + S.loss[1] + S.loss[2] + S.loss[3];
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(T0) : "memory");
+}
+
+// Gradient slots (one per CTA) and loss partials of the batch [s0, s1).
+cudaError_t mlp_train_tc(const float *X, const float *T, long long s0, long long s1, const float *w, const void *pk,
+                         float *gpart, float *lpart, int max_blocks, int *err, cudaStream_t s, int *nblk_out) {
+    static bool attr = false;
+    const int smem = (int)sizeof(TrainTcSmem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = (s1 - s0 + TM - 1) / TM;
+    int nb = (int)(tiles < max_blocks ? tiles : max_blocks);
+    if (nb < 1) nb = 1;
+    TrainTcArgs a;
+    a.X = X;
+    a.T = T;
+    a.s0 = s0;
+    a.s1 = s1;
+    a.inv = 2.0f / (float)((double)(s1 - s0) * TC_OUT);
+    a.w = w;
+    a.pk = (const unsigned short *)pk;
+    a.gpart = gpart;
+    a.lpart = lpart;
+    a.err = err;
+    mlp_train_tc_kernel<<<nb, TM, smem, s>>>(a);
+    *nblk_out = nb;
+    return cudaGetLastError();
+}
+
 // Y (n x 9) = network(X (n x 85)); pk: the packed BF16 operand block of w.
 cudaError_t mlp_forward_tc(const float *X, long long n, const float *w, const void *pk, float *Y, int *err,
                            cudaStream_t s) {

@@ -44,7 +44,7 @@ struct Plan {
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, seg_bnd, bvals, wrec, gidx, gvals, refill;
+    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, slink4, seg_bnd, bvals, wrec, gidx, gvals, refill;
     long long max_refill;
     long long max_seg;
     size_t xy_start, xy_j, xy_w, it_k, it_w;
@@ -112,6 +112,7 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.seg = L.take(16 * (size_t)P.max_seg);
     P.slink = L.take(8 * ml);
     P.slink_rank = L.take(4 * ml);
+    P.slink4 = L.take(16 * ml);
     P.seg_bnd = L.take(8 * (size_t)P.max_seg);
     P.bvals = L.take(19 * sb * ms);
     P.wrec = L.take(8 * ms);
@@ -602,6 +603,7 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.slink = (uint2 *)(b + P.slink);
     c.static_links = 0;
     c.slink_rank = (int *)(b + P.slink_rank);
+    c.slink4 = (uint4 *)(b + P.slink4);
     c.seg_bnd = (uint2 *)(b + P.seg_bnd);
     c.bvals = b + P.bvals;
     c.wrec = (uint2 *)(b + P.wrec);
@@ -875,6 +877,49 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
                 CK(cudaMemcpy(c.seg_bnd, sb.data(), 8 * sb.size(), cudaMemcpyHostToDevice));
                 c.bvals_ready = 1;
                 c.bvals_valid = 0;
+                // ghost-pass records once the wall cells' values are kept:
+                // upstream cell, the two interpolation weights, wall-cell rank
+                // (the linear scheme: 2q, 1 - 2q on f_l(x_f), f_l(x_f - c_l)
+                // for q < 1/2; 1/(2q), (2q - 1)/(2q) on f_l(x_f), f_ibar(x_f)
+                // for q >= 1/2; the single-node scheme keeps 0.5 (1 - 2q))
+                std::vector<uint4> r4(nl);
+                bool rok = true;
+                for (size_t at = 0; at < nl && rok; at++) {
+                    const unsigned cell = pk[at].x & 0x3fffffffu, sch = pk[at].x >> 30;
+                    float qf;
+                    std::memcpy(&qf, &pk[at].y, 4);
+                    int l = 0;
+                    while (l < 19 && (long long)at >= c.slink_off[l + 1]) l++;
+                    const long long x = cell % c.nx, y = (cell / c.nx) % c.ny, z = cell / ((long long)c.nx * c.ny);
+                    const long long x1 = (x - cx(l) + c.nx) % c.nx, y1 = (y - cy(l) + c.ny) % c.ny,
+                                    z1 = (z - cz(l) + c.nz) % c.nz;
+                    const unsigned c1 = (unsigned)(x1 + c.nx * (y1 + (long long)c.ny * z1));
+                    const double q = (double)qf;
+                    float k1, k2;
+                    unsigned own = 0, single = 0;
+                    if (sch == 1 && q < 0.5) {
+                        k1 = (float)(2.0 * q);
+                        k2 = (float)(1.0 - 2.0 * q);
+                    } else if (sch == 1) {
+                        k1 = (float)(1.0 / (2.0 * q));
+                        k2 = (float)((2.0 * q - 1.0) / (2.0 * q));
+                        own = 1;
+                    } else if (sch == 2) {
+                        k1 = 1.0f;
+                        k2 = (float)(0.5 * (1.0 - 2.0 * q));
+                        single = 1;
+                    } else {
+                        rok = false;  // the quadratic scheme keeps the general pass
+                        break;
+                    }
+                    unsigned b1, b2;
+                    std::memcpy(&b1, &k1, 4);
+                    std::memcpy(&b2, &k2, 4);
+                    r4[at] = make_uint4(c1 | (own << 30) | (single << 31), b1, b2, (unsigned)rk[at]);
+                }
+                rok = rok && c.pipe_nowrap;  // the pass recovers x_f from x_f - c_l across z ends only
+                if (rok) CK(cudaMemcpy(c.slink4, r4.data(), 16 * nl, cudaMemcpyHostToDevice));
+                c.slink4_ready = rok ? 1 : 0;
             }
         }
     }

@@ -59,6 +59,8 @@ struct Ctx {
     // wall cells' post-collision populations, written by the sweep for the
     // next ghost pass: 19 values (storage type) per wall cell in cell order
     int *slink_rank;    // per static link: rank of its wall cell
+    uint4 *slink4;      // per static link: upstream cell | flags, two weights, wall-cell rank
+    int slink4_ready;   // 1: the records hold every static link
     uint2 *seg_bnd;     // per sweep item: rank of its first wall cell, lane mask of wall cells
     void *bvals;
     long long max_bvals;
@@ -201,6 +203,8 @@ cudaError_t mlp_pack_device(const float *w, void *pk, cudaStream_t s);
 // tensor-core (tcgen05) closure inference, closure_tc.cu
 cudaError_t mlp_forward_tc(const float *X, long long n, const float *w, const void *pk, float *Y, int *err,
                            cudaStream_t s);
+cudaError_t mlp_train_tc(const float *X, const float *T, long long s0, long long s1, const float *w, const void *pk,
+                         float *gpart, float *lpart, int max_blocks, int *err, cudaStream_t s, int *nblk_out);
 cudaError_t closure_eps_tc(const Ctx &c, const float *u32, const int *cells, const int *pid, const long long *count,
                            long long cap, const void *pk, float *eps_o, int *err);
 }  // namespace lbmgb

@@ -322,6 +322,7 @@ static unsigned site_grid(const Ctx &c, int tb) {
 // uniform over the block and neighbouring threads touch neighbouring cells.
 struct StaticLinkArgs {
     void *A;
+    const uint4 *slink4;  // link records of the kept-values pass (see ibb_links_kept)
     const uint2 *slink;  // x = cell | scheme << 30, y = FP32 bits of q
     const int *rank;     // wall-cell rank of each link
     const void *bvals;   // wall cells' values (19 per cell), or null: read A
@@ -335,6 +336,56 @@ struct StaticLinkArgs {
     float Fs[3];
     Rates rt;
 };
+
+// The ghost pass of the static wall from per-link records (16 bytes: the
+// upstream cell x_f - c_l with the flags "second value is f_ibar(x_f)" and
+// "single-node", the two FP32 weights, the wall cell's rank), grouped by
+// direction as the links are:
+//   v = k1 f*_l(x_f) + k2 f*_l(x_f - c_l)   (linear, q < 1/2)
+//   v = k1 f*_l(x_f) + k2 f*_ibar(x_f)      (linear, q >= 1/2)
+//   v = f*_l(x_f) + k2 (d_l + d_ibar)       (single-node, Sec. 3.1)
+// The wall cell's own populations come from the values the last sweep kept
+// (19 per wall cell), or, before the first sweep, from A at x_f (only z
+// wraps between x_f - c_l and x_f: the walls of this pass touch no x or y
+// face). No division or index decoding per link.
+template <int S, bool SN>
+__global__ void __launch_bounds__(256) ibb_links_kept(StaticLinkArgs a) {
+    typedef typename Store<S>::T T;
+    typedef typename Store<S>::R R;
+    const int l = blockIdx.y;
+    const int k0 = a.off[l], k1 = a.off[l + 1];
+    const size_t N = (size_t)a.N;
+    const T *A = (const T *)a.A + (size_t)l * N;  // plane l
+    const int i = opp(l);
+    const bool kept = a.bvals != nullptr;
+    const long long offl = (long long)cx(l) + (long long)a.nx * (cy(l) + (long long)a.ny * cz(l));
+    for (int k = k0 + blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += gridDim.x * blockDim.x) {
+        const uint4 m = __ldg(a.slink4 + k);
+        const int gi = __ldg(a.gidx + k);
+        const unsigned c1 = m.x & 0x3fffffffu;
+        const bool own = (m.x >> 30) & 1u, single = m.x >> 31;
+        const T *wv;
+        size_t stride;
+        if (kept) {
+            wv = (const T *)a.bvals + (size_t)19 * m.w;
+            stride = 1;
+        } else {
+            long long c = (long long)c1 + offl;
+            c = c < 0 ? c + (long long)N : (c >= (long long)N ? c - (long long)N : c);
+            wv = (const T *)a.A + c;
+            stride = N;
+        }
+        const R fl0 = Store<S>::ld(wv + (size_t)l * stride);
+        const R second = own ? Store<S>::ld(wv + (size_t)i * stride) : (single ? R(0) : Store<S>::ld(A + c1));
+        R v = fmaf(R(__uint_as_float(m.y)), fl0, R(__uint_as_float(m.z)) * second);
+        if (SN && single)
+            v = fmaf(R(__uint_as_float(m.z)),
+                     single_node_pair<S>(wv, stride, l, body_force<R>(a, 0), body_force<R>(a, 1), body_force<R>(a, 2),
+                                         a.rt),
+                     fl0);
+        Store<S>::st((T *)a.gvals + gi, v);
+    }
+}
 
 template <int S, bool SN>
 __global__ void __launch_bounds__(256) ibb_links_static(StaticLinkArgs a) {
@@ -386,6 +437,7 @@ static cudaError_t launch_links_s(Ctx &c) {
     if (c.static_links && c.np == 0 && S != LBM_F64) {
         StaticLinkArgs a;
         a.A = c.fA;
+        a.slink4 = c.slink4;
         a.slink = c.slink;
         a.rank = c.slink_rank;
         a.bvals = c.bvals_valid ? c.bvals : nullptr;
@@ -407,10 +459,17 @@ static cudaError_t launch_links_s(Ctx &c) {
         for (int l = 0; l < 19; l++) most = std::max(most, c.slink_off[l + 1] - c.slink_off[l]);
         unsigned nbx = (unsigned)((most + 255) / 256);
         if (nbx < 1) nbx = 1;
+
         count_launch(c, G_BND);
         // the variant with the single-node scheme only for walls that have such links
-        if (c.static_single > 0) ibb_links_static<S, true><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
-        else ibb_links_static<S, false><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        if (c.slink4_ready && a.gvals) {  // every step, so a restart repeats the same arithmetic
+            if (c.static_single > 0) ibb_links_kept<S, true><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+            else ibb_links_kept<S, false><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        } else if (c.static_single > 0) {
+            ibb_links_static<S, true><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        } else {
+            ibb_links_static<S, false><<<dim3(nbx, 19), 256, 0, c.stream>>>(a);
+        }
         return cudaGetLastError();
     }
     LinkArgs a{c.fA, c.link_cell, c.link_pid, c.link_dir, c.link_scheme, c.link_q, c.link_dP, c.link_dT,
