@@ -1,12 +1,15 @@
-// Learned closure inference on the fifth-generation tensor cores (tcgen05),
-// fused with the near-surface dissipation diagnostic.
+// Learned closure on the fifth-generation tensor cores (tcgen05): inference
+// fused with the near-surface dissipation diagnostic, inference over a
+// feature array, and training (loss, data and weight gradients; below).
 //
 // The closure (an 85-64-64-64-9 ReLU perceptron, see closure.cu) maps the
 // IBM velocity stencil around a near-surface node to its 9 velocity
 // gradients; the paper motivates it by IBM's underestimated dissipation
 // inside the diffused interface (Sec. 3.2, Sec. 4).
 //
-// One CTA of 256 threads works on tiles of 128 samples (the MMA's M):
+// A CTA works on tiles of 128 samples (the MMA's M) with 256 threads (two
+// per sample, two CTAs per SM) when it gathers from the field, 128 (one per
+// sample, four CTAs per SM) over a feature array:
 // - inputs: either 85 FP32 features per sample read from memory
 //   (lbm_mlp_forward), or, fused, gathered from an FP32 copy of the
 //   velocity field at the listed near-surface cells (the 27-point stencil
@@ -14,10 +17,10 @@
 //   feature array in HBM; rounded to BF16 into shared memory;
 // - four layers, each: one elected thread issues tcgen05.mma (kind::f16,
 //   BF16 operands from shared memory, FP32 accumulators in tensor memory)
-//   over K in steps of 16 and commits to an mbarrier; the 8 warps read the
-//   accumulators back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4)..,
-//   columns 32 (w / 4)..), add the FP32 bias, apply ReLU and write the next
-//   layer's BF16 operand;
+//   over K in steps of 16 and commits to an mbarrier; the warps read the
+//   accumulators back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4)..;
+//   with two threads per sample, columns 32 (w / 4)..), add the FP32 bias,
+//   apply ReLU and write the next layer's BF16 operand;
 // - output: the 9 gradients (FP32), or, fused, the dissipation
 //   2 nu s_ij s_ij of the predicted gradients at the cell.
 // Operands use the no-swizzle K-major layout of 8 x 8 BF16 core matrices
@@ -34,12 +37,11 @@ size_t mlp_pack_bytes();
 
 namespace {
 
-#ifndef LBM_TC_THREADS
-#define LBM_TC_THREADS 128  // threads per CTA: 128 (a sample row each) or 256 (two per row)
-#endif
-constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16, TC_THREADS = LBM_TC_THREADS;
-constexpr int TPR = TC_THREADS / TM;  // threads per sample row
-static_assert(TPR == 1 || TPR == 2, "128 or 256 threads");
+constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16;
+// threads per sample row: the fused gather runs two (each issues the loads
+// of one half of the stencil at once: 0.177 ms per diagnostic against 0.194
+// with one thread per row), the feature array one (0.319 against 0.349 ms)
+template <bool FIELD> __host__ __device__ constexpr int tc_tpr() { return FIELD ? 2 : 1; }
 constexpr int TC_IN = 85, TC_H = 64, TC_OUT = 9;
 // packed operand block of closure.cu: WT_l [out_pad][in_pad] (BF16)
 constexpr int PW1 = 0, PW2 = PW1 + TC_H * TK1, PW3 = PW2 + TC_H * TC_H, PW4 = PW3 + TC_H * TC_H;
@@ -180,8 +182,7 @@ __device__ __forceinline__ float fmimg(float d, int n) {
 // 96), BF16 into row `row` of the layer-1 operand, in two halves of 48
 // columns: stencil points 0-15, then points 16-26, the distance to the
 // surface, the node again and 11 zeros. Each half's 16-byte velocity loads
-// are issued together; the second half's lines are first requested into L2
-// (no registers held), so its loads find them there.
+// are issued together (the fused kernel gives each half its own thread).
 template <int H0, int H1>
 __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigned short *A, int row) {
     const unsigned c = (unsigned)a.cells[s];
@@ -209,11 +210,6 @@ __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigne
         o[1] = (u.y - (Uv.y + (Wv.z * sx - Wv.x * sz))) * ius;
         o[2] = (u.z - (Uv.z + (Wv.x * sy - Wv.y * sx))) * ius;
     };
-    if constexpr (H0 == 0 && H1 == 2) {
-#pragma unroll
-        for (int j = 16; j < 27; j += 3)  // rows of the second half (x - 1 .. x + 1 share a line or two)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(addr(j)));
-    }
     // values go out 8 columns at a time (compile-time positions after unrolling)
     float buf[8];
     int fill = 0, col = 0;
@@ -254,12 +250,11 @@ __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigne
     }
 }
 
-#ifndef LBM_TC_CTAS
-#define LBM_TC_CTAS (512 / TC_THREADS)  // CTAs per SM (each takes 128 of the 512 tensor-memory columns)
-#endif
-
+// CTAs per SM: 512 tensor-memory columns / 128 per CTA, and the registers
+// of 128 x TPR threads
 template <bool FIELD>
-__global__ void __launch_bounds__(TC_THREADS, LBM_TC_CTAS) mlp_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) mlp_tc_kernel(TcArgs a) {
+    constexpr int TPR = tc_tpr<FIELD>(), TC_THREADS = 128 * TPR;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -447,11 +442,11 @@ static cudaError_t tc_launch(const TcArgs &a, bool field, long long max_tiles, c
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long nb = (long long)LBM_TC_CTAS * (sms > 0 ? sms : 1);
+    long long nb = (long long)(field ? 2 : 4) * (sms > 0 ? sms : 1);
     if (nb > max_tiles) nb = max_tiles;
     if (nb < 1) nb = 1;
-    if (field) mlp_tc_kernel<true><<<(unsigned)nb, TC_THREADS, smem, s>>>(a);
-    else mlp_tc_kernel<false><<<(unsigned)nb, TC_THREADS, smem, s>>>(a);
+    if (field) mlp_tc_kernel<true><<<(unsigned)nb, 128 * tc_tpr<true>(), smem, s>>>(a);
+    else mlp_tc_kernel<false><<<(unsigned)nb, 128 * tc_tpr<false>(), smem, s>>>(a);
     return cudaGetLastError();
 }
 
