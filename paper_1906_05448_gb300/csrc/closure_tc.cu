@@ -7,9 +7,9 @@
 // gradients; the paper motivates it by IBM's underestimated dissipation
 // inside the diffused interface (Sec. 3.2, Sec. 4).
 //
-// A CTA works on tiles of 128 samples (the MMA's M) with 256 threads (two
-// per sample, two CTAs per SM) when it gathers from the field, 128 (one per
-// sample, four CTAs per SM) over a feature array:
+// A CTA works on tiles of 128 samples (the MMA's M); over a feature array
+// with 128 threads (a sample each, four CTAs per SM), fused with 256 in two
+// roles (gather and layers, two CTAs per SM; see mlp_tc_field_ws_kernel):
 // - inputs: either 85 FP32 features per sample read from memory
 //   (lbm_mlp_forward), or, fused, gathered from an FP32 copy of the
 //   velocity field at the listed near-surface cells (the 27-point stencil
@@ -18,9 +18,8 @@
 // - four layers, each: one elected thread issues tcgen05.mma (kind::f16,
 //   BF16 operands from shared memory, FP32 accumulators in tensor memory)
 //   over K in steps of 16 and commits to an mbarrier; the warps read the
-//   accumulators back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4)..;
-//   with two threads per sample, columns 32 (w / 4)..), add the FP32 bias,
-//   apply ReLU and write the next layer's BF16 operand;
+//   accumulators back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4)..),
+//   add the FP32 bias, apply ReLU and write the next layer's BF16 operand;
 // - output: the 9 gradients (FP32), or, fused, the dissipation
 //   2 nu s_ij s_ij of the predicted gradients at the cell.
 // Operands use the no-swizzle K-major layout of 8 x 8 BF16 core matrices
@@ -38,10 +37,6 @@ size_t mlp_pack_bytes();
 namespace {
 
 constexpr int TM = 128, TK1 = 96, TKH = 64, TN4 = 16;
-// threads per sample row: the fused gather runs two (each issues the loads
-// of one half of the stencil at once: 0.177 ms per diagnostic against 0.194
-// with one thread per row), the feature array one (0.319 against 0.349 ms)
-template <bool FIELD> __host__ __device__ constexpr int tc_tpr() { return FIELD ? 2 : 1; }
 constexpr int TC_IN = 85, TC_H = 64, TC_OUT = 9;
 // packed operand block of closure.cu: WT_l [out_pad][in_pad] (BF16)
 constexpr int PW1 = 0, PW2 = PW1 + TC_H * TK1, PW3 = PW2 + TC_H * TC_H, PW4 = PW3 + TC_H * TC_H;
@@ -182,7 +177,7 @@ __device__ __forceinline__ float fmimg(float d, int n) {
 // 96), BF16 into row `row` of the layer-1 operand, in two halves of 48
 // columns: stencil points 0-15, then points 16-26, the distance to the
 // surface, the node again and 11 zeros. Each half's 16-byte velocity loads
-// are issued together (the fused kernel gives each half its own thread).
+// are issued together.
 template <int H0, int H1>
 __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigned short *A, int row) {
     const unsigned c = (unsigned)a.cells[s];
@@ -250,15 +245,14 @@ __device__ __forceinline__ void gather_put(const TcArgs &a, long long s, unsigne
     }
 }
 
-// CTAs per SM: 512 tensor-memory columns / 128 per CTA, and the registers
-// of 128 x TPR threads
-template <bool FIELD>
-__global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) mlp_tc_kernel(TcArgs a) {
-    constexpr int TPR = tc_tpr<FIELD>(), TC_THREADS = 128 * TPR;
+// Inference over a feature array (lbm_mlp_forward): 128 threads, a sample
+// row each, four CTAs per SM (512 tensor-memory columns / 128 per CTA).
+__global__ void __launch_bounds__(128, 4) mlp_tc_kernel(TcArgs a) {
+    constexpr int TC_THREADS = 128;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long n = FIELD ? (*a.count < a.cap ? *a.count : a.cap) : a.n;
+    const long long n = a.n;
     const long long tiles = (n + TM - 1) / TM;
     if ((long long)blockIdx.x >= tiles) return;  // the whole block leaves before any tensor memory is taken
     // weights into the core-matrix layout, biases
@@ -293,7 +287,6 @@ __global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) ml
     const uint32_t T0 = S.taddr;                               // columns 0..63 and 64..127 of this CTA
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const int row = 32 * (warp & 3) + lane;                    // this thread's sample row in the tile
-    const int half = TPR == 2 ? warp >> 2 : 0;                 // its column half in the epilogues (two per row)
     uint32_t parity = 0;
     bool ok = true;
     // one layer: MMA over K into TMEM column base tc, then the epilogue of
@@ -315,8 +308,8 @@ __global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) ml
     // epilogue overwrites the operand in place; 32 columns at a time
     auto hidden_out = [&](uint32_t tc, int boff) {
 #pragma unroll
-        for (int ch = 0; ch < 2 / TPR; ch++) {
-            const int c0 = 32 * (TPR == 2 ? half : ch);
+        for (int ch = 0; ch < 2; ch++) {
+            const int c0 = 32 * ch;
             float v[32];
             tmem_ld32(T0 + lane_base + tc + c0, v);
 #pragma unroll
@@ -332,19 +325,7 @@ __global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) ml
         const long long s = tile * TM + row;
         // layer-1 operand: 85 features (BF16), zero padding to 96, zero rows past n
         {
-            if (FIELD && s < n) {
-                if (TPR == 1) gather_put<0, 2>(a, s, S.a, row);
-                else if (half == 0) gather_put<0, 1>(a, s, S.a, row);
-                else gather_put<1, 2>(a, s, S.a, row);
-            } else if (FIELD) {  // rows past n: zeros
-#pragma unroll
-                for (int h = 0; h < 2 / TPR; h++) {
-                    const int k0 = 48 * (TPR == 2 ? half : h);
-                    const float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int g = 0; g < 6; g++) put8(S.a, cm(row, k0 + 8 * g, TK1), f);
-                }
-            } else {
+            {
                 // the tile's rows are one contiguous run of 85 x rows floats:
                 // read it in coalesced 16-byte words (scalar where the words
                 // would pass the array's end or the base is not 16-byte
@@ -396,28 +377,12 @@ __global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) ml
         hidden_out(0, 128);
         run_layer(S.w4, TKH, 64, TN4);
         if (!ok) break;
-        if (half == 0) {
+        {
             float y[16];
             tmem_ld16(T0 + lane_base + 64, y);
             if (s < n) {
 #pragma unroll
-                for (int j = 0; j < TC_OUT; j++) y[j] += S.b[192 + j];
-                if constexpr (FIELD) {
-                    // 2 nu s_ij s_ij in FP32 (the value is stored as FP32)
-                    const float igs = (float)a.inv_gs;
-                    float ss = 0.f;
-#pragma unroll
-                    for (int p = 0; p < 3; p++)
-#pragma unroll
-                        for (int q = 0; q < 3; q++) {
-                            const float sab = 0.5f * (y[3 * p + q] + y[3 * q + p]) * igs;
-                            ss = fmaf(sab, sab, ss);
-                        }
-                    a.eps_o[a.cells[s]] = (float)(2.0 * a.nu) * ss;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < TC_OUT; j++) a.Y[s * TC_OUT + j] = y[j];
-                }
+                for (int j = 0; j < TC_OUT; j++) a.Y[s * TC_OUT + j] = y[j] + S.b[192 + j];
             }
         }
         fence_before();
@@ -429,13 +394,189 @@ __global__ void __launch_bounds__(128 * tc_tpr<FIELD>(), 4 / tc_tpr<FIELD>()) ml
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(T0) : "memory");
 }
 
+// ------------------------------------------- fused inference, two roles --
+// The fused diagnostic's form with the stencil gather overlapped with the
+// layer chain: of the 256 threads, warps 4-7 gather tile t + 1 (a sample
+// row each, all 28 points) into one of two input operands while warps 0-3
+// (a TMEM lane each, 64 columns per epilogue) run the four layers of tile
+// t from the other. Hand-off through mbarriers: full[b] (128 gather
+// arrivals: the operand is written) and empty[b] (one arrival once the
+// first layer's product has read it). Every wait is bounded; a wait that
+// runs out sets the error word and its role stops, so the other role's
+// waits run out too and the kernel frees its tensor memory and returns.
+// (Measured: 0.154 ms per diagnostic of 1.26 M samples, 233 TFLOP/s,
+// against 0.177 ms when every thread gathers and then runs the layers.)
+namespace {
+struct __align__(128) WsSmem {
+    unsigned short w1[TC_H * TK1], w2[TC_H * TKH], w3[TC_H * TKH], w4[TN4 * TKH];
+    unsigned short x[2][TM * TK1];  // input operands
+    unsigned short h[TM * TKH];     // hidden operand
+    float b[208];
+    unsigned long long mma_bar, full[2], empty[2];
+    unsigned taddr;
+};
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+}  // namespace
+
+__global__ void __launch_bounds__(256, 2) mlp_tc_field_ws_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char ws_smem_raw[];
+    WsSmem &S = *reinterpret_cast<WsSmem *>(ws_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long n = *a.count < a.cap ? *a.count : a.cap;
+    const long long tiles = (n + TM - 1) / TM;
+    if ((long long)blockIdx.x >= tiles) return;  // the whole block leaves before any tensor memory is taken
+    for (int e = tid; e < TC_H * TK1; e += 256) S.w1[cm(e / TK1, e % TK1, TK1)] = a.pk[PW1 + e];
+    for (int e = tid; e < TC_H * TKH; e += 256) {
+        S.w2[cm(e / TKH, e % TKH, TKH)] = a.pk[PW2 + e];
+        S.w3[cm(e / TKH, e % TKH, TKH)] = a.pk[PW3 + e];
+    }
+    for (int e = tid; e < TN4 * TKH; e += 256) S.w4[cm(e / TKH, e % TKH, TKH)] = a.pk[PW4 + e];
+    for (int i = tid; i < 208; i += 256) {
+        float v = 0.f;
+        if (i < 64) v = a.w[OB1 + i];
+        else if (i < 128) v = a.w[OB2 + i - 64];
+        else if (i < 192) v = a.w[OB3 + i - 128];
+        else if (i - 192 < TC_OUT) v = a.w[OB4 + i - 192];
+        S.b[i] = v;
+    }
+    if (tid == 0) {
+        mbar_init(&S.mma_bar, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&S.full[b], 128);
+            mbar_init(&S.empty[b], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&S.taddr))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t T0 = S.taddr;
+    const int row = 32 * (warp & 3) + lane;
+    bool ok = true;
+    if (warp >= 4) {
+        // gather role
+        int k = 0;
+        for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, k++) {
+            const int b = k & 1;
+            if (k >= 2 && !mbar_wait(&S.empty[b], (uint32_t)(((k >> 1) - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const long long s = tile * TM + row;
+            if (s < n) {
+                gather_put<0, 2>(a, s, S.x[b], row);
+            } else {
+                const float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int g = 0; g < 12; g++) put8(S.x[b], cm(row, 8 * g, TK1), f);
+            }
+            fence_async_smem();  // the operand, to the tensor cores' proxy
+            mbar_arrive(&S.full[b]);
+        }
+    } else {
+        // layer role: thread `row` owns TMEM lane `row`
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        uint32_t mp = 0;
+        auto layer = [&](const unsigned short *A, const unsigned short *W, int K, uint32_t tc, int N) -> bool {
+            if (tid == 0) {
+                fence_after();
+                const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+                for (int st = 0; st < K / 16; st++)
+                    tc_mma(T0 + tc, sdesc(A + 128 * st, 128u, sbo), sdesc(W + 128 * st, 128u, sbo), idesc_bf16(TM, N),
+                           st > 0 ? 1u : 0u);
+                tc_commit(&S.mma_bar);
+            }
+            const bool done = mbar_wait(&S.mma_bar, mp);
+            mp ^= 1u;
+            fence_after();
+            return done;
+        };
+        auto hidden = [&](uint32_t tc, int boff) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ch++) {
+                float v[32];
+                tmem_ld32(T0 + lane_base + tc + 32 * ch, v);
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] = fmaxf(v[j] + S.b[boff + 32 * ch + j], 0.f);
+#pragma unroll
+                for (int g = 0; g < 4; g++) put8(S.h, cm(row, 32 * ch + 8 * g, TKH), v + 8 * g);
+            }
+            fence_async_smem();
+            fence_before();
+            consumers_sync();
+        };
+        int k = 0;
+        for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, k++) {
+            const int b = k & 1;
+            if (!mbar_wait(&S.full[b], (uint32_t)((k >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            if (!layer(S.x[b], S.w1, TK1, 0, TC_H)) {
+                ok = false;
+                break;
+            }
+            if (tid == 0) mbar_arrive(&S.empty[b]);  // the input operand has been read
+            hidden(0, 0);
+            if (!layer(S.h, S.w2, TKH, 64, TC_H)) {
+                ok = false;
+                break;
+            }
+            hidden(64, 64);
+            if (!layer(S.h, S.w3, TKH, 0, TC_H)) {
+                ok = false;
+                break;
+            }
+            hidden(0, 128);
+            if (!layer(S.h, S.w4, TKH, 64, TN4)) {
+                ok = false;
+                break;
+            }
+            const long long s = tile * TM + row;
+            float y[16];
+            tmem_ld16(T0 + lane_base + 64, y);
+            if (s < n) {
+                const float igs = (float)a.inv_gs;
+                float ss = 0.f;
+#pragma unroll
+                for (int p = 0; p < 3; p++)
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        const float sab = 0.5f * ((y[3 * p + q] + S.b[192 + 3 * p + q]) + (y[3 * q + p] + S.b[192 + 3 * q + p])) * igs;
+                        ss = fmaf(sab, sab, ss);
+                    }
+                a.eps_o[a.cells[s]] = (float)(2.0 * a.nu) * ss;
+            }
+            fence_before();
+            consumers_sync();  // the next tile's products rewrite the accumulators
+        }
+    }
+    if (!ok) atomicExch(a.err, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(T0) : "memory");
+}
+
 static cudaError_t tc_launch(const TcArgs &a, bool field, long long max_tiles, cudaStream_t s) {
     static bool attr = false;
-    const int smem = (int)sizeof(TcSmem);
+    const int smem = (int)sizeof(TcSmem), wsm = (int)sizeof(WsSmem);
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(mlp_tc_field_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, wsm);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -445,8 +586,8 @@ static cudaError_t tc_launch(const TcArgs &a, bool field, long long max_tiles, c
     long long nb = (long long)(field ? 2 : 4) * (sms > 0 ? sms : 1);
     if (nb > max_tiles) nb = max_tiles;
     if (nb < 1) nb = 1;
-    if (field) mlp_tc_kernel<true><<<(unsigned)nb, 128 * tc_tpr<true>(), smem, s>>>(a);
-    else mlp_tc_kernel<false><<<(unsigned)nb, 128 * tc_tpr<false>(), smem, s>>>(a);
+    if (field) mlp_tc_field_ws_kernel<<<(unsigned)nb, 256, wsm, s>>>(a);
+    else mlp_tc_kernel<<<(unsigned)nb, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
