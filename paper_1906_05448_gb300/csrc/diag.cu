@@ -371,18 +371,37 @@ __global__ void closure_target_kernel(const double *u, const uint8_t *flags, con
 
 // the near-surface fluid nodes of the fused closure dissipation: cell and
 // nearest particle (distance to the surface in (0, 2]); order not fixed
-__global__ void closure_list_kernel(const uint8_t *flags, const unsigned long long *near_key, long long N, int *cells,
-                                    int *pids, long long *count, long long cap) {
+// One slot range per block and 256 consecutive cells, filled in cell
+// order, so that neighbouring samples of the list are mostly neighbouring
+// cells (their stencils share lines in the inference kernel's gather).
+__global__ void __launch_bounds__(256) closure_list_kernel(const uint8_t *flags, const unsigned long long *near_key,
+                                                           long long N, int *cells, int *pids, long long *count,
+                                                           long long cap) {
+    __shared__ unsigned wcnt[8];
+    __shared__ unsigned long long base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long span = (long long)gridDim.x * blockDim.x;
     for (long long c0 = (long long)blockIdx.x * blockDim.x; c0 < N; c0 += span) {
         const long long c = c0 + threadIdx.x;
         const unsigned long long key = c < N && !(flags[c] & FL_SOLID) ? near_key[c] : NEAR_EMPTY;
         const double d = near_s_of(key);  // r - R_p of the nearest particle
         const bool take = key != NEAR_EMPTY && d > 0.0 && d <= 2.0;
-        const long long k = warp_slot(take, count);
-        if (!take || k >= cap) continue;
-        cells[k] = (int)c;
-        pids[k] = near_pid_of(key);
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) wcnt[warp] = (unsigned)__popc(m);
+        __syncthreads();
+        unsigned before = 0, total = 0;
+        for (int w = 0; w < 8; w++) {
+            before += w < warp ? wcnt[w] : 0u;
+            total += wcnt[w];
+        }
+        if (threadIdx.x == 0) base = total ? atomicAdd((unsigned long long *)count, (unsigned long long)total) : 0ull;
+        __syncthreads();
+        const long long k = (long long)base + before + __popc(m & ((1u << lane) - 1u));
+        if (take && k < cap) {
+            cells[k] = (int)c;
+            pids[k] = near_pid_of(key);
+        }
+        __syncthreads();  // wcnt and base are rewritten next round
     }
 }
 

@@ -741,6 +741,12 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
         q27_pipe_colmask(c, mask);
         CK(cudaMemcpy(c.q27_colmask, mask.data(), sizeof(unsigned) * mask.size(), cudaMemcpyHostToDevice));
         CK(launch_q27_coef(c));
+        // no fluid column on an x or y face: the sweep addresses pulls by plane pointers
+        c.pipe_nowrap = 1;
+        for (int y = 0; y < c.ny; y++)
+            for (int x = 0; x < c.nx; x++)
+                if (!(mask[(size_t)x + (size_t)c.nx * y] & 1u) && (x == 0 || x == c.nx - 1 || y == 0 || y == c.ny - 1))
+                    c.pipe_nowrap = 0;
         return sync_all(c);
     }
     c.has_pipe = 1;

@@ -178,6 +178,12 @@ struct Q27PipeArgs {
     Q27Args b;
     const unsigned *colmask, *hmask;
     const void *coef;  // per column x 27 directions: two weights in the arithmetic type
+    // when no fluid cell touches an x or y face: the pull of direction i
+    // for cell c is Ap[i][c] (plus N or minus N across the z ends), its
+    // store Bp[i][c]: one address operation per access
+    int nowrap;
+    const void *Ap[Q27];  // A + i N - (c_x + nx c_y + nx ny c_z)
+    void *Bp[Q27];        // B + i N
 };
 
 template <typename R>
@@ -243,12 +249,21 @@ __global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
     T *__restrict__ B = (T *)a.B;
     const size_t N = (size_t)a.N;
     R g[Q27];
+    if (pa.nowrap) {
+        const int zpl = z == 0 ? (int)N : 0, zmi = z == nz - 1 ? (int)N : 0;
 #pragma unroll
-    for (int i = 0; i < Q27; i++) {
-        const int xs = q27x(i) > 0 ? xm : (q27x(i) < 0 ? xp : x);
-        const int ys = q27y(i) > 0 ? ym : (q27y(i) < 0 ? yp : y);
-        const int zs = q27z(i) > 0 ? zm : (q27z(i) < 0 ? zp : z);
-        g[i] = Store<S>::ld(A + (i * N + (size_t)(xs + nx * (ys + ny * zs))));
+        for (int i = 0; i < Q27; i++) {
+            const int o = (int)c + (q27z(i) > 0 ? zpl : 0) - (q27z(i) < 0 ? zmi : 0);
+            g[i] = Store<S>::ld((const T *)pa.Ap[i] + o);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q27; i++) {
+            const int xs = q27x(i) > 0 ? xm : (q27x(i) < 0 ? xp : x);
+            const int ys = q27y(i) > 0 ? ym : (q27y(i) < 0 ? yp : y);
+            const int zs = q27z(i) > 0 ? zm : (q27z(i) < 0 ? zp : z);
+            g[i] = Store<S>::ld(A + (i * N + (size_t)(xs + nx * (ys + ny * zs))));
+        }
     }
     if (m) {  // wall cell: the populations coming back from the wall
         const unsigned h = __ldg(pa.hmask + rem);
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
             const R cF = R(q27x(i)) * Fx + R(q27y(i)) * Fy + R(q27z(i)) * Fz;
             v += (c1 * R(q27w(i))) * (R(3) * cF - uF3 + R(9) * cu * cF);
         }
-        Store<S>::st(B + (i * N + (size_t)c), v);
+        Store<S>::st(pa.nowrap ? (T *)pa.Bp[i] + c : B + (i * N + (size_t)c), v);
     }
     watchdog(rho, ux, uy, uz, a.status);
 }
@@ -321,7 +336,18 @@ cudaError_t launch_q27_step(Ctx &c) {
     const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
     count_launch(c, G_BULK);
     if (c.has_pipe) {
-        Q27PipeArgs pa{a, c.q27_colmask, c.q27_hmask, c.q27_coef};
+        Q27PipeArgs pa;
+        pa.b = a;
+        pa.colmask = c.q27_colmask;
+        pa.hmask = c.q27_hmask;
+        pa.coef = c.q27_coef;
+        pa.nowrap = c.pipe_nowrap && c.N < (1LL << 30);
+        const size_t sb = storage_bytes(c.storage);
+        for (int i = 0; i < Q27; i++) {
+            const long long off = q27x(i) + (long long)c.nx * q27y(i) + (long long)c.nx * c.ny * q27z(i);
+            pa.Ap[i] = (const void *)((const char *)c.fA + sb * (size_t)((long long)i * c.N - off));
+            pa.Bp[i] = (void *)((char *)c.fB + sb * (size_t)((long long)i * c.N));
+        }
         const unsigned nb = (unsigned)((c.N + 255) / 256);
         if (c.storage == LBM_F64) {
             if (force) q27_pipe_kernel<LBM_F64, true><<<nb, 256, 0, c.stream>>>(pa);

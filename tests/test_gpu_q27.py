@@ -83,12 +83,15 @@ def _pipe_pair(lbm, nx, ny, nz, R, tau, F, storage, seed):
     return g, o, solid, links
 
 
-@pytest.mark.parametrize("R", [10.3, 6.4])
+@pytest.mark.parametrize("R", [10.3, 6.4, 7.4])
 def test_pipe_wall_f64_step_by_step(lbm, R):
     """The D3Q27 pipe with the linear interpolated bounce-back on its wall
-    (and the halfway fallback, which the 6.4 radius in a 16 x 16 section
+    (and the halfway fallback, which the 6.4 radius in a 16 x 15 section
     reaches), a body force along z: every fluid cell's populations after
-    each step against the oracle's pipe step."""
+    each step against the oracle's pipe step. The 7.4 radius in a 16 x 15
+    section puts fluid cells on the y faces, whose pulls wrap
+    periodically; the other two keep the faces solid, where the sweep
+    addresses pulls by per-direction plane pointers."""
     n = 24 if R > 8 else 16
     nz, F, tau = 5, (0.0, 0.0, 3e-6), 0.62
     g, o, solid, links = _pipe_pair(lbm, n, n - 1, nz, R, tau, F, lbm.F64, seed=3)
