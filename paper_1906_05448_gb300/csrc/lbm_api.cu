@@ -44,7 +44,7 @@ struct Plan {
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, slink4, seg_bnd, bvals, wrec, gidx, gvals, refill;
+    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, slink4, seg_bnd, bvals, wrec, gidx, gvals, wcoef, wlane, refill;
     long long max_refill;
     long long max_seg;
     size_t xy_start, xy_j, xy_w, it_k, it_w;
@@ -118,6 +118,8 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.wrec = L.take(8 * ms);
     P.gidx = L.take(4 * ml);
     P.gvals = L.take(sb * ml);
+    P.wcoef = L.take(8 * ml);
+    P.wlane = L.take(2 * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
     P.counts = L.take(64);
@@ -609,6 +611,9 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.wrec = (uint2 *)(b + P.wrec);
     c.gidx = (int *)(b + P.gidx);
     c.gvals = b + P.gvals;
+    c.wcoef = (uint2 *)(b + P.wcoef);
+    c.wlane = (unsigned short *)(b + P.wlane);
+    c.wcoef_ready = 0;
     c.max_bvals = P.max_sites;
     c.bvals_ready = 0;
     c.bvals_valid = 0;
@@ -835,6 +840,7 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
             // per sweep item: rank of its first wall cell and the lanes that hold wall cells
             bool bok = LBM_WALL_VALUES && sorted && c.nseg > 0 && (long long)bcells.size() <= c.max_bvals;
             std::vector<uint2> sb(bok ? items.size() : 0);
+            std::vector<int> lane_of(bok ? bcells.size() : 0, -1);  // sweep lane of each wall cell
             for (size_t it = 0; bok && it < items.size(); it++) {
                 const SweepItem &w = items[it];
                 const unsigned la = (w.word_a >> 16) & 0xff;
@@ -852,6 +858,7 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
                     if (base < 0) base = r;
                     if (r != base + __builtin_popcount(mask)) bok = false;  // ranks must follow the lanes
                     mask |= 1u << lane;
+                    lane_of[(size_t)r] = (int)lane;
                 }
                 sb[it] = make_uint2((unsigned)(base < 0 ? 0 : base), mask);
             }
@@ -889,6 +896,9 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
                 // for q < 1/2; 1/(2q), (2q - 1)/(2q) on f_l(x_f), f_ibar(x_f)
                 // for q >= 1/2; the single-node scheme keeps 0.5 (1 - 2q))
                 std::vector<uint4> r4(nl);
+                // the inline wall form's weights and lanes, in the order of the compact values
+                std::vector<uint2> wc(nl);
+                std::vector<unsigned short> wl(nl, 0);
                 bool rok = true;
                 for (size_t at = 0; at < nl && rok; at++) {
                     const unsigned cell = pk[at].x & 0x3fffffffu, sch = pk[at].x >> 30;
@@ -922,10 +932,26 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
                     std::memcpy(&b1, &k1, 4);
                     std::memcpy(&b2, &k2, 4);
                     r4[at] = make_uint4(c1 | (own << 30) | (single << 31), b1, b2, (unsigned)rk[at]);
+                    wc[(size_t)gx[at]] = make_uint2(b1, b2 | (own << 31));
+                }
+                for (size_t r = 0; r < bcells.size() && rok; r++) {
+                    if (lane_of[r] < 0) {
+                        rok = false;  // a wall cell no sweep lane holds
+                        break;
+                    }
+                    for (int i = 0; i < 19; i++)
+                        if ((wr[r].y >> i) & 1u)
+                            wl[wr[r].x + (unsigned)__builtin_popcount(wr[r].y & ((1u << i) - 1u))] =
+                                (unsigned short)(lane_of[r] | (i << 5));
                 }
                 rok = rok && c.pipe_nowrap;  // the pass recovers x_f from x_f - c_l across z ends only
-                if (rok) CK(cudaMemcpy(c.slink4, r4.data(), 16 * nl, cudaMemcpyHostToDevice));
+                if (rok) {
+                    CK(cudaMemcpy(c.slink4, r4.data(), 16 * nl, cudaMemcpyHostToDevice));
+                    CK(cudaMemcpy(c.wcoef, wc.data(), 8 * nl, cudaMemcpyHostToDevice));
+                    CK(cudaMemcpy(c.wlane, wl.data(), 2 * nl, cudaMemcpyHostToDevice));
+                }
                 c.slink4_ready = rok ? 1 : 0;
+                c.wcoef_ready = rok ? 1 : 0;
             }
         }
     }
@@ -1016,7 +1042,8 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
             t1 = pmark(c);
             pspan(c, G_BND, t0, t1);
             CK(launch_stream_collide(c, bc));
-            c.bvals_valid = c.bvals_ready;  // the sweep wrote the wall cells' values
+            // what the sweep left for the next step's wall
+            c.bvals_valid = pipe_inline_walls(c) ? 2 : (c.bvals_ready ? 1 : 0);
             t0 = pmark(c);
             pspan(c, G_BULK, t1, t0);
             if (c.np > 0) CK(launch_gimem(c));

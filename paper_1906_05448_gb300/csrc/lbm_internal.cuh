@@ -72,7 +72,13 @@ struct Ctx {
     void *gvals;
     int bvals_ready;    // the tables above are built
     int pipe_nowrap;    // no fluid cell on an x or y face: pulls wrap only in z (lean pipe sweep)
-    int bvals_valid;    // bvals holds the values of the current state
+    // what the last sweep left for the next step's wall: 0 nothing (read
+    // the populations), 1 bvals holds the wall cells' values of the current
+    // state, 2 gvals holds the partial values p of the inline wall form
+    int bvals_valid;
+    uint2 *wcoef;       // inline wall form: per compact value k1, k2 (bit 31: q >= 1/2)
+    unsigned short *wlane;  // inline wall form: per compact value its wall cell's sweep lane | direction << 5
+    int wcoef_ready;
     // compaction scratch
     int nblk;
     long long *blk_sites, *blk_links;
@@ -162,6 +168,8 @@ cudaError_t launch_set_populations(Ctx &c, const double *f_dev);
 cudaError_t launch_get_populations(Ctx &c, double *f_dev);
 cudaError_t launch_stream_collide(Ctx &c, int bc);
 bool launch_pipe_sweep(Ctx &c, cudaError_t &err);  // sweep_pipe.cu: false when it does not apply
+bool pipe_inline_walls(const Ctx &c);             // the lean sweep runs the inline wall form
+cudaError_t launch_pipe_wall_prime(Ctx &c);       // partial values p from the populations
 cudaError_t launch_ibb_links(Ctx &c);
 cudaEvent_t prof_event(Ctx &c);  // profiling event on the stream (null when off)
 void prof_span(Ctx &c, int g, cudaEvent_t a, cudaEvent_t b);  // time from a to b into group g

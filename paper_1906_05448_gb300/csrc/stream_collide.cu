@@ -435,12 +435,15 @@ template <int S>
 static cudaError_t launch_links_s(Ctx &c) {
     if (c.max_links == 0) return cudaSuccess;
     if (c.static_links && c.np == 0 && S != LBM_F64) {
+        // the inline wall form: the last sweep left the partial values, or
+        // they are formed once from the populations
+        if (pipe_inline_walls(c)) return c.bvals_valid == 2 ? cudaSuccess : launch_pipe_wall_prime(c);
         StaticLinkArgs a;
         a.A = c.fA;
         a.slink4 = c.slink4;
         a.slink = c.slink;
         a.rank = c.slink_rank;
-        a.bvals = c.bvals_valid ? c.bvals : nullptr;
+        a.bvals = c.bvals_valid == 1 ? c.bvals : nullptr;
         a.gidx = c.gidx;
         a.gvals = c.bvals_ready ? c.gvals : nullptr;
         for (int l = 0; l < 20; l++) a.off[l] = c.slink_off[l];
