@@ -1020,11 +1020,21 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
     } else if (c.armed_bc != bc) {
         return fail(c, LBM_ESTATE, "boundary treatment fixed to %d by the first step", c.armed_bc);
     }
+    // profiling: one event at each boundary between groups that launched
+    // something (adjacent spans share it; a group that launched nothing in
+    // a step records no span), so the steady pipe step carries one event
+    cudaEvent_t t0 = nsteps > 0 ? pmark(c) : nullptr;
+    auto close = [&](int g, long long before) {
+        if (c.group_launches[g] == before) return;
+        cudaEvent_t t1 = pmark(c);
+        pspan(c, g, t0, t1);
+        t0 = t1;
+    };
     if (c.q == 27) {  // periodic box, or the pipe with its wall inside the sweep (checked above)
         for (int n = 0; n < nsteps; n++) {
-            cudaEvent_t t0 = pmark(c);
+            const long long b0 = c.group_launches[G_BULK];
             CK(launch_q27_step(c));
-            pspan(c, G_BULK, t0, pmark(c));
+            close(G_BULK, b0);
             std::swap(c.fA, c.fB);
             c.step++;
         }
@@ -1033,57 +1043,59 @@ lbm_status lbm_step(lbm_ctx *h, int nsteps, int bc) {
     const bool ibm = bc == LBM_BC_IBM_U || bc == LBM_BC_IBM_B;
     const bool moving = c.np > 0 && !c.fixed;
     for (int n = 0; n < nsteps; n++) {
-        cudaEvent_t t0 = pmark(c), t1;
+        long long b0 = c.group_launches[G_BULK];
         if (bc == LBM_BC_NONE) {
             CK(launch_stream_collide(c, bc));
-            pspan(c, G_BULK, t0, pmark(c));
+            close(G_BULK, b0);
         } else if (bc == LBM_BC_IBB) {
+            const long long l0 = c.group_launches[G_BND];
             CK(launch_ibb_links(c));
-            t1 = pmark(c);
-            pspan(c, G_BND, t0, t1);
+            close(G_BND, l0);
+            b0 = c.group_launches[G_BULK];
             CK(launch_stream_collide(c, bc));
             // what the sweep left for the next step's wall
             c.bvals_valid = pipe_inline_walls(c) ? 2 : (c.bvals_ready ? 1 : 0);
-            t0 = pmark(c);
-            pspan(c, G_BULK, t1, t0);
+            close(G_BULK, b0);
+            const long long p0 = c.group_launches[G_PART];
             if (c.np > 0) CK(launch_gimem(c));
             if (moving) CK(launch_particle_update(c));
-            t1 = pmark(c);
-            pspan(c, G_PART, t0, t1);
+            close(G_PART, p0);
+            const long long g0 = c.group_launches[G_GEOM];
             if (moving) {
                 CK(launch_sphere_mark(c, true));
                 CK(launch_refill(c));
                 CK(launch_finish_geometry(c));
                 CK(build_sites(c, 1));
             }
-            pspan(c, G_GEOM, t1, pmark(c));
+            close(G_GEOM, g0);
         } else if (ibm) {
+            long long g0 = c.group_launches[G_GEOM];
             if (moving && c.step > 0) {
                 CK(launch_support_mark(c));
                 CK(build_sites(c, 2));
             }
-            t1 = pmark(c);
-            pspan(c, G_GEOM, t0, t1);
+            close(G_GEOM, g0);
+            b0 = c.group_launches[G_BULK];
             CK(launch_stream_collide(c, bc));
-            t0 = pmark(c);
-            pspan(c, G_BULK, t1, t0);
+            close(G_BULK, b0);
+            const long long i0 = c.group_launches[G_IBM];
             CK(launch_ibm_passes(c));
-            t1 = pmark(c);
-            pspan(c, G_IBM, t0, t1);
+            close(G_IBM, i0);
+            const long long k0 = c.group_launches[G_IBMCOL];
             CK(launch_ibm_collide(c));
-            t0 = pmark(c);
-            pspan(c, G_IBMCOL, t1, t0);
+            close(G_IBMCOL, k0);
+            const long long p0 = c.group_launches[G_PART];
             if (c.np > 0) CK(launch_ibm_particle_sums(c, false));
             if (moving) CK(launch_particle_update(c));
-            t1 = pmark(c);
-            pspan(c, G_PART, t0, t1);
+            close(G_PART, p0);
+            g0 = c.group_launches[G_GEOM];
             if (moving) {
                 CK(launch_markers_place(c));
                 CK(launch_marker_offsets(c));
                 CK(launch_sphere_mark(c, true));
                 CK(launch_finish_geometry(c));
             }
-            pspan(c, G_GEOM, t1, pmark(c));
+            close(G_GEOM, g0);
         }
         std::swap(c.fA, c.fB);
         c.step++;
