@@ -740,11 +740,9 @@ __global__ void __launch_bounds__(CT) site_emit_kernel(SiteArgs a) {
             if (a.mode == 1) {
                 // cell and direction only; link_geom_kernel fills in q, owner and scheme
                 long long lk = l0;
-                for (int l = 1; l < 19; l++) {
-                    if (!((mask[k] >> l) & 1u)) continue;
+                for (unsigned mm = mask[k] & ~1u; mm; mm &= mm - 1u, lk++) {  // set bits, ascending
                     a.link_cell[lk] = (int)c;
-                    a.link_dir[lk] = (int8_t)l;
-                    lk++;
+                    a.link_dir[lk] = (int8_t)(__ffs(mm) - 1);
                 }
             }
         } else if (a.mode == 2) {
@@ -820,6 +818,46 @@ __global__ void __launch_bounds__(256) bnd_mark_kernel(SiteArgs a) {
     }
 }
 
+// bnd_mark_kernel with the solid bits of the particle's box and its one-cell
+// rim staged in shared memory (a tile of side T, the same for every
+// particle, T >= 2 (ceil R_p + 2) + 4): the 18 neighbour tests of a shell
+// cell become loads at fixed offsets. The kernel changes only BND bits, so
+// the staged solid bits stay those of the grid.
+__global__ void __launch_bounds__(256) bnd_mark_tile_kernel(SiteArgs a, int T) {
+    extern __shared__ uint8_t sol[];
+    const int p = blockIdx.x;
+    const int r = (int)ceil(a.R[p]) + 2;
+    const int bx = (int)floor(a.X[3 * p]) - r, by = (int)floor(a.X[3 * p + 1]) - r, bz = (int)floor(a.X[3 * p + 2]) - r;
+    const int w = 2 * r + 2;
+    const FastDiv fT((unsigned)T), fw((unsigned)w);
+    for (int t = threadIdx.x; t < T * T * T; t += blockDim.x) {
+        int ix, iy, iz;
+        box_coords(t, fT, T, ix, iy, iz);
+        const int x = gwrap(bx - 1 + ix, a.nx), y = gwrap(by - 1 + iy, a.ny), z = gwrap(bz - 1 + iz, a.nz);
+        sol[t] = a.flags[(long long)x + (long long)a.nx * (y + (long long)a.ny * z)] & FL_SOLID;
+    }
+    __syncthreads();
+    const float Ro = (float)a.R[p] + 1.5f, Ri = fmaxf((float)a.R[p] - 1.5f, 0.f), ro2 = Ro * Ro, ri2 = Ri * Ri;
+    const float fX0 = (float)a.X[3 * p] - bx, fX1 = (float)a.X[3 * p + 1] - by, fX2 = (float)a.X[3 * p + 2] - bz;
+    for (int t = threadIdx.x; t < w * w * w; t += blockDim.x) {
+        int ix, iy, iz;
+        box_coords(t, fw, w, ix, iy, iz);
+        const float ex = ix - fX0, ey = iy - fX1, ez = iz - fX2, e2 = ex * ex + ey * ey + ez * ez;
+        if (e2 > ro2 || e2 < ri2) continue;
+        const uint8_t *s = sol + (ix + 1) + T * ((iy + 1) + T * (iz + 1));
+        if (*s) continue;
+        unsigned m = 0;
+#pragma unroll
+        for (int l = 1; l < 19; l++)
+            if (s[cx(l) + T * (cy(l) + T * cz(l))]) m |= 1u << l;
+        if (m == 0u) continue;
+        const int x = gwrap(bx + ix, a.nx), y = gwrap(by + iy, a.ny), z = gwrap(bz + iz, a.nz);
+        const long long c = (long long)x + (long long)a.nx * (y + (long long)a.ny * z);
+        a.aux[c] = (int)m;  // the same value from every box that holds the cell
+        atomic_or_flag(a.flags, c, FL_BND);
+    }
+}
+
 // the VT flag bytes of a thread's cells (zero past the grid's end)
 __device__ __forceinline__ void load_flags16(const SiteArgs &a, long long base, uint8_t f[VT]) {
     if (base + VT <= a.N) {
@@ -890,11 +928,9 @@ __global__ void __launch_bounds__(CT) bnd_emit_kernel(SiteArgs a) {
             a.site_mask[s0] = m;
             a.aux[c] = (int)s0;
             long long lk = l0;
-            for (int l = 1; l < 19; l++) {
-                if (!((m >> l) & 1u)) continue;
+            for (unsigned mm = m & ~1u; mm; mm &= mm - 1u, lk++) {  // set bits, ascending
                 a.link_cell[lk] = (int)c;
-                a.link_dir[lk] = (int8_t)l;
-                lk++;
+                a.link_dir[lk] = (int8_t)(__ffs(mm) - 1);
             }
         } else {
             a.flags[c] = (uint8_t)(a.flags[c] & ~FL_BND);
@@ -954,7 +990,10 @@ cudaError_t build_sites(Ctx &c, int mode) {
         count_launch(c, G_GEOM, 6);  // with the link pass below
         bnd_clear_kernel<<<(unsigned)std::min<long long>(152LL * 8, (c.max_sites + 255) / 256), 256, 0, c.stream>>>(
             c.flags, c.site_cell, c.d_counts, c.max_sites);
-        bnd_mark_kernel<<<c.np, 256, 0, c.stream>>>(a);
+        // the shared-memory tile of the largest particle's box and rim, when it is small
+        const int T = 2 * ((int)ceil(c.max_radius) + 2) + 4;
+        if ((long long)T * T * T <= 32768) bnd_mark_tile_kernel<<<c.np, 256, (size_t)T * T * T, c.stream>>>(a, T);
+        else bnd_mark_kernel<<<c.np, 256, 0, c.stream>>>(a);
         bnd_count_kernel<<<nblk, CT, 0, c.stream>>>(a);
         site_scan_kernel<<<1, ST, 0, c.stream>>>(a, nblk);
         bnd_emit_kernel<<<nblk, CT, 0, c.stream>>>(a);
