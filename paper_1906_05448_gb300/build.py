@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm_gb300.so")
-SOURCES = ["lbm_api.cu", "sweep.cu", "sweep_pipe.cu", "stream_collide.cu", "geometry.cu", "particles.cu", "diag.cu", "closure.cu", "closure_tc.cu", "spectra.cu", "noalloc.cu", "budget.cu", "q27.cu"]
+SOURCES = ["lbm_api.cu", "sweep.cu", "sweep_pipe.cu", "sweep_pair16.cu", "stream_collide.cu", "geometry.cu", "particles.cu", "diag.cu", "closure.cu", "closure_tc.cu", "spectra.cu", "noalloc.cu", "budget.cu", "q27.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

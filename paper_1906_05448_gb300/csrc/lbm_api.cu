@@ -44,7 +44,7 @@ struct Plan {
     size_t fA, fB, flags, owner, aux;
     size_t site_cell, site_first, site_mask, sup_ru, sup_F, sup_Fp;
     size_t link_cell, link_pid, link_dir, link_scheme, link_q, link_dP, link_dT;
-    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, slink4, seg_bnd, bvals, wrec, gidx, gvals, wcoef, wlane, refill;
+    size_t blk_sites, blk_links, counts, status, seg, slink, slink_rank, slink4, seg_bnd, bvals, wrec, gidx, gvals, wcoef, wlane, pair_items, pair_wall, wslot, refill;
     long long max_refill;
     long long max_seg;
     size_t xy_start, xy_j, xy_w, it_k, it_w;
@@ -120,6 +120,9 @@ bool make_plan(const lbm_grid *g, Plan &P) {
     P.gvals = L.take(sb * ml);
     P.wcoef = L.take(8 * ml);
     P.wlane = L.take(2 * ml);
+    P.pair_items = L.take(16 * (size_t)P.max_seg);
+    P.pair_wall = L.take(16 * (size_t)P.max_seg);
+    P.wslot = L.take(2 * ml);
     P.blk_sites = L.take(8 * (size_t)P.nblk);
     P.blk_links = L.take(8 * (size_t)P.nblk);
     P.counts = L.take(64);
@@ -613,6 +616,10 @@ lbm_status lbm_create(const lbm_grid *grid, double tau, const double force[3], v
     c.gvals = b + P.gvals;
     c.wcoef = (uint2 *)(b + P.wcoef);
     c.wlane = (unsigned short *)(b + P.wlane);
+    c.pair_items = (uint4 *)(b + P.pair_items);
+    c.pair_wall = (uint4 *)(b + P.pair_wall);
+    c.wslot = (unsigned short *)(b + P.wslot);
+    c.pair_ready = 0;
     c.wcoef_ready = 0;
     c.max_bvals = P.max_sites;
     c.bvals_ready = 0;
@@ -952,6 +959,8 @@ lbm_status lbm_set_pipe(lbm_ctx *h, double radius) {
                 }
                 c.slink4_ready = rok ? 1 : 0;
                 c.wcoef_ready = rok ? 1 : 0;
+                // 16-bit storage: the pair sweep's work list and wall tables
+                if (rok && (c.storage == LBM_F16S || c.storage == LBM_BF16S)) build_pair16(c, fl.data(), bcells, wr);
             }
         }
     }

@@ -78,6 +78,13 @@ struct Ctx {
     int bvals_valid;
     uint2 *wcoef;       // inline wall form: per compact value k1, k2 (bit 31: q >= 1/2)
     unsigned short *wlane;  // inline wall form: per compact value its wall cell's sweep lane | direction << 5
+    // the pair sweep of 16-bit storage (sweep_pair16.cu): items of up to 32
+    // cell pairs, per item {first slot, links, 64-bit wall-cell mask}, per
+    // compact value the cell of its item | direction << 6
+    uint4 *pair_items, *pair_wall;
+    unsigned short *wslot;
+    long long npair_items;
+    int pair_ready;
     int wcoef_ready;
     // compaction scratch
     int nblk;
@@ -169,6 +176,8 @@ cudaError_t launch_get_populations(Ctx &c, double *f_dev);
 cudaError_t launch_stream_collide(Ctx &c, int bc);
 bool launch_pipe_sweep(Ctx &c, cudaError_t &err);  // sweep_pipe.cu: false when it does not apply
 bool pipe_inline_walls(const Ctx &c);             // the lean sweep runs the inline wall form
+bool launch_pair16_sweep(Ctx &c, cudaError_t &err);  // sweep_pair16.cu: false when it does not apply
+bool build_pair16(Ctx &c, const uint8_t *fl, const std::vector<int> &bcells, const std::vector<uint2> &wr);
 cudaError_t launch_pipe_wall_prime(Ctx &c);       // partial values p from the populations
 cudaError_t launch_ibb_links(Ctx &c);
 cudaEvent_t prof_event(Ctx &c);  // profiling event on the stream (null when off)

@@ -355,6 +355,7 @@ static cudaError_t launch_bulk_s(Ctx &c, int bc, bool force) {
 cudaError_t launch_stream_collide(Ctx &c, int bc) {
     if (LBM_PIPE_SWEEP && bc == LBM_BC_IBB) {
         cudaError_t e = cudaSuccess;
+        if (launch_pair16_sweep(c, e)) return e;
         if (launch_pipe_sweep(c, e)) return e;
     }
     const bool force = c.F[0] != 0.0 || c.F[1] != 0.0 || c.F[2] != 0.0;
