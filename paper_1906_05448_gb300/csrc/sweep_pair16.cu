@@ -137,11 +137,6 @@ template <int S>
 __device__ __forceinline__ float unpack1(unsigned short v) {
     return unpack2<S>((unsigned)v).x;
 }
-// a value as it reads back from 16-bit storage
-template <int S>
-__device__ __forceinline__ float round16(float v) {
-    return unpack2<S>(pack2<S>(make_float2(v, 0.0f))).x;
-}
 
 // the partial value p of a wall link (w: k1, k2 with bit 31 set for
 // q >= 1/2) from the wall cell's own values f*_l and f*_ibar: the arithmetic
@@ -266,18 +261,16 @@ __global__ void __launch_bounds__(256, LBM_PAIR16_MINB) stream_collide_pair16(Pa
 #pragma unroll
             for (int i = 0; i < 19; i++) {
                 // zero cells (solid) complete the word
-                const float2 v = make_float2(zero0 ? 0.0f : g[i].x, zero1 ? 0.0f : g[i].y);
-                *((unsigned *)((T *)a.Bp[i] + c0)) = pack2<S>(v);
-            }
-        }
-        if (lnum) {  // the values for the partial values p of the next step
-            if (mine) {
-#pragma unroll
-                for (int i = 0; i < 19; i++) {
-                    gs[i][2 * lane] = round16<S>(g[i].x);
-                    gs[i][2 * lane + 1] = round16<S>(g[i].y);
+                const unsigned word = pack2<S>(make_float2(zero0 ? 0.0f : g[i].x, zero1 ? 0.0f : g[i].y));
+                *((unsigned *)((T *)a.Bp[i] + c0)) = word;
+                if (mine) {  // wall cells: the stored values, for the partial values p of the next step
+                    const float2 r = unpack2<S>(word);
+                    gs[i][2 * lane] = r.x;
+                    gs[i][2 * lane + 1] = r.y;
                 }
             }
+        }
+        if (lnum) {
             __syncwarp();
             pb0 = lb0;
             pnum = lnum;
