@@ -375,6 +375,23 @@ def test_16bit_storage_ragged_rows_and_pipe(lbm, storage, tol):
     assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol
 
 
+@pytest.mark.parametrize("storage,tol", [("f16s", 2e-3), ("bf16s", 3e-2)])
+def test_16bit_pipe_odd_width_one_cell_sweep(lbm, storage, tol):
+    """A pipe of odd width on 16-bit storage: pairs of cells do not share
+    aligned words, so the one-cell sweep of the inline wall form runs
+    (even widths take the two-cells-per-lane sweep)."""
+    nx, ny, nz, R = 47, 46, 8, 21.5
+    g, o = pair(lbm, (nz, ny, nx), 0.6, force=(0, 0, 2e-6), storage=lbm.STORAGE[storage])
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.02, perturbation=0.1, seed=6)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.set_pipe(R)
+    g.step(100, lbm.BC_IBB)
+    o.step(100, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0
+    assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol
+
+
 def test_moving_spheres_ibm_b_f32_200_steps(lbm):
     """The particle-laden IBM-B step in FP32 storage (the benchmark's HIT
     path) over 200 steps: velocity, density and the particles' motion."""
