@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "pairs.h"
 #include "segments.h"
 
 namespace lbmgb {
@@ -280,85 +281,21 @@ __global__ void __launch_bounds__(256, LBM_PAIR16_MINB) stream_collide_pair16(Pa
 }
 
 // ----------------------------------------------------------------- host --
-// The pair work list and wall tables of a static wall whose fluid runs the
-// one-cell sweep already lists (fl: flags, host copy; bcells: wall cells in
-// cell order, their rank the index; wr: per rank its first ghost slot and
-// the mask of directions it replaces). Returns false (nothing built) when
-// the grid or the wall does not fit the form: nx odd, more items than the
-// workspace holds, or an item whose wall cells are not consecutive ranks.
+// The pair work list and wall tables (pairs.h) of a static wall whose fluid
+// runs the one-cell sweep already lists, uploaded to the workspace. Returns
+// false (nothing built) when the form does not fit or the workspace holds
+// too few items.
 bool build_pair16(Ctx &c, const uint8_t *fl, const std::vector<int> &bcells, const std::vector<uint2> &wr) {
     c.pair_ready = 0;
-    if (c.nx % 2 != 0 || c.nx >= 65536) return false;
-    std::vector<unsigned long long> segs;
-    for (long long row = 0; row < (long long)c.ny * c.nz; row++) {
-        const long long base = row * c.nx;
-        for (int x = 0; x < c.nx;) {
-            if (fl[base + x] & FL_SOLID) {
-                x++;
-                continue;
-            }
-            int xe = x;
-            while (xe + 1 < c.nx && !(fl[base + xe + 1] & FL_SOLID)) xe++;
-            // pairs from an even cell: an odd first cell takes its solid left
-            // neighbour, an even last cell its solid right neighbour
-            const int lead = x & 1, trail = (xe & 1) ? 0 : 1;
-            const int xs = x - lead, np = (xe + trail - xs + 1) / 2;
-            for (int off = 0; off < np; off += 32) {
-                const int len = np - off < 32 ? np - off : 32;
-                const int fa = off == 0 ? lead : 0, zt = off + len == np ? trail : 0;
-                segs.push_back((unsigned long long)row | ((unsigned long long)(xs / 2 + off + fa) << 32) |
-                               ((unsigned long long)len << 48) | ((unsigned long long)fa << 56) |
-                               ((unsigned long long)zt << 60));
-            }
-            x = xe + 1;
-        }
-    }
     std::vector<SweepItem> items;
-    pack_sweep_items(segs, items);
+    std::vector<PairItemWall> iw;
+    std::vector<unsigned short> ws;
+    if (!build_pair_tables(fl, c.nx, c.ny, c.nz, FL_SOLID, bcells, wr, items, iw, ws)) return false;
     if ((long long)items.size() > c.max_seg) return false;
-    auto rank_of = [&](long long cell) -> long long {
-        auto it = std::lower_bound(bcells.begin(), bcells.end(), (int)cell);
-        return (it != bcells.end() && *it == (int)cell) ? (long long)(it - bcells.begin()) : -1;
-    };
-    std::vector<uint4> iw(items.size());
-    size_t nl = 0;
-    for (const uint2 &v : wr) nl += (size_t)__builtin_popcount(v.y);
-    std::vector<unsigned short> ws(nl, 0);
-    for (size_t it = 0; it < items.size(); it++) {
-        const SweepItem &w = items[it];
-        const int la = (int)((w.word_a >> 16) & 0xff);
-        long long first = -1, count = 0;
-        unsigned lnum = 0;
-        unsigned long long mask = 0;
-        for (int lane = 0; lane < 32; lane++) {
-            const bool pa = lane < la;
-            const unsigned wd = pa ? w.word_a : w.word_b, row = pa ? w.row_a : w.row_b;
-            const int lp = pa ? lane : lane - la;
-            const int len = (int)((wd >> 16) & 0xff), lead = (int)((wd >> 24) & 15), trail = (int)(wd >> 28);
-            if (lp >= len) continue;
-            const long long c0 = (long long)row * c.nx + 2LL * ((long long)(wd & 0xffff) - lead + lp);
-            for (int h = 0; h < 2; h++) {
-                if ((h == 0 && lead && lp == 0) || (h == 1 && trail && lp == len - 1)) continue;  // zero cell
-                const long long r = rank_of(c0 + h);
-                if (r < 0) continue;
-                if (first < 0) first = r;
-                if (r != first + count) return false;  // the item's links must be one range of slots
-                count++;
-                const int slot = 2 * lane + h;
-                mask |= 1ULL << slot;
-                for (int i = 1; i < 19; i++)
-                    if ((wr[(size_t)r].y >> i) & 1u)
-                        ws[wr[(size_t)r].x + (unsigned)__builtin_popcount(wr[(size_t)r].y & ((1u << i) - 1u))] =
-                            (unsigned short)(slot | (i << 6));
-                lnum += (unsigned)__builtin_popcount(wr[(size_t)r].y);
-            }
-        }
-        iw[it] = make_uint4(first < 0 ? 0u : wr[(size_t)first].x, lnum, (unsigned)mask, (unsigned)(mask >> 32));
-    }
-    static_assert(sizeof(SweepItem) == sizeof(uint4), "item layout");
+    static_assert(sizeof(SweepItem) == sizeof(uint4) && sizeof(PairItemWall) == sizeof(uint4), "item layout");
     if (cudaMemcpy(c.pair_items, items.data(), 16 * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c.pair_wall, iw.data(), 16 * iw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c.wslot, ws.data(), 2 * nl, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(c.wslot, ws.data(), 2 * ws.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return false;
     c.npair_items = (long long)items.size();
     c.pair_ready = 1;
