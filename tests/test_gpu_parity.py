@@ -375,6 +375,25 @@ def test_16bit_storage_ragged_rows_and_pipe(lbm, storage, tol):
     assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol
 
 
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16s", 2e-3), ("bf16s", 3e-2)])
+def test_pipe_ibb_without_body_force(lbm, storage, tol):
+    """The pipe sweeps' variants without a body force (a perturbed flow
+    decaying against the wall): the one-cell FP32 sweep and the 16-bit pair
+    sweep, each with the wall inside the sweep, over 150 steps."""
+    nx, ny, nz, R = 46, 44, 10, 20.5
+    g, o = pair(lbm, (nz, ny, nx), 0.62, storage=lbm.STORAGE[storage])
+    u = workloads.pipe_velocity(nx, ny, nz, R, 0.03, perturbation=0.2, seed=9)
+    for s in (g, o):
+        s.init_velocity(u)
+        s.set_pipe(R)
+    g.step(150, lbm.BC_IBB)
+    o.step(150, oracle.BC_IBB)
+    fluid = o.solid()[0] == 0
+    assert rel(g.macro()[1][:, fluid], o.macro()[1][:, fluid]) < tol
+    if storage == "f32":
+        assert rel(g.populations()[:, fluid], o.populations()[:, fluid]) < tol
+
+
 @pytest.mark.parametrize("storage,tol", [("f16s", 2e-3), ("bf16s", 3e-2)])
 def test_16bit_pipe_odd_width_one_cell_sweep(lbm, storage, tol):
     """A pipe of odd width on 16-bit storage: pairs of cells do not share
