@@ -475,13 +475,17 @@ def traffic_for(kernel_key):
 def profile_case(case, steps, warmup):
     """One workload alone, for a profiler's launch list or a kernel capture
     (the bench line itself is not printed): the particle-laden 256^3 box
-    (IBB or IBM-B), or the closure diagnostic on the 256^3 (or 128^3, 250
-    spheres) IBM-B box after `warmup` steps, repeated `steps` times."""
+    (IBB or IBM-B), the closure diagnostic on the 256^3 (or 128^3, 250
+    spheres) IBM-B box after `warmup` steps, repeated `steps` times, or the
+    D3Q27 pipe (FP32, its length from --nz) for `steps` steps."""
     import torch
     from paper_1906_05448_gb300 import build as B
     from paper_1906_05448_gb300 import lbm
     B.build()
     lbm.load()
+    if case == "q27_pipe":
+        print(json.dumps({"case": case, **q27_report(lbm, torch, steps=steps, warmup=warmup)}))
+        return
     if case.startswith("hit256"):
         bc = lbm.BC_IBB if case == "hit256_ibb" else lbm.BC_IBM_B
         r = run_case(lbm, torch, case, 256, 256, 256, 0.51, (0, 0, 0), lbm.F32, lbm.RATES_DHUMIERES, bc, steps,
@@ -523,7 +527,7 @@ def main():
                     help="wall treatment of the main line (default ibb; ibm_b only for profiler captures "
                          "of the IBM step, whose line is then not the benchmark's)")
     ap.add_argument("--case", default=None,
-                    choices=["hit256_ibb", "hit256_ibm_b", "closure256", "closure128"],
+                    choices=["hit256_ibb", "hit256_ibm_b", "closure256", "closure128", "q27_pipe"],
                     help="profiler captures only: run this one workload (--steps steps after --warmup) "
                          "and print its timings instead of the bench line")
     args = ap.parse_args()

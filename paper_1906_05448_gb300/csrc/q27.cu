@@ -11,6 +11,10 @@
 
 #include <vector>
 
+#ifndef LBM_Q27_MINB
+#define LBM_Q27_MINB 0  // resident blocks of 256 per SM the pipe kernel's registers are sized for (0: per storage)
+#endif
+
 namespace lbmgb {
 
 namespace {
@@ -229,8 +233,14 @@ __global__ void q27_coef_kernel(const unsigned *colmask, unsigned *hmask, void *
     hmask[col] = h;
 }
 
+// FP32: registers for 4 resident blocks of 256 per SM (64, no spills):
+// 0.387 ms per step on the benchmark pipe against 0.477 ms at 80 registers
+// (3 blocks), where only 13 of the 24 possible warps were active (the solid
+// cells' threads end at once, their blocks stay resident)
+constexpr int q27_min_blocks(int S) { return LBM_Q27_MINB > 0 ? LBM_Q27_MINB : (S == LBM_F32 ? 4 : 1); }
+
 template <int S, bool FORCE>
-__global__ void __launch_bounds__(256) q27_pipe_kernel(Q27PipeArgs pa) {
+__global__ void __launch_bounds__(256, q27_min_blocks(S)) q27_pipe_kernel(Q27PipeArgs pa) {
     typedef typename Store<S>::T T;
     typedef typename Store<S>::R R;
     const Q27Args &a = pa.b;
